@@ -1,0 +1,234 @@
+"""Upwind DG convection, its explicit propagation and the transfer operators.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+Definitions followed (Lehrenfeld & Schoeberl, arXiv:1508.04245):
+
+* Sec. 2.3: V_h = [P^k(T)]^d per element, mass form M^V (diagonal with the
+  orthonormal basis: M^V_T = |det J_T| Id), and the upwind trilinear form
+      C(u; w, z) = sum_T  - int_T (w (x) u) : grad z dx
+                          + int_{dT} (u . n) w^ z ds,
+  w^ the upwind value, i.e. the trace from the side the wind comes from.
+  With (w (x) u) : grad z = sum_c w_c (u . grad z_c), every velocity
+  component is transported as an independent scalar.
+* Sec. 3.2.2: the propagation problem dv/ds + (M^V)^{-1} C^V v = 0 with a
+  frozen wind; integrated here by SSP-RK2 (Heun) or SSP-RK3 (Shu-Osher)
+  (reading A6).
+* Sec. 2.4: the embedding I: W_h -> V_h through the L2 problem
+  int (I u) v = int u v for all v in V_h, and its transpose I^T.
+
+Readings: exact quadrature (A1); ``apply`` returns +(M^V)^{-1} C^V w, the
+ODE uses its negative (A8); a zero inflow datum on the domain boundary (A5);
+the interior trace on a tie u . n = 0 (A4).
+
+The operator is evaluated in physical coordinates: physical quadrature
+points, normals and facet measures, the wind by the Piola map, and the
+neighbour trace by mapping the physical facet point back into the neighbour
+with the inverse of its affine map (no permutation tables).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import basis as B
+from . import hdiv as H
+from .quadrature import simplex_rule
+
+
+class ConvectionOracle:
+    """(M^V)^{-1} C^V(u) for one fixed wind u in W_h, on a set of elements.
+
+    ``sel`` restricts the output to a subset of elements (the input state is
+    always the full vector, as neighbours are needed).
+    """
+
+    def __init__(self, mesh, k, u_hdiv, sel=None):
+        self.mesh, self.k = mesh, k
+        d = self.d = mesh.dim
+        self.N = B.dim_pk(d, k)
+        sel = np.arange(mesh.n_elem) if sel is None else np.asarray(sel, dtype=np.int64)
+        self.sel = sel
+        S = sel.size
+        J, Jinv, detJ = mesh.J[sel], mesh.Jinv[sel], mesh.detJ[sel]
+        self.absdet = np.abs(detJ)
+        Ucoef = H.ref_coeffs(mesh, k, u_hdiv, sel=sel)                  # [S, d, N]
+
+        # ---- volume: int_T w_c (u . grad psi_i) dx at exact quadrature -------
+        xq, wq = simplex_rule(d, 3 * k - 1)
+        polys = B.dubiner_polys(d, k)
+        self.Psi = B.eval_polys(polys, xq)                                # [Q, N]
+        dpolys = B.grad_polys(polys, d)
+        self.dPsi = np.stack([np.stack([B.P.evaluate(g[a], xq) for a in range(d)], axis=1)
+                              for g in dpolys], axis=1)                   # [Q, N, d]
+        uref = np.einsum("sci,qi->sqc", Ucoef, self.Psi)
+        uphys = np.einsum("sab,sqb->sqa", J, uref) / detJ[:, None, None]  # Piola
+        # u . grad psi_i = u . J^{-T} grad^ psi^_i = (J^{-1} u) . grad^ psi^_i
+        self.vol_g = (wq[None, :, None] * self.absdet[:, None, None]
+                      * np.einsum("sab,sqb->sqa", Jinv, uphys))           # [S, Q, d]
+
+        # ---- facets ---------------------------------------------------------
+        s, ws = simplex_rule(d - 1, 3 * k)
+        Qf = s.shape[0]
+        fact = math.factorial(d - 1)
+        X = mesh.X[sel]
+        self.psi_own = np.empty((S, d + 1, Qf, self.N))
+        self.psi_nb = np.zeros((S, d + 1, Qf, self.N))
+        self.un = np.empty((S, d + 1, Qf))
+        self.wt = np.empty((S, d + 1, Qf))
+        self.nbr = mesh.nbr[sel]
+        for f in range(d + 1):
+            fv = [v for v in range(d + 1) if v != f]
+            x = np.repeat(X[:, fv[0], None, :], Qf, axis=1)
+            for j in range(d - 1):
+                x = x + s[None, :, j, None] * (X[:, fv[j + 1], None, :] - X[:, fv[0], None, :])
+            xf = x.reshape(-1, d)                                          # physical facet points
+            ee = np.repeat(sel, Qf)
+            xi = mesh.to_reference(ee, xf)
+            self.psi_own[:, f] = B.dubiner_values(d, k, xi).reshape(S, Qf, self.N)
+            u_at = np.einsum("mab,mb->ma", mesh.J[ee],
+                             np.einsum("mci,mi->mc", np.repeat(Ucoef, Qf, axis=0),
+                                       self.psi_own[:, f].reshape(-1, self.N))) / mesh.detJ[ee][:, None]
+            self.un[:, f] = np.einsum("sqa,sa->sq", u_at.reshape(S, Qf, d), mesh.normal[sel, f])
+            self.wt[:, f] = fact * mesh.area[sel, f][:, None] * ws[None, :]
+            nb = self.nbr[:, f]
+            inner = nb >= 0
+            if np.any(inner):
+                ne = np.repeat(nb[inner], Qf)
+                xi_n = mesh.to_reference(ne, x[inner].reshape(-1, d))
+                self.psi_nb[inner, f] = B.dubiner_values(d, k, xi_n).reshape(-1, Qf, self.N)
+
+    def apply(self, w) -> np.ndarray:
+        """r = (M^V)^{-1} C^V(u) w on the selected elements; w: [E, d, N] -> [S, d, N]."""
+        w = np.asarray(w)
+        ws = w[self.sel]
+        # volume:  - sum_q w_q |det J| w_c(x_q) (u . grad psi_i)(x_q)
+        Wq = np.einsum("sci,qi->scq", ws, self.Psi)
+        vol = -np.einsum("scq,sqa,qia->sci", Wq, self.vol_g, self.dPsi, optimize=True)
+        # facets:  sum_f sum_q |F| w_q (u.n) w^_c psi_i
+        w_own = np.einsum("sci,sfqi->sfqc", ws, self.psi_own)
+        nbw = w[np.maximum(self.nbr, 0)]                                  # [S, d+1, d, N]
+        w_nb = np.einsum("sfci,sfqi->sfqc", nbw, self.psi_nb)             # 0 where boundary
+        hat = np.where((self.un >= 0)[..., None], w_own, w_nb)
+        flux = (self.wt * self.un)[..., None] * hat                       # [S, d+1, Qf, d]
+        fac = np.einsum("sfqc,sfqi->sci", flux, self.psi_own)
+        return (vol + fac) / self.absdet[:, None, None]
+
+
+def rk_substeps(op: ConvectionOracle, v, ds: float, nsteps: int, scheme: int) -> np.ndarray:
+    """nsteps explicit substeps of dv/ds = L v, L = -(M^V)^{-1} C^V (Sec. 3.2.2)."""
+    assert op.sel.size == op.mesh.n_elem
+    v = np.array(v, dtype=np.float64)
+    L = lambda x: -op.apply(x)                                            # noqa: E731
+    for _ in range(nsteps):
+        if scheme == 2:          # SSP-RK2 (Heun)
+            v1 = v + ds * L(v)
+            v = 0.5 * v + 0.5 * (v1 + ds * L(v1))
+        elif scheme == 3:        # SSP-RK3 (Shu-Osher)
+            v1 = v + ds * L(v)
+            v2 = 0.75 * v + 0.25 * (v1 + ds * L(v1))
+            v = v / 3.0 + 2.0 / 3.0 * (v2 + ds * L(v2))
+        else:
+            raise ValueError(scheme)
+    return v
+
+
+def transfer(mesh, k, u_hdiv) -> np.ndarray:
+    """w = I u: w_{c,i} = (1/|det J|) int_T u_c psi_i dx   (Sec. 2.4, L2 problem)."""
+    d = mesh.dim
+    xq, wq = simplex_rule(d, 2 * k)
+    E = mesh.n_elem
+    psi = B.dubiner_values(d, k, xq)                                     # [Q, N]
+    u = np.stack([H.evaluate(mesh, k, u_hdiv, np.full(xq.shape[0], e), xq) for e in range(E)]) \
+        if E <= 64 else _eval_all(mesh, k, u_hdiv, xq)                    # [E, Q, d]
+    return np.einsum("q,eqc,qi->eci", wq, u, psi)
+
+
+def _eval_all(mesh, k, u_hdiv, xq):
+    coef = H.ref_coeffs(mesh, k, u_hdiv)                                  # [E, d, N]
+    psi = B.dubiner_values(mesh.dim, k, xq)
+    uref = np.einsum("eci,qi->eqc", coef, psi)
+    return np.einsum("eab,eqb->eqa", mesh.J, uref) / mesh.detJ[:, None, None]
+
+
+def transfer_T(mesh, k, f_dg) -> np.ndarray:
+    """g = I^T f: g_j = sum_T sum_{c,i} f_{T,c,i} (I phi_j)_{T,c,i}  (Sec. 2.4).
+
+    Per element the local matrix column for the local BDM function s_j phi^_j
+    (Piola-mapped) is its transfer, (1/det J) J int_T^ phi^_j psi^_i dxi,
+    computed here by quadrature; the transpose is accumulated into the
+    global DOFs with np.add.at.
+    """
+    d = mesh.dim
+    N = B.dim_pk(d, k)
+    n_fm, n_int, n_w, n_hdiv = H.layout(mesh, k)
+    xq, wq = simplex_rule(d, 2 * k)
+    psi = B.dubiner_values(d, k, xq)                                     # [Q, N]
+    Cb = np.asarray(B.bdm_element(d, k), dtype=np.float64)               # phi_j = sum_b Cb[b, j] b_b
+    phi = np.einsum("qi,cib->qcb", psi, Cb.reshape(d, N, n_w))           # phi^_j(x_q) [Q, d, n_w]
+    R = np.einsum("q,qdj,qi->dij", wq, phi, psi)                         # int phi^_{j,dd} psi^_i
+    f = np.asarray(f_dg)
+    y = np.einsum("ecd,eci->edi", mesh.J, f) / mesh.detJ[:, None, None]  # (J / det J)^T f
+    z = np.einsum("dij,edi->ej", R, y)                                   # [E, n_w]
+    idx, sgn = H.dof_map(mesh, k)
+    g = np.zeros(n_hdiv)
+    np.add.at(g, idx.ravel(), (sgn * z).ravel())
+    return g
+
+
+def mass(mesh, v) -> np.ndarray:
+    """M^V v = |det J| v per element."""
+    return np.abs(mesh.detJ)[:, None, None] * np.asarray(v)
+
+
+def upwind_energy(mesh, k, u_hdiv, w) -> float:
+    """1/2 sum_F int_F |u.n| [[w]]^2 + 1/2 int_{dOmega} |u.n| w^2, by facet quadrature.
+
+    Computed facet by facet from physical facet points, with both traces
+    found by affine inversion; the right-hand side of the upwind energy
+    identity that follows from the stability statement of Sec. 2.3.
+    """
+    d = mesh.dim
+    s, ws = simplex_rule(d - 1, 3 * k)
+    fact = math.factorial(d - 1)
+    total = 0.0
+    for g in range(mesh.n_facets):
+        e, f = mesh.facet_owner[g]
+        fv = [v for v in range(d + 1) if v != f]
+        X = mesh.X[e]
+        x = X[fv[0]] + s @ (X[fv[1:]] - X[fv[0]])
+        xi = mesh.to_reference(np.full(len(s), e), x)
+        un = H.evaluate(mesh, k, u_hdiv, np.full(len(s), e), xi) @ mesh.normal[e, f]
+        wa = np.einsum("ci,qi->qc", w[e], B.dubiner_values(d, k, xi))
+        e2 = mesh.nbr[e, f]
+        if e2 >= 0:
+            xi2 = mesh.to_reference(np.full(len(s), e2), x)
+            wb = np.einsum("ci,qi->qc", w[e2], B.dubiner_values(d, k, xi2))
+        else:
+            wb = 0.0
+        total += 0.5 * fact * mesh.area[e, f] * np.sum(ws * np.abs(un) * np.sum((wa - wb) ** 2, axis=1))
+    return total
+
+
+def assemble(op: ConvectionOracle) -> np.ndarray:
+    """Dense matrix of w -> (M^V)^{-1} C^V w, column by column (tiny meshes)."""
+    E, d, N = op.mesh.n_elem, op.d, op.N
+    n = E * d * N
+    A = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = op.apply(e.reshape(E, d, N)).ravel()
+    return A
+
+
+def max_wind_speed(mesh, k, u_hdiv) -> float:
+    """max |u(x_q)| over the volume quadrature points (degree 3k-1 rule)."""
+    xq, _ = simplex_rule(mesh.dim, 3 * k - 1)
+    return float(np.linalg.norm(_eval_all(mesh, k, u_hdiv, xq), axis=2).max())
+
+
+def cfl_ds(mesh, k, u_hdiv, cfl: float) -> float:
+    """Substep size (reading A7): cfl * min_T h_T / ((2k+1) max |u|), h_T the shortest edge."""
+    return cfl * float(mesh.shortest_edge().min()) / ((2 * k + 1) * max_wind_speed(mesh, k, u_hdiv))
