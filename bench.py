@@ -1,0 +1,366 @@
+"""Benchmark of the explicit upwind-DG convection step on one GB300.
+
+Workload (default): 2D unit square, 256 x 256 squares split into 131072
+triangles, interior vertices jittered +-10% of h, order k = 4, wind = curl of a
+seeded 8-mode stream function, state = the BDM_k interpolant of a seeded
+8-mode Fourier velocity field; 100 SSP-RK3 substeps at CFL 0.2.
+
+One step is one pass of the whole hot path, the OIFS right-hand side of the
+paper's Sec. 3.2 for this velocity:
+    a1 geometry -> a2 v = I u^n -> 100 x (a3..a7 RK3 substep, frozen wind)
+    -> a6 M^V v -> a8 g = I^T M^V v.
+The metric counts DOF-stage updates: E * N * dim * 3 stages * 100 substeps.
+
+``value`` is measured with every input resident in HBM; ``e2e`` repeats the
+step through the same public calls with u^n and the wind copied from pinned
+host memory and g copied back inside the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1508_04245_gb300 import workloads as W  # noqa: E402
+
+METRIC = "DG convection DOF-stage updates/s, plain FP64 vs mixed/batched at ≤1e-6 err"
+WORKLOAD = "square256_k4"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dgconv", choices=["dgconv", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--substeps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload construction (untimed)
+# ---------------------------------------------------------------------------
+def make_inputs(wl, torch, dgconv):
+    verts, elems = wl.mesh()
+    mesh = dgconv.Mesh(wl.dim, wl.k, verts, elems)
+    pot = dgconv.potential_values(mesh, wl.potential())
+    wind = mesh.wind_from_potential(torch.tensor(pot, dtype=torch.float64, device="cuda"))
+    if wl.unit_peak_speed:
+        wind /= mesh.max_wind_speed(wind)
+    field = W.fourier_field(wl.seed + 2000, wl.dim)
+    X = mesh.point_coords(2)
+    u_n = mesh.hdiv_interpolate(torch.tensor(field(X), dtype=torch.float64, device="cuda"))
+    ds = mesh.cfl_ds(wind, wl.cfl)
+    return mesh, wind, u_n, ds
+
+
+def stage_bytes_flops(wl):
+    """Algorithmic bytes and flops per element per RK stage (method's own work).
+
+    bytes: read v^(i), read v^n, write v^(i+1) (FP64), the wind's N_W
+    coefficients, d^2+1 geometry values, d+1 neighbour ids.
+    flops: wind and state at the volume points, the gradient test
+    contraction, traces and facet test contraction.
+    """
+    d, k = wl.dim, wl.k
+    N = math.comb(k + d, d)
+    nq = (3 * k - 1) // 2 + 1
+    nf = (3 * k) // 2 + 1
+    Qv = nq ** d
+    Qf = nf ** (d - 1)
+    NW = d * N
+    byts = 3 * N * d * 8 + NW * 8 + (d * d + 1) * 8 + (d + 1) * 4
+    flops = 2 * Qv * N * d + 2 * Qv * N * d + 2 * Qv * N * d * d + 4 * (d + 1) * Qf * N * d
+    return byts, flops, N
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            m = json.load(f)
+        return m.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+class OracleRunner:
+    """The CPU oracle on the full mesh of a workload (setup untimed)."""
+
+    def __init__(self, wl):
+        from oracle import dg as ODG
+        from oracle import hdiv as OH
+        from oracle import mesh as OM
+        self.wl = wl
+        verts, elems = wl.mesh()
+        om = OM.Mesh(verts, elems)
+        wind = OH.wind_from_potential(om, wl.k, wl.potential())
+        if wl.unit_peak_speed:
+            wind = wind / ODG.max_wind_speed(om, wl.k, wind)
+        field = W.fourier_field(wl.seed + 2000, wl.dim)
+        u_n = OH.dofs_of_function(om, wl.k, lambda x: field(x))
+        self.op = ODG.ConvectionOracle(om, wl.k, wind)
+        self.v = ODG.transfer(om, wl.k, u_n)
+        self.ds = ODG.cfl_ds(om, wl.k, wind, wl.cfl)
+        self.units_per_stage = om.n_elem * math.comb(wl.k + wl.dim, wl.dim) * wl.dim
+
+    def stages(self, n: int):
+        """Time n explicit stages v <- v + ds L v of the oracle's operator."""
+        t0 = time.perf_counter()
+        v = self.v
+        for _ in range(n):
+            v = v + self.ds * (-self.op.apply(v))
+        dt = time.perf_counter() - t0
+        return self.units_per_stage * n / dt, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    wl = W.WORKLOADS[args.workload]
+    runner = OracleRunner(wl)
+    for _ in range(args.warmup):
+        runner.stages(1)
+    timed = [runner.stages(1) for _ in range(args.steps)]
+    total_t = sum(dt for _, dt in timed)
+    value = runner.units_per_stage * len(timed) / total_t
+    cores = os.cpu_count()
+    sample = "1 explicit stage (E*N*dim DOF updates) of the FP64 numpy oracle on the full mesh per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-stage updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / len(timed), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "elements": wl.n_elem, "k": wl.k, "dim": wl.dim, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "DOF-stage updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "DOF-stage updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    from paper_1508_04245_gb300 import build, dgconv
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = W.WORKLOADS[args.workload]
+    substeps = args.substeps or wl.substeps
+    mesh, wind, u_n, ds = make_inputs(wl, torch, dgconv)
+    stream = torch.cuda.current_stream()
+    v = mesh.dg_zeros()
+    mv = mesh.dg_zeros()
+    g = mesh.hdiv_zeros()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(un=u_n, wnd=wind):
+        mesh.geometry()                                   # a1
+        mesh.transfer(un, out=v)                          # a2
+        mesh.rk_substeps(wnd, v, ds, substeps, 3, args.prec)   # a3..a7
+        mesh.mass(v, out=mv)                              # a6 (M^V)
+        mesh.transfer_T(mv, out=g)                        # a8
+    launches_per_step = 1 + 1 + (1 + 3 * substeps) + 1 + 2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()                                     # evict L2 between timed steps
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+    # stage-kernel duration: difference of two graph lengths cancels the per-call kernels
+    def time_rk(n, reps=3):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            mesh.rk_substeps(wind, v, ds, n, 3, args.prec)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+    n_lo = max(substeps // 2, 1)
+    mesh.rk_substeps(wind, v, ds, n_lo, 3, args.prec)
+    t_lo = time_rk(n_lo)
+    mesh.rk_substeps(wind, v, ds, substeps, 3, args.prec)
+    t_hi = time_rk(substeps)
+    stage_ms = (t_hi - t_lo) / (3 * (substeps - n_lo))
+    clk = clocks.stop()
+
+    # end to end through the public calls with host buffers
+    u_host = torch.empty(mesh.n_hdiv, dtype=torch.float64, pin_memory=True)
+    w_host = torch.empty(mesh.n_hdiv, dtype=torch.float64, pin_memory=True)
+    g_host = torch.empty(mesh.n_hdiv, dtype=torch.float64, pin_memory=True)
+    u_host.copy_(u_n)
+    w_host.copy_(wind)
+    u_dev = torch.empty_like(u_n)
+    w_dev = torch.empty_like(wind)
+    e2e_ms = []
+    for i in range(max(args.steps, 1)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        u_dev.copy_(u_host, non_blocking=True)
+        w_dev.copy_(w_host, non_blocking=True)
+        step(u_dev, w_dev)
+        g_host.copy_(g, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+
+    # error of the mixed path against the FP64 GPU path (itself pinned to the oracle)
+    err = None
+    if args.prec != "fp64":
+        v64 = mesh.transfer(u_n)
+        mesh.rk_substeps(wind, v64, ds, substeps, 3, "fp64")
+        vmx = mesh.transfer(u_n)
+        mesh.rk_substeps(wind, vmx, ds, substeps, 3, args.prec)
+        torch.cuda.synchronize()
+        err = float((vmx - v64).abs().max() / v64.abs().max())
+
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    byts, flops, N = stage_bytes_flops(wl)
+    units_per_step = wl.n_elem * N * wl.dim * 3 * substeps
+    value = world * units_per_step / (ms * 1e-3)
+    e2e_val = world * units_per_step / (statistics.mean(e2e_ms) * 1e-3)
+    hbm, hbm_src = peaks()
+    achieved = byts * wl.n_elem / (stage_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "peak_source": hbm_src, "kernel": "stage_kernel",
+            "stage_ms": stage_ms, "alg_bytes_per_elem_stage": byts, "alg_flops_per_elem_stage": flops,
+            "achieved_tflops": flops * wl.n_elem / (stage_ms * 1e-3) / 1e12}
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF-stage updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "elements": wl.n_elem, "dim": wl.dim, "k": wl.k, "substeps": substeps,
+                   "scheme": "SSP-RK3", "prec": args.prec, "l2": "flushed between timed steps",
+                   "step": "a1 geometry, a2 I, 100x RK3 (a3-a7), M^V, a8 I^T"},
+        "max_rel_err_vs_fp64": err,
+        "e2e": {"value": e2e_val, "unit": "DOF-stage updates/s", "h2d_bytes_per_step": 2 * mesh.n_hdiv * 8,
+                "d2h_bytes_per_step": mesh.n_hdiv * 8},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        runner = OracleRunner(wl)
+        rate, dt = runner.stages(3)
+        line["cpu_baseline"] = {"value": rate, "unit": "DOF-stage updates/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"3 explicit stages of the FP64 numpy oracle on the full "
+                                          f"{wl.n_elem}-element mesh ({dt:.1f} s, setup untimed)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * dgconv -- the explicit upwind-DG convection step of Lehrenfeld & Schoeberl,
+ * "High order exactly divergence-free Hybrid Discontinuous Galerkin Methods
+ * for unsteady incompressible flows" (arXiv:1508.04245), on one GB300 GPU.
+ *
+ * The library evaluates, for affine triangles (dim = 2) and tetrahedra
+ * (dim = 3) of polynomial order k:
+ *
+ *   I        the transfer from the H(div)-conforming velocity space W_h
+ *            (BDM_k) to the DG space V_h = [P^k]^dim            (Sec. 2.4)
+ *   I^T      its transpose, from functionals on V_h to functionals on W_h
+ *   M^-1 C   the upwind DG convection operator of Sec. 2.3 with the diagonal
+ *            mass matrix of an L2-orthonormal basis
+ *   Q        explicit SSP Runge-Kutta substeps of the propagation problem
+ *            dv/ds + (M^V)^-1 C^V(u) v = 0 with a frozen wind u   (Sec. 3.2.2)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Status: 0 (DGC_OK) on success, a negative DGC_ERR_* code otherwise; the
+ *   message is available from dgc_last_error().  Argument errors are detected
+ *   on the host before anything is launched.
+ * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is enqueued asynchronously; no call synchronizes unless its
+ *   comment says so.
+ * - Memory: every array argument marked "device" is caller-owned device memory
+ *   of the stated length in doubles; "host" arrays are caller-owned host memory.
+ *   The library owns only the dgc_mesh handle, its geometry, its scratch
+ *   buffers and its cached CUDA graphs, all released by dgc_mesh_free().
+ * - DG layout ("dg vector", n_dg = E * dim * N doubles): element-major
+ *   [E][dim][N], coefficients of each velocity component on the orthonormal
+ *   Dubiner basis of the element (N = dim P^k), so M^V_T = |det J_T| Id.
+ * - H(div) layout ("hdiv vector", n_hdiv doubles): [n_facets][n_fm] facet
+ *   normal moments int_F u.n_F q_m dS (n_F = outward normal of the facet's
+ *   lower-index element, q_m the facet Dubiner basis in the facet's
+ *   sorted-vertex parametrisation, n_fm = dim P^k(F)), then [E][n_int]
+ *   interior moments against the unit-normalised Nedelec space N_{k-1}.
+ *   Global facets are numbered by their sorted vertex tuples in lexicographic
+ *   order.  The tangential facet unknowns of the HDG space have no part in
+ *   convection (Sec. 2.4) and are not represented.
+ * - Orders supported: dim 2, k = 1..6; dim 3, k = 1..5 (DGC_ERR_UNSUPPORTED
+ *   otherwise).
+ */
+#ifndef DGCONV_H
+#define DGCONV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgc_mesh dgc_mesh;
+typedef int dgc_status;
+
+#define DGC_OK 0
+#define DGC_ERR_ARG (-1)          /* invalid argument (null pointer, bad size, degenerate mesh) */
+#define DGC_ERR_CUDA (-2)         /* a CUDA runtime call or kernel launch failed */
+#define DGC_ERR_UNSUPPORTED (-3)  /* dimension / order / precision not available */
+#define DGC_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up */
+#define DGC_ERR_NONFINITE (-5)    /* a NaN or Inf was produced */
+#define DGC_ERR_ALLOC (-6)        /* device or host allocation failed */
+
+typedef enum { DGC_FP64 = 0, DGC_FP32 = 1, DGC_BF16X3 = 2 } dgc_prec;
+typedef enum { DGC_SSPRK2 = 2, DGC_SSPRK3 = 3 } dgc_scheme;
+
+/* Build a mesh handle: connectivity on the host, then geometry on the device
+ * (step a1).  verts: host [n_vert][dim]; elems: host [n_elem][dim+1] vertex
+ * ids of affine simplices (any local order; the library sorts each element's
+ * vertices by global id, which orients every facet consistently).  The mesh
+ * must be conforming (a facet is shared by at most two elements) and no
+ * element may be degenerate.  Synchronizes `stream` once at the end.
+ * Sec. 2 "Preliminaries" (affine simplicial partition, facets). */
+dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int n_elem,
+                           const int32_t* elems, void* stream, dgc_mesh** out);
+
+/* Release the handle and everything the library allocated for it. */
+dgc_status dgc_mesh_free(dgc_mesh* mesh);
+
+/* Lengths of the dg and hdiv vectors of this mesh. */
+dgc_status dgc_sizes(const dgc_mesh* mesh, int64_t* n_dg, int64_t* n_hdiv);
+
+/* info[0..10] = dim, k, n_elem, n_facets, N, N_W (=dim*N), n_fm, n_int,
+ * n_lagrange (=dim P^{k+1}), n_proj (points of the projection rule),
+ * n_dofpts (points per element of the H(div) interpolation). */
+dgc_status dgc_mesh_info(const dgc_mesh* mesh, int64_t* info);
+
+/* Step a1: recompute J (columns x_{i+1}-x_0 of the sorted vertices) and
+ * det J of every element on the device.  Affine elements, Sec. 2. */
+dgc_status dgc_geometry(dgc_mesh* mesh, void* stream);
+
+/* Step a2, w = I u (Sec. 2.4, eq. for the L2 problem defining I):
+ * (M^V)^-1 M^{U,V} applied to an hdiv vector.  u_hdiv: device [n_hdiv];
+ * w_dg: device [n_dg], overwritten.  FP64. */
+dgc_status dgc_transfer(dgc_mesh* mesh, const double* u_hdiv, double* w_dg, void* stream);
+
+/* Step a8, g = I^T f (Sec. 2.4): the transpose of I, mapping a functional on
+ * V_h (dg layout) to one on W_h (hdiv layout).  Facet entries are summed
+ * over their (at most two) elements in a fixed order, owner first, so the
+ * result is deterministic.  f_dg: device [n_dg]; g_hdiv: device [n_hdiv],
+ * overwritten.  FP64. */
+dgc_status dgc_transfer_T(dgc_mesh* mesh, const double* f_dg, double* g_hdiv, void* stream);
+
+/* out = M^V v (inverse = 0) or (M^V)^-1 v (inverse = 1); M^V_T = |det J_T| Id
+ * (Sec. 2.3, diagonal mass of an orthonormal basis).  device [n_dg] each;
+ * out may equal v. */
+dgc_status dgc_mass_apply(dgc_mesh* mesh, const double* v_dg, double* out_dg, int inverse, void* stream);
+
+/* Steps a3-a6: out = (M^V)^-1 C^V(u) w, the upwind DG convection operator of
+ * Sec. 2.3 with wind u in W_h (hdiv vector, exactly divergence-free for the
+ * stability statement of Sec. 2.3 to hold) and zero inflow datum on the domain
+ * boundary.  wind_hdiv: device [n_hdiv]; w_dg, out_dg: device [n_dg], must not
+ * overlap.  prec selects the contraction precision (DGC_FP64 or DGC_FP32; the
+ * result is written in FP64). */
+dgc_status dgc_conv_apply(dgc_mesh* mesh, const double* wind_hdiv, const double* w_dg, double* out_dg,
+                          dgc_prec prec, void* stream);
+
+/* Steps a3-a7 repeated: nsteps substeps of size ds of dv/ds = -(M^V)^-1 C^V(u) v
+ * (the propagation problem of Sec. 3.2.2) by SSP-RK2 (Heun) or SSP-RK3
+ * (Shu-Osher), wind frozen for the whole call.  v_dg: device [n_dg], FP64,
+ * updated in place; the stage combinations are accumulated in FP64 whatever
+ * prec is.  The launch sequence is captured in a CUDA graph cached on the
+ * handle and replayed when the same arguments come again. */
+dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg, double ds, int nsteps,
+                           dgc_scheme scheme, dgc_prec prec, void* stream);
+
+/* Points at which callers evaluate input fields, host [count][dim]:
+ * kind 0: the element-wise equispaced P^{k+1} Lagrange nodes used by
+ *         dgc_wind_from_potential ([E][n_lagrange][dim]);
+ * kind 1: the points of the projection rule used by dgc_project
+ *         ([E][n_proj][dim]);
+ * kind 2: the points of dgc_hdiv_interpolate ([E][n_dofpts][dim]): the facet
+ *         DOF points of local facets 0..dim, then the interior points.
+ * Writes count = rows when xyz is NULL. */
+dgc_status dgc_point_coords(const dgc_mesh* mesh, int kind, double* xyz, int64_t* count);
+
+/* Exactly divergence-free wind: the BDM_k DOFs of the curl of the P^{k+1}
+ * Lagrange interpolant of a stream function (dim 2) or of the three
+ * components of a vector potential (dim 3).  pot: device [E][n_lagrange]
+ * (dim 2) or [E][n_lagrange][3] (dim 3) values at the kind-0 points;
+ * u_hdiv: device [n_hdiv], overwritten.  (Input construction for the frozen,
+ * discretely divergence-free wind of Sec. 3.2.2.) */
+dgc_status dgc_wind_from_potential(dgc_mesh* mesh, const double* pot, double* u_hdiv, void* stream);
+
+/* BDM_k interpolant in W_h of a physical vector field given at the kind-2
+ * points: facet moments against the facet basis (taken from the facet's
+ * owner element), interior moments against N_{k-1}.  vals: device
+ * [E][n_dofpts][dim]; u_hdiv: device [n_hdiv], overwritten.  (Input
+ * construction: the H(div)-conforming velocity of Sec. 2.1.1.) */
+dgc_status dgc_hdiv_interpolate(dgc_mesh* mesh, const double* vals, double* u_hdiv, void* stream);
+
+/* L2 projection onto V_h of a field given at the kind-1 points:
+ * vals: device [E][n_proj][dim]; w_dg: device [n_dg], overwritten. */
+dgc_status dgc_project(dgc_mesh* mesh, const double* vals, double* w_dg, void* stream);
+
+/* max |u(x_q)| over the volume quadrature points (degree 3k-1 rule) of all
+ * elements.  Synchronizes `stream`; result in *out (host). */
+dgc_status dgc_max_wind_speed(dgc_mesh* mesh, const double* wind_hdiv, double* out, void* stream);
+
+/* Shortest element edge of the mesh (host value, from the upload). */
+dgc_status dgc_min_edge(const dgc_mesh* mesh, double* out);
+
+/* Host-only introspection (no GPU needed) -------------------------------- */
+
+/* Reference table `name` of the (dim, k) element, host double array.
+ * Names: "Bv" [QV][N] basis at the volume points, "Gv" [QV][N][dim] reference
+ * gradients, "wv" [QV] volume weights, "xv" [QV][dim] volume points, "wf" [QF]
+ * and "sf" [QF][dim-1] the facet rule, "Ef" [dim+1][n_fm][N] traces on the facet
+ * basis, "Qt" [QF][n_fm] facet basis at the facet points, "Cb" [N_W][N_W]
+ * the BDM_k basis on the vector Dubiner basis.  Writes *count = entries; out
+ * may be NULL to query the size. */
+dgc_status dgc_table(int dim, int k, const char* name, double* out, int64_t* count);
+
+/* Host connectivity exactly as dgc_mesh_upload builds it: facet_id
+ * [n_elem][dim+1], nbr [n_elem][dim+1] ((neighbour << 2) | neighbour's local
+ * facet, or -1 on the boundary), orient [n_elem][dim+1] (+1 owner/boundary,
+ * -1 otherwise), *n_facets.  Local facet f is opposite the f-th smallest
+ * vertex id of the element. */
+dgc_status dgc_connectivity(int dim, int n_vert, int n_elem, const int32_t* elems, int32_t* facet_id,
+                            int32_t* nbr, int8_t* orient, int32_t* n_facets);
+
+/* Copy the last error message of the calling thread into buf (len bytes,
+ * NUL-terminated).  Synchronizes nothing. */
+dgc_status dgc_last_error(char* buf, int len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGCONV_H */

@@ -1,0 +1,558 @@
+// C-ABI of the dgconv library: argument checking, the mesh handle (host
+// connectivity, device geometry, reference tables, scratch) and the launch
+// sequences of the entry points declared in include/dgconv.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dgconv.h"
+#include "dgc_kernels.h"
+#include "dgc_stage.cuh"
+
+using dgc::DevMesh;
+using dgc::Sizes;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+dgc_status fail(dgc_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define DGC_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t err_ = (call);                                                              \
+    if (err_ != cudaSuccess)                                                                \
+      return fail(DGC_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(err_),   \
+                  __FILE__, __LINE__);                                                      \
+  } while (0)
+
+template <typename T>
+struct DevBuf {
+  T* ptr = nullptr;
+  size_t n = 0;
+  cudaError_t alloc(size_t count) {
+    if (count <= n && ptr) return cudaSuccess;
+    release();
+    n = count;
+    return cudaMalloc(&ptr, std::max<size_t>(count, 1) * sizeof(T));
+  }
+  cudaError_t upload(const std::vector<T>& v) {
+    cudaError_t e = alloc(v.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    n = 0;
+  }
+};
+
+struct GraphKey {
+  const double* wind;
+  double* v;
+  double ds;
+  int nsteps, scheme, prec;
+  bool operator==(const GraphKey& o) const {
+    return wind == o.wind && v == o.v && ds == o.ds && nsteps == o.nsteps && scheme == o.scheme &&
+           prec == o.prec;
+  }
+};
+
+}  // namespace
+
+struct dgc_mesh {
+  Sizes s;
+  int E = 0, nF = 0, nV = 0;
+  std::vector<double> h_verts;     // [nV][D]
+  std::vector<int> h_elems;        // [E][NF] sorted
+  double h_min = 0.0;
+  DevBuf<double> verts, J, detJ;
+  DevBuf<int> elems, nbr, facet_id, facet_sides;
+  DevBuf<signed char> orient;
+  // FP64 tables
+  DevBuf<double> Bv, wv, wf, Bf, Cb, Lg_int, Lg_fac, Tint, wd, wfd, Qfd, Bd;
+  // stage-table blobs
+  DevBuf<double> tab64;
+  DevBuf<float> tab32;
+  // scratch
+  DevBuf<double> Uw64, Fw64, stage1, stage2, zbuf;
+  DevBuf<float> Uw32, Fw32;
+  DevBuf<unsigned long long> reduce;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  GraphKey graph_key{};
+
+  DevMesh view() const {
+    DevMesh m;
+    m.s = s;
+    m.E = E;
+    m.nF = nF;
+    m.nV = nV;
+    m.verts = verts.ptr;
+    m.elems = elems.ptr;
+    m.J = J.ptr;
+    m.detJ = detJ.ptr;
+    m.nbr = nbr.ptr;
+    m.facet_id = facet_id.ptr;
+    m.orient = orient.ptr;
+    m.facet_sides = facet_sides.ptr;
+    m.Bv = Bv.ptr;
+    m.wv = wv.ptr;
+    m.wf = wf.ptr;
+    m.Bf = Bf.ptr;
+    m.Cb = Cb.ptr;
+    m.Lg_int = Lg_int.ptr;
+    m.Lg_fac = Lg_fac.ptr;
+    m.Tint = Tint.ptr;
+    m.wd = wd.ptr;
+    m.wfd = wfd.ptr;
+    m.Qfd = Qfd.ptr;
+    m.Bd = Bd.ptr;
+    return m;
+  }
+
+  void release_all() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+    capture_stream = nullptr;
+    for (auto* b : {&verts, &J, &detJ, &Bv, &wv, &wf, &Bf, &Cb, &Lg_int, &Lg_fac, &Tint, &wd, &wfd, &Qfd,
+                    &Bd, &tab64, &Uw64, &Fw64, &stage1, &stage2, &zbuf})
+      b->release();
+    for (auto* b : {&elems, &nbr, &facet_id, &facet_sides}) b->release();
+    orient.release();
+    tab32.release();
+    Uw32.release();
+    Fw32.release();
+    reduce.release();
+  }
+};
+
+namespace {
+
+// stage-table blob in the layout of dgc::StageTab
+template <typename T>
+std::vector<T> stage_blob(const dgc::Tables& t) {
+  const Sizes& s = t.s;
+  auto pad = [](size_t n) { return (n + 3) / 4 * 4; };
+  std::vector<T> out;
+  auto put = [&](const std::vector<double>& v) {
+    size_t o = out.size();
+    out.resize(o + pad(v.size()), (T)0);
+    for (size_t j = 0; j < v.size(); ++j) out[o + j] = (T)v[j];
+  };
+  put(t.Bv);
+  put(t.Gv);
+  put(t.Ef);
+  put(t.Qt);
+  (void)s;
+  return out;
+}
+
+dgc_status check_mesh(const dgc_mesh* m) {
+  if (!m) return fail(DGC_ERR_ARG, "mesh handle is NULL");
+  return DGC_OK;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+dgc_status ensure_wind_scratch(dgc_mesh* m, bool fp32) {
+  cudaError_t perr = m->s.D == 2 ? dgc::launch_stage_2d(m->s.K, fp32, nullptr, nullptr)
+                                 : dgc::launch_stage_3d(m->s.K, fp32, nullptr, nullptr);
+  if (perr != cudaSuccess) return fail(DGC_ERR_CUDA, "stage kernel setup failed: %s", cudaGetErrorString(perr));
+  const size_t nu = (size_t)m->s.QV * m->s.D * m->E, nf = (size_t)m->s.NF * m->s.QF * m->E;
+  if (fp32) {
+    DGC_CUDA(m->Uw32.alloc(nu));
+    DGC_CUDA(m->Fw32.alloc(nf));
+  } else {
+    DGC_CUDA(m->Uw64.alloc(nu));
+    DGC_CUDA(m->Fw64.alloc(nf));
+  }
+  return DGC_OK;
+}
+
+dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double* vn, double* vout,
+                        double alpha, double beta, double gamma, cudaStream_t st) {
+  dgc::StageArgs a;
+  a.vin = vin;
+  a.vn = vn;
+  a.vout = vout;
+  a.Uw = fp32 ? (const void*)m->Uw32.ptr : (const void*)m->Uw64.ptr;
+  a.Fw = fp32 ? (const void*)m->Fw32.ptr : (const void*)m->Fw64.ptr;
+  a.nbr = m->nbr.ptr;
+  a.tab = fp32 ? (const void*)m->tab32.ptr : (const void*)m->tab64.ptr;
+  a.E = m->E;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.gamma = gamma;
+  cudaError_t err = m->s.D == 2 ? dgc::launch_stage_2d(m->s.K, fp32, &a, st) : dgc::launch_stage_3d(m->s.K, fp32, &a, st);
+  if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "stage kernel launch failed: %s", cudaGetErrorString(err));
+  return DGC_OK;
+}
+
+dgc_status check_prec(dgc_prec prec) {
+  if (prec == DGC_FP64 || prec == DGC_FP32) return DGC_OK;
+  if (prec == DGC_BF16X3) return fail(DGC_ERR_UNSUPPORTED, "precision DGC_BF16X3 is not available in this build");
+  return fail(DGC_ERR_ARG, "unknown precision %d", (int)prec);
+}
+
+// The launch sequence of dgc_rk_substeps (also what gets captured).
+dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, int nsteps, int scheme, bool fp32,
+                       cudaStream_t st) {
+  cudaError_t err = dgc::launch_wind_prep(m->view(), wind, fp32 ? (void*)m->Uw32.ptr : (void*)m->Uw64.ptr,
+                                          fp32 ? (void*)m->Fw32.ptr : (void*)m->Fw64.ptr, fp32, st);
+  if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "wind preparation failed: %s", cudaGetErrorString(err));
+  double* v1 = m->stage1.ptr;
+  double* v2 = m->stage2.ptr;
+  for (int n = 0; n < nsteps; ++n) {
+    dgc_status rc;
+    if (scheme == DGC_SSPRK2) {
+      // v1 = v + ds L(v);  v = 1/2 v + 1/2 (v1 + ds L(v1))
+      if ((rc = launch_stage(m, fp32, v, nullptr, v1, 0.0, 1.0, ds, st))) return rc;
+      if ((rc = launch_stage(m, fp32, v1, v, v, 0.5, 0.5, 0.5 * ds, st))) return rc;
+    } else {
+      // Shu-Osher SSP-RK3
+      if ((rc = launch_stage(m, fp32, v, nullptr, v1, 0.0, 1.0, ds, st))) return rc;
+      if ((rc = launch_stage(m, fp32, v1, v, v2, 0.75, 0.25, 0.25 * ds, st))) return rc;
+      if ((rc = launch_stage(m, fp32, v2, v, v, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * ds, st))) return rc;
+    }
+  }
+  return DGC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dgc_status dgc_last_error(char* buf, int len) {
+  if (!buf || len <= 0) return DGC_ERR_ARG;
+  snprintf(buf, (size_t)len, "%s", g_last_error.c_str());
+  return DGC_OK;
+}
+
+dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int n_elem, const int32_t* elems,
+                           void* stream, dgc_mesh** out) {
+  if (!out) return fail(DGC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fail(DGC_ERR_UNSUPPORTED, "dim must be 2 or 3 (got %d)", dim);
+  if (!dgc::supported(dim, k)) return fail(DGC_ERR_UNSUPPORTED, "order k=%d not supported for dim %d", k, dim);
+  if (n_vert <= 0 || n_elem <= 0 || !verts || !elems)
+    return fail(DGC_ERR_ARG, "empty mesh or NULL arrays (n_vert=%d, n_elem=%d)", n_vert, n_elem);
+  const int NF = dim + 1;
+  dgc_mesh* m = new dgc_mesh();
+  m->s = dgc::make_sizes(dim, k);
+  m->E = n_elem;
+  m->nV = n_vert;
+  m->h_verts.assign(verts, verts + (size_t)n_vert * dim);
+  m->h_elems.assign(elems, elems + (size_t)n_elem * NF);
+  // ---- connectivity (sorts each element's vertices) ---------------------------
+  dgc::Connectivity con;
+  std::string why = dgc::build_connectivity(dim, n_vert, n_elem, m->h_elems, con);
+  if (!why.empty()) {
+    delete m;
+    return fail(DGC_ERR_ARG, "%s", why.c_str());
+  }
+  m->nF = con.n_facets;
+  // ---- validate geometry, shortest edge ---------------------------------------
+  double hmin = INFINITY;
+  for (int e = 0; e < n_elem; ++e) {
+    const int* v = &m->h_elems[(size_t)e * NF];
+    double Jm[9];
+    for (int c = 0; c < dim; ++c)
+      for (int r = 0; r < dim; ++r) Jm[r * dim + c] = verts[(size_t)v[c + 1] * dim + r] - verts[(size_t)v[0] * dim + r];
+    double det = dim == 2 ? Jm[0] * Jm[3] - Jm[1] * Jm[2]
+                          : Jm[0] * (Jm[4] * Jm[8] - Jm[5] * Jm[7]) - Jm[1] * (Jm[3] * Jm[8] - Jm[5] * Jm[6]) +
+                                Jm[2] * (Jm[3] * Jm[7] - Jm[4] * Jm[6]);
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) {
+      delete m;
+      return fail(DGC_ERR_ARG, "element %d is degenerate (det J = %g)", e, det);
+    }
+    for (int a = 0; a < NF; ++a)
+      for (int b = a + 1; b < NF; ++b) {
+        double l2 = 0.0;
+        for (int r = 0; r < dim; ++r) {
+          double d = verts[(size_t)v[a] * dim + r] - verts[(size_t)v[b] * dim + r];
+          l2 += d * d;
+        }
+        hmin = std::min(hmin, std::sqrt(l2));
+      }
+  }
+  m->h_min = hmin;
+  // ---- device data ------------------------------------------------------------
+  cudaStream_t st = as_stream(stream);
+  const dgc::Tables* tp;
+  try {
+    tp = &dgc::tables(dim, k);
+  } catch (const std::exception& ex) {
+    delete m;
+    return fail(DGC_ERR_ARG, "reference table build failed: %s", ex.what());
+  }
+  const dgc::Tables& t = *tp;
+  auto up = [&](cudaError_t err) -> bool { return err == cudaSuccess; };
+  bool ok = up(m->verts.upload(m->h_verts)) && up(m->elems.upload(m->h_elems)) && up(m->nbr.upload(con.nbr)) &&
+            up(m->facet_id.upload(con.facet_id)) && up(m->orient.upload(con.orient)) &&
+            up(m->facet_sides.upload(con.sides)) &&
+            up(m->J.alloc((size_t)n_elem * dim * dim)) && up(m->detJ.alloc(n_elem)) && up(m->Bv.upload(t.Bv)) &&
+            up(m->wv.upload(t.wv)) && up(m->wf.upload(t.wf)) && up(m->Bf.upload(t.Bf)) && up(m->Cb.upload(t.Cb)) &&
+            up(m->Lg_int.upload(t.Lg_int)) && up(m->Lg_fac.upload(t.Lg_fac)) && up(m->Tint.upload(t.Tint)) &&
+            up(m->wd.upload(t.wd)) && up(m->wfd.upload(t.wfd)) && up(m->Qfd.upload(t.Qfd)) &&
+            up(m->Bd.upload(t.Bd)) && up(m->tab64.upload(stage_blob<double>(t))) &&
+            up(m->tab32.upload(stage_blob<float>(t)));
+  if (!ok) {
+    cudaError_t err = cudaGetLastError();
+    m->release_all();
+    delete m;
+    return fail(DGC_ERR_ALLOC, "device upload failed: %s", cudaGetErrorString(err));
+  }
+  cudaError_t err = dgc::launch_geometry(m->view(), st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) {
+    m->release_all();
+    delete m;
+    return fail(DGC_ERR_CUDA, "geometry kernel failed: %s", cudaGetErrorString(err));
+  }
+  *out = m;
+  return DGC_OK;
+}
+
+dgc_status dgc_mesh_free(dgc_mesh* mesh) {
+  if (!mesh) return DGC_OK;
+  mesh->release_all();
+  delete mesh;
+  return DGC_OK;
+}
+
+dgc_status dgc_sizes(const dgc_mesh* mesh, int64_t* n_dg, int64_t* n_hdiv) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (n_dg) *n_dg = (int64_t)mesh->E * mesh->s.D * mesh->s.N;
+  if (n_hdiv) *n_hdiv = (int64_t)mesh->nF * mesh->s.NFM + (int64_t)mesh->E * mesh->s.NINT;
+  return DGC_OK;
+}
+
+dgc_status dgc_mesh_info(const dgc_mesh* mesh, int64_t* info) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!info) return fail(DGC_ERR_ARG, "info is NULL");
+  const Sizes& s = mesh->s;
+  int64_t v[11] = {s.D, s.K, mesh->E, mesh->nF, s.N, s.NW, s.NFM, s.NINT, s.NLAG, s.QD, s.NF * s.QFD + s.QD};
+  std::memcpy(info, v, sizeof(v));
+  return DGC_OK;
+}
+
+dgc_status dgc_geometry(dgc_mesh* mesh, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  DGC_CUDA(dgc::launch_geometry(mesh->view(), as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_transfer(dgc_mesh* mesh, const double* u_hdiv, double* w_dg, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!u_hdiv || !w_dg) return fail(DGC_ERR_ARG, "NULL vector");
+  DGC_CUDA(dgc::launch_transfer(mesh->view(), u_hdiv, w_dg, as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_transfer_T(dgc_mesh* mesh, const double* f_dg, double* g_hdiv, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!f_dg || !g_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
+  DGC_CUDA(mesh->zbuf.alloc((size_t)mesh->E * mesh->s.NF * mesh->s.NFM));
+  DGC_CUDA(dgc::launch_transfer_T(mesh->view(), f_dg, g_hdiv, mesh->zbuf.ptr, as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_mass_apply(dgc_mesh* mesh, const double* v_dg, double* out_dg, int inverse, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!v_dg || !out_dg) return fail(DGC_ERR_ARG, "NULL vector");
+  DGC_CUDA(dgc::launch_mass(mesh->view(), v_dg, out_dg, inverse != 0, as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_conv_apply(dgc_mesh* mesh, const double* wind_hdiv, const double* w_dg, double* out_dg,
+                          dgc_prec prec, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (dgc_status rc = check_prec(prec)) return rc;
+  if (!wind_hdiv || !w_dg || !out_dg) return fail(DGC_ERR_ARG, "NULL vector");
+  const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
+  if (out_dg < w_dg + n && w_dg < out_dg + n) return fail(DGC_ERR_ARG, "out_dg overlaps w_dg");
+  const bool fp32 = prec == DGC_FP32;
+  if (dgc_status rc = ensure_wind_scratch(mesh, fp32)) return rc;
+  cudaStream_t st = as_stream(stream);
+  DGC_CUDA(dgc::launch_wind_prep(mesh->view(), wind_hdiv, fp32 ? (void*)mesh->Uw32.ptr : (void*)mesh->Uw64.ptr,
+                                 fp32 ? (void*)mesh->Fw32.ptr : (void*)mesh->Fw64.ptr, fp32, st));
+  // out = -L(w) = (M^V)^-1 C^V w
+  return launch_stage(mesh, fp32, w_dg, nullptr, out_dg, 0.0, 0.0, -1.0, st);
+}
+
+dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg, double ds, int nsteps,
+                           dgc_scheme scheme, dgc_prec prec, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (dgc_status rc = check_prec(prec)) return rc;
+  if (!wind_hdiv || !v_dg) return fail(DGC_ERR_ARG, "NULL vector");
+  if (scheme != DGC_SSPRK2 && scheme != DGC_SSPRK3) return fail(DGC_ERR_ARG, "unknown scheme %d", (int)scheme);
+  if (nsteps < 0) return fail(DGC_ERR_ARG, "nsteps must be >= 0 (got %d)", nsteps);
+  if (!(ds > 0.0) || !std::isfinite(ds)) return fail(DGC_ERR_ARG, "ds must be positive and finite (got %g)", ds);
+  if (nsteps == 0) return DGC_OK;
+  const bool fp32 = prec == DGC_FP32;
+  const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
+  if (dgc_status rc = ensure_wind_scratch(mesh, fp32)) return rc;
+  DGC_CUDA(mesh->stage1.alloc(n));
+  DGC_CUDA(mesh->stage2.alloc(n));
+  cudaStream_t st = as_stream(stream);
+  GraphKey key{wind_hdiv, v_dg, ds, nsteps, (int)scheme, (int)prec};
+  if (!(mesh->graph && mesh->graph_key == key)) {
+    if (mesh->graph) cudaGraphExecDestroy(mesh->graph);
+    mesh->graph = nullptr;
+    if (!mesh->capture_stream) DGC_CUDA(cudaStreamCreateWithFlags(&mesh->capture_stream, cudaStreamNonBlocking));
+    DGC_CUDA(cudaStreamBeginCapture(mesh->capture_stream, cudaStreamCaptureModeThreadLocal));
+    dgc_status rc = rk_sequence(mesh, wind_hdiv, v_dg, ds, nsteps, (int)scheme, fp32, mesh->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t err = cudaStreamEndCapture(mesh->capture_stream, &g);
+    if (rc != DGC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(err));
+    err = cudaGraphInstantiate(&mesh->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) {
+      mesh->graph = nullptr;
+      return fail(DGC_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(err));
+    }
+    mesh->graph_key = key;
+  }
+  DGC_CUDA(cudaGraphLaunch(mesh->graph, st));
+  return DGC_OK;
+}
+
+dgc_status dgc_point_coords(const dgc_mesh* mesh, int kind, double* xyz, int64_t* count) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (kind < 0 || kind > 2) return fail(DGC_ERR_ARG, "kind must be 0, 1 or 2");
+  const dgc::Tables& t = dgc::tables(mesh->s.D, mesh->s.K);
+  const int D = mesh->s.D, NF = D + 1;
+  std::vector<double> dofpts;
+  if (kind == 2) {   // facet DOF points of every local facet, then the interior points
+    dofpts = t.xfd;
+    dofpts.insert(dofpts.end(), t.xd.begin(), t.xd.end());
+  }
+  const std::vector<double>& ref = kind == 0 ? t.lag_nodes : (kind == 1 ? t.xd : dofpts);
+  const int P = (int)ref.size() / D;
+  if (count) *count = (int64_t)mesh->E * P;
+  if (!xyz) return DGC_OK;
+  for (int e = 0; e < mesh->E; ++e) {
+    const int* v = &mesh->h_elems[(size_t)e * NF];
+    const double* X0 = &mesh->h_verts[(size_t)v[0] * D];
+    for (int p = 0; p < P; ++p)
+      for (int r = 0; r < D; ++r) {
+        double x = X0[r];
+        for (int c = 0; c < D; ++c) x += (mesh->h_verts[(size_t)v[c + 1] * D + r] - X0[r]) * ref[p * D + c];
+        xyz[((size_t)e * P + p) * D + r] = x;
+      }
+  }
+  return DGC_OK;
+}
+
+dgc_status dgc_wind_from_potential(dgc_mesh* mesh, const double* pot, double* u_hdiv, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!pot || !u_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
+  DGC_CUDA(dgc::launch_wind_from_potential(mesh->view(), pot, u_hdiv, as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_hdiv_interpolate(dgc_mesh* mesh, const double* vals, double* u_hdiv, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!vals || !u_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
+  DGC_CUDA(dgc::launch_hdiv_interpolate(mesh->view(), vals, u_hdiv, as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_project(dgc_mesh* mesh, const double* vals, double* w_dg, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!vals || !w_dg) return fail(DGC_ERR_ARG, "NULL vector");
+  DGC_CUDA(dgc::launch_project(mesh->view(), vals, w_dg, as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_max_wind_speed(dgc_mesh* mesh, const double* wind_hdiv, double* out, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!wind_hdiv || !out) return fail(DGC_ERR_ARG, "NULL argument");
+  cudaStream_t st = as_stream(stream);
+  DGC_CUDA(mesh->reduce.alloc(1));
+  DGC_CUDA(cudaMemsetAsync(mesh->reduce.ptr, 0, sizeof(unsigned long long), st));
+  DGC_CUDA(dgc::launch_max_speed(mesh->view(), wind_hdiv, mesh->reduce.ptr, st));
+  unsigned long long bits = 0;
+  DGC_CUDA(cudaMemcpyAsync(&bits, mesh->reduce.ptr, sizeof(bits), cudaMemcpyDeviceToHost, st));
+  DGC_CUDA(cudaStreamSynchronize(st));
+  double v;
+  std::memcpy(&v, &bits, sizeof(v));
+  *out = v;
+  return DGC_OK;
+}
+
+dgc_status dgc_table(int dim, int k, const char* name, double* out, int64_t* count) {
+  if (!name || !count) return fail(DGC_ERR_ARG, "NULL argument");
+  if (!dgc::supported(dim, k)) return fail(DGC_ERR_UNSUPPORTED, "order k=%d not supported for dim %d", k, dim);
+  const dgc::Tables* tp;
+  try {
+    tp = &dgc::tables(dim, k);
+  } catch (const std::exception& ex) {
+    return fail(DGC_ERR_ARG, "reference table build failed: %s", ex.what());
+  }
+  const dgc::Tables& t = *tp;
+  const std::vector<double>* v = nullptr;
+  const std::string n(name);
+  if (n == "Bv") v = &t.Bv;
+  else if (n == "Gv") v = &t.Gv;
+  else if (n == "wv") v = &t.wv;
+  else if (n == "xv") v = &t.xv;
+  else if (n == "wf") v = &t.wf;
+  else if (n == "sf") v = &t.sf;
+  else if (n == "Ef") v = &t.Ef;
+  else if (n == "Qt") v = &t.Qt;
+  else if (n == "Cb") v = &t.Cb;
+  else return fail(DGC_ERR_ARG, "unknown table '%s'", name);
+  *count = (int64_t)v->size();
+  if (out) std::memcpy(out, v->data(), v->size() * sizeof(double));
+  return DGC_OK;
+}
+
+dgc_status dgc_connectivity(int dim, int n_vert, int n_elem, const int32_t* elems, int32_t* facet_id, int32_t* nbr,
+                            int8_t* orient, int32_t* n_facets) {
+  if (dim != 2 && dim != 3) return fail(DGC_ERR_UNSUPPORTED, "dim must be 2 or 3");
+  if (n_elem <= 0 || n_vert <= 0 || !elems) return fail(DGC_ERR_ARG, "empty mesh");
+  std::vector<int> el(elems, elems + (size_t)n_elem * (dim + 1));
+  dgc::Connectivity con;
+  std::string why = dgc::build_connectivity(dim, n_vert, n_elem, el, con);
+  if (!why.empty()) return fail(DGC_ERR_ARG, "%s", why.c_str());
+  const size_t n = (size_t)n_elem * (dim + 1);
+  for (size_t j = 0; j < n; ++j) {
+    if (facet_id) facet_id[j] = con.facet_id[j];
+    if (nbr) nbr[j] = con.nbr[j];
+    if (orient) orient[j] = con.orient[j];
+  }
+  if (n_facets) *n_facets = con.n_facets;
+  return DGC_OK;
+}
+
+dgc_status dgc_min_edge(const dgc_mesh* mesh, double* out) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!out) return fail(DGC_ERR_ARG, "out is NULL");
+  *out = mesh->h_min;
+  return DGC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,423 @@
+// Per-element FP64 kernels around the stage kernel: geometry (step a1),
+// frozen-wind preparation, the transfer I (a2) and its transpose I^T (a8),
+// the diagonal mass, and input construction (curl-of-potential winds,
+// L2 projection, wind speed for the CFL rule).
+//
+// These run once per call (not once per RK stage), so they use runtime sizes
+// and per-thread scratch arrays sized for the largest supported order.
+#include <cuda_runtime.h>
+
+#include "dgc_kernels.h"
+
+namespace dgc {
+namespace {
+
+constexpr int MAXW = 168;   // BDM_5 on tetrahedra
+constexpr int MAXF = 21;    // dim P^5 on a triangle
+constexpr int MAXI = 84;    // interior moments of BDM_5 on tetrahedra
+constexpr int MAXL = 84;    // dim P^6 in 3D (Lagrange nodes of P^{k+1})
+constexpr int BLOCK = 128;
+
+inline int grid_for(long n) { return (int)((n + BLOCK - 1) / BLOCK); }
+
+// -grad lambda_f on the reference simplex: (1, .., 1) for f = 0, -e_{f-1} otherwise
+__device__ __forceinline__ double mgl(int f, int a) { return f == 0 ? 1.0 : (a == f - 1 ? -1.0 : 0.0); }
+
+__global__ void geometry_kernel(DevMesh m) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const int D = m.s.D;
+  const int* v = m.elems + (long)e * (D + 1);
+  double X0[3], J[9];
+  for (int a = 0; a < D; ++a) X0[a] = m.verts[(long)v[0] * D + a];
+  for (int c = 0; c < D; ++c)
+    for (int r = 0; r < D; ++r) J[r * D + c] = m.verts[(long)v[c + 1] * D + r] - X0[r];
+  double det;
+  if (D == 2) {
+    det = J[0] * J[3] - J[1] * J[2];
+  } else {
+    det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+          J[2] * (J[3] * J[7] - J[4] * J[6]);
+  }
+  for (int j = 0; j < D * D; ++j) m.J[(long)e * D * D + j] = J[j];
+  m.detJ[e] = det;
+}
+
+// local BDM DOFs of element e, signs applied: facet moments of local facet f
+// carry orient(e, f) * sign(det J), interior moments are element-owned.
+__device__ void gather_local(const DevMesh& m, int e, const double* __restrict__ u, double* ut) {
+  const Sizes& s = m.s;
+  const double sg = m.detJ[e] > 0 ? 1.0 : -1.0;
+  for (int f = 0; f < s.NF; ++f) {
+    const long g = m.facet_id[(long)e * s.NF + f];
+    const double sf = sg * (double)m.orient[(long)e * s.NF + f];
+    for (int j = 0; j < s.NFM; ++j) ut[f * s.NFM + j] = sf * u[g * s.NFM + j];
+  }
+  const long base = (long)m.nF * s.NFM + (long)e * s.NINT;
+  for (int j = 0; j < s.NINT; ++j) ut[s.NF * s.NFM + j] = u[base + j];
+}
+
+// reference wind on the vector Dubiner basis: uc[a*N + i] = sum_j Cb[a*N+i][j] ut[j]
+__device__ void bdm_to_dubiner(const DevMesh& m, const double* ut, double* uc) {
+  const int NW = m.s.NW;
+  for (int b = 0; b < NW; ++b) {
+    double acc = 0.0;
+    const double* row = m.Cb + (long)b * NW;
+    for (int j = 0; j < NW; ++j) acc += row[j] * ut[j];
+    uc[b] = acc;
+  }
+}
+
+template <typename T>
+__global__ void wind_prep_kernel(DevMesh m, const double* __restrict__ u, T* __restrict__ Uw, T* __restrict__ Fw) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const Sizes& s = m.s;
+  const int D = s.D, N = s.N;
+  const long E = m.E;
+  double ut[MAXW], uc[MAXW];
+  gather_local(m, e, u, ut);
+  bdm_to_dubiner(m, ut, uc);
+  const double inv = 1.0 / m.detJ[e];
+  for (int q = 0; q < s.QV; ++q)
+    for (int a = 0; a < D; ++a) {
+      double acc = 0.0;
+      for (int i = 0; i < N; ++i) acc += m.Bv[q * N + i] * uc[a * N + i];
+      Uw[(long)(q * D + a) * E + e] = (T)(inv * m.wv[q] * acc);
+    }
+  for (int f = 0; f < s.NF; ++f)
+    for (int q = 0; q < s.QF; ++q) {
+      double acc = 0.0;
+      for (int a = 0; a < D; ++a) {
+        const double g = mgl(f, a);
+        if (g == 0.0) continue;
+        double ua = 0.0;
+        for (int i = 0; i < N; ++i) ua += m.Bf[(long)(f * s.QF + q) * N + i] * uc[a * N + i];
+        acc += g * ua;
+      }
+      Fw[(long)(f * s.QF + q) * E + e] = (T)(inv * m.wf[q] * acc);
+    }
+}
+
+// w_{c,i} = (1/det J) sum_a J[c][a] uc[a][i]   (= (1/|det J|) int_T u_c psi_i)
+__global__ void transfer_kernel(DevMesh m, const double* __restrict__ u, double* __restrict__ w) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const Sizes& s = m.s;
+  const int D = s.D, N = s.N;
+  double ut[MAXW], uc[MAXW];
+  gather_local(m, e, u, ut);
+  bdm_to_dubiner(m, ut, uc);
+  const double inv = 1.0 / m.detJ[e];
+  const double* J = m.J + (long)e * D * D;
+  double* we = w + (long)e * D * N;
+  for (int c = 0; c < D; ++c)
+    for (int i = 0; i < N; ++i) {
+      double acc = 0.0;
+      for (int a = 0; a < D; ++a) acc += J[c * D + a] * uc[a * N + i];
+      we[c * N + i] = inv * acc;
+    }
+}
+
+// transpose: y = (J/det J)^T f, z = Cb^T y; interior entries go straight to g,
+// facet entries (with their signs) to zbuf[e][f][m] for the facet reduction.
+__global__ void transfer_T_kernel(DevMesh m, const double* __restrict__ f, double* __restrict__ g,
+                                  double* __restrict__ zbuf) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const Sizes& s = m.s;
+  const int D = s.D, N = s.N, NW = s.NW;
+  double y[MAXW];
+  const double inv = 1.0 / m.detJ[e];
+  const double* J = m.J + (long)e * D * D;
+  const double* fe = f + (long)e * D * N;
+  for (int a = 0; a < D; ++a)
+    for (int i = 0; i < N; ++i) {
+      double acc = 0.0;
+      for (int c = 0; c < D; ++c) acc += J[c * D + a] * fe[c * N + i];
+      y[a * N + i] = inv * acc;
+    }
+  const double sg = m.detJ[e] > 0 ? 1.0 : -1.0;
+  for (int j = 0; j < NW; ++j) {
+    double z = 0.0;
+    for (int b = 0; b < NW; ++b) z += m.Cb[(long)b * NW + j] * y[b];
+    if (j < s.NF * s.NFM) {
+      const int lf = j / s.NFM;
+      const double sf = sg * (double)m.orient[(long)e * s.NF + lf];
+      zbuf[(long)e * s.NF * s.NFM + j] = sf * z;
+    } else {
+      g[(long)m.nF * s.NFM + (long)e * s.NINT + (j - s.NF * s.NFM)] = z;
+    }
+  }
+}
+
+// deterministic facet sums: owner side first, then the other side
+__global__ void facet_reduce_kernel(DevMesh m, const double* __restrict__ zbuf, double* __restrict__ g) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int NFM = m.s.NFM, NF = m.s.NF;
+  if (t >= (long)m.nF * NFM) return;
+  const long fg = t / NFM;
+  const int j = (int)(t % NFM);
+  const int s0 = m.facet_sides[2 * fg], s1 = m.facet_sides[2 * fg + 1];
+  double v = zbuf[((long)(s0 >> 2) * NF + (s0 & 3)) * NFM + j];
+  if (s1 >= 0) v += zbuf[((long)(s1 >> 2) * NF + (s1 & 3)) * NFM + j];
+  g[t] = v;
+}
+
+__global__ void mass_kernel(DevMesh m, const double* __restrict__ v, double* out, bool inverse) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long per = (long)m.s.D * m.s.N;
+  if (t >= (long)m.E * per) return;
+  const double a = fabs(m.detJ[t / per]);
+  out[t] = inverse ? v[t] / a : v[t] * a;
+}
+
+// inverse of the row-major D x D matrix J (det given)
+__device__ void invert_jacobian(int D, const double* J, double det, double* Jinv) {
+  if (D == 2) {
+    Jinv[0] = J[3] / det;
+    Jinv[1] = -J[1] / det;
+    Jinv[2] = -J[2] / det;
+    Jinv[3] = J[0] / det;
+  } else {
+    Jinv[0] = (J[4] * J[8] - J[5] * J[7]) / det;
+    Jinv[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+    Jinv[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+    Jinv[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+    Jinv[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+    Jinv[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+    Jinv[6] = (J[3] * J[7] - J[4] * J[6]) / det;
+    Jinv[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+    Jinv[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+  }
+}
+
+// reference field u^ = det J J^{-1} curl(potential interpolant) at one point
+__device__ void curl_ref(const DevMesh& m, const double* pot, const double* Lg, const double* Jinv, double det,
+                         double* uh) {
+  const int D = m.s.D, NL = m.s.NLAG;
+  const int nc = D == 2 ? 1 : 3;
+  double gr[3][3] = {{0}};
+  for (int n = 0; n < NL; ++n)
+    for (int c = 0; c < nc; ++c)
+      for (int a = 0; a < D; ++a) gr[c][a] += pot[n * nc + c] * Lg[n * D + a];
+  double gp[3][3] = {{0}};   // physical gradient J^{-T} grad^
+  for (int c = 0; c < nc; ++c)
+    for (int b = 0; b < D; ++b)
+      for (int a = 0; a < D; ++a) gp[c][b] += Jinv[a * D + b] * gr[c][a];
+  double u[3];
+  if (D == 2) {
+    u[0] = gp[0][1];
+    u[1] = -gp[0][0];
+  } else {
+    u[0] = gp[2][1] - gp[1][2];
+    u[1] = gp[0][2] - gp[2][0];
+    u[2] = gp[1][0] - gp[0][1];
+  }
+  for (int a = 0; a < D; ++a) {
+    double acc = 0.0;
+    for (int b = 0; b < D; ++b) acc += Jinv[a * D + b] * u[b];
+    uh[a] = det * acc;
+  }
+}
+
+__global__ void wind_from_potential_kernel(DevMesh m, const double* __restrict__ pot_all, double* __restrict__ u) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const Sizes& s = m.s;
+  const int D = s.D, NL = s.NLAG, nc = D == 2 ? 1 : 3;
+  const double* J = m.J + (long)e * D * D;
+  const double det = m.detJ[e];
+  double Jinv[9];
+  invert_jacobian(D, J, det, Jinv);
+  double pot[MAXL * 3];
+  for (int j = 0; j < NL * nc; ++j) pot[j] = pot_all[(long)e * NL * nc + j];
+  const double sg = det > 0 ? 1.0 : -1.0;
+  double uh[3];
+  // facet moments, computed by the facet's owner (orient = +1)
+  for (int f = 0; f < s.NF; ++f) {
+    if (m.orient[(long)e * s.NF + f] < 0) continue;
+    double acc[MAXF];
+    for (int j = 0; j < s.NFM; ++j) acc[j] = 0.0;
+    for (int q = 0; q < s.QFD; ++q) {
+      curl_ref(m, pot, m.Lg_fac + (long)(f * s.QFD + q) * NL * D, Jinv, det, uh);
+      double flux = 0.0;
+      for (int a = 0; a < D; ++a) flux += mgl(f, a) * uh[a];
+      for (int j = 0; j < s.NFM; ++j) acc[j] += m.wfd[q] * flux * m.Qfd[q * s.NFM + j];
+    }
+    const long g = m.facet_id[(long)e * s.NF + f];
+    for (int j = 0; j < s.NFM; ++j) u[g * s.NFM + j] = sg * acc[j];
+  }
+  if (s.NINT) {
+    double acc[MAXI];
+    for (int j = 0; j < s.NINT; ++j) acc[j] = 0.0;
+    for (int q = 0; q < s.QD; ++q) {
+      curl_ref(m, pot, m.Lg_int + (long)q * NL * D, Jinv, det, uh);
+      for (int j = 0; j < s.NINT; ++j) {
+        double t = 0.0;
+        for (int a = 0; a < D; ++a) t += uh[a] * m.Tint[((long)q * s.NINT + j) * D + a];
+        acc[j] += m.wd[q] * t;
+      }
+    }
+    const long base = (long)m.nF * s.NFM + (long)e * s.NINT;
+    for (int j = 0; j < s.NINT; ++j) u[base + j] = acc[j];
+  }
+}
+
+// BDM DOFs of a physical field given at the DOF points of every element:
+// vals[e][f*QFD + q][:] on local facet f, vals[e][NF*QFD + q][:] inside.
+__global__ void hdiv_interpolate_kernel(DevMesh m, const double* __restrict__ vals, double* __restrict__ u) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const Sizes& s = m.s;
+  const int D = s.D;
+  const int P = s.NF * s.QFD + s.QD;
+  const double* J = m.J + (long)e * D * D;
+  const double det = m.detJ[e];
+  double Jinv[9];
+  invert_jacobian(D, J, det, Jinv);
+  const double sg = det > 0 ? 1.0 : -1.0;
+  const double* ve = vals + (long)e * P * D;
+  double uh[3];
+  auto to_ref = [&](const double* x) {   // u^ = det J J^{-1} u
+    for (int a = 0; a < D; ++a) {
+      double acc = 0.0;
+      for (int b = 0; b < D; ++b) acc += Jinv[a * D + b] * x[b];
+      uh[a] = det * acc;
+    }
+  };
+  for (int f = 0; f < s.NF; ++f) {
+    if (m.orient[(long)e * s.NF + f] < 0) continue;
+    double acc[MAXF];
+    for (int j = 0; j < s.NFM; ++j) acc[j] = 0.0;
+    for (int q = 0; q < s.QFD; ++q) {
+      to_ref(ve + (long)(f * s.QFD + q) * D);
+      double flux = 0.0;
+      for (int a = 0; a < D; ++a) flux += mgl(f, a) * uh[a];
+      for (int j = 0; j < s.NFM; ++j) acc[j] += m.wfd[q] * flux * m.Qfd[q * s.NFM + j];
+    }
+    const long g = m.facet_id[(long)e * s.NF + f];
+    for (int j = 0; j < s.NFM; ++j) u[g * s.NFM + j] = sg * acc[j];
+  }
+  if (s.NINT) {
+    double acc[MAXI];
+    for (int j = 0; j < s.NINT; ++j) acc[j] = 0.0;
+    for (int q = 0; q < s.QD; ++q) {
+      to_ref(ve + (long)(s.NF * s.QFD + q) * D);
+      for (int j = 0; j < s.NINT; ++j) {
+        double t = 0.0;
+        for (int a = 0; a < D; ++a) t += uh[a] * m.Tint[((long)q * s.NINT + j) * D + a];
+        acc[j] += m.wd[q] * t;
+      }
+    }
+    const long base = (long)m.nF * s.NFM + (long)e * s.NINT;
+    for (int j = 0; j < s.NINT; ++j) u[base + j] = acc[j];
+  }
+}
+
+__global__ void project_kernel(DevMesh m, const double* __restrict__ vals, double* __restrict__ w) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const Sizes& s = m.s;
+  const int D = s.D, N = s.N;
+  for (int c = 0; c < D; ++c)
+    for (int i = 0; i < N; ++i) {
+      double acc = 0.0;
+      for (int q = 0; q < s.QD; ++q) acc += m.wd[q] * vals[((long)e * s.QD + q) * D + c] * m.Bd[q * N + i];
+      w[((long)e * D + c) * N + i] = acc;
+    }
+}
+
+__global__ void max_speed_kernel(DevMesh m, const double* __restrict__ u, unsigned long long* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const Sizes& s = m.s;
+  const int D = s.D, N = s.N;
+  double ut[MAXW], uc[MAXW];
+  gather_local(m, e, u, ut);
+  bdm_to_dubiner(m, ut, uc);
+  const double* J = m.J + (long)e * D * D;
+  const double inv = 1.0 / fabs(m.detJ[e]);
+  double vmax = 0.0;
+  for (int q = 0; q < s.QV; ++q) {
+    double uh[3];
+    for (int a = 0; a < D; ++a) {
+      double acc = 0.0;
+      for (int i = 0; i < N; ++i) acc += m.Bv[q * N + i] * uc[a * N + i];
+      uh[a] = acc;
+    }
+    double n2 = 0.0;
+    for (int r = 0; r < D; ++r) {
+      double x = 0.0;
+      for (int a = 0; a < D; ++a) x += J[r * D + a] * uh[a];
+      n2 += x * x;
+    }
+    vmax = fmax(vmax, sqrt(n2) * inv);
+  }
+  atomicMax(out, (unsigned long long)__double_as_longlong(vmax));
+}
+
+}  // namespace
+
+cudaError_t launch_geometry(const DevMesh& m, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  geometry_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wind_prep(const DevMesh& m, const double* u, void* Uw, void* Fw, bool fp32, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  if (fp32)
+    wind_prep_kernel<float><<<grid_for(m.E), BLOCK, 0, s>>>(m, u, (float*)Uw, (float*)Fw);
+  else
+    wind_prep_kernel<double><<<grid_for(m.E), BLOCK, 0, s>>>(m, u, (double*)Uw, (double*)Fw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transfer(const DevMesh& m, const double* u, double* w, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  transfer_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, u, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transfer_T(const DevMesh& m, const double* f, double* g, double* zbuf, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  transfer_T_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, f, g, zbuf);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  facet_reduce_kernel<<<grid_for((long)m.nF * m.s.NFM), BLOCK, 0, s>>>(m, zbuf, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass(const DevMesh& m, const double* v, double* out, bool inverse, cudaStream_t s) {
+  const long n = (long)m.E * m.s.D * m.s.N;
+  if (n == 0) return cudaSuccess;
+  mass_kernel<<<grid_for(n), BLOCK, 0, s>>>(m, v, out, inverse);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wind_from_potential(const DevMesh& m, const double* pot, double* u, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  wind_from_potential_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, pot, u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hdiv_interpolate(const DevMesh& m, const double* vals, double* u, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  hdiv_interpolate_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, vals, u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(const DevMesh& m, const double* vals, double* w, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  project_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, vals, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_speed(const DevMesh& m, const double* u, unsigned long long* out, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  max_speed_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, u, out);
+  return cudaGetLastError();
+}
+
+}  // namespace dgc

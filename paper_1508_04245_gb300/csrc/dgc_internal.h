@@ -1,0 +1,91 @@
+// Internal declarations of the dgconv library (not part of the C-ABI).
+//
+// Discretisation (Lehrenfeld & Schoeberl, arXiv:1508.04245):
+//   V_h  = [P^k(T)]^d per affine simplex, L2-orthonormal (Dubiner) basis, so
+//          the DG mass matrix is |det J_T| Id            (Sec. 2.3)
+//   W_h  = BDM_k, facet normal moments + Nedelec interior moments (Sec. 2.1.1)
+//   C_h  = upwind DG trilinear form                      (Sec. 2.3)
+//
+// Everything a kernel needs is expressed on the reference simplex: with the
+// contravariant Piola map u = J u^/det J the volume term u . grad psi_i
+// |det J| becomes sign(det J) u^ . grad^ psi^_i and the facet flux
+// (u . n) dS becomes sign(det J) (u^ . (-grad lambda_f)) ds on the facet
+// parameter simplex, so the stage kernels see one scalar 1/det J per element,
+// folded into the frozen wind data, and no Jacobian.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace dgc {
+
+constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
+
+// Compile-time sizes of one (dimension, order) pair.
+template <int D, int K>
+struct Dims {
+  static constexpr int N = D == 2 ? (K + 1) * (K + 2) / 2 : (K + 1) * (K + 2) * (K + 3) / 6;
+  static constexpr int NF = D + 1;                                    // facets per element
+  static constexpr int NFM = D == 2 ? K + 1 : (K + 1) * (K + 2) / 2;  // dim P^k(facet)
+  static constexpr int NW = D * N;                                    // dim BDM_k
+  static constexpr int NINT = NW - NF * NFM;                          // interior moments
+  static constexpr int NQ1V = (3 * K - 1) / 2 + 1;                    // volume rule, degree 3k-1
+  static constexpr int QV = cpow(NQ1V, D);
+  static constexpr int NQ1F = (3 * K) / 2 + 1;                        // facet rule, degree 3k
+  static constexpr int QF = cpow(NQ1F, D - 1);
+};
+
+// Runtime copy of the same sizes.
+struct Sizes {
+  int D, K, N, NF, NFM, NW, NINT, QV, QF;
+  int NLAG;      // Lagrange nodes of P^{k+1} (potential interpolation)
+  int QD;        // interior rule of the DOF / projection computations
+  int QFD;       // facet rule of the DOF computations
+};
+Sizes make_sizes(int D, int K);
+
+// Reference tables of one (D, K), built on the host in long double and
+// stored as double.  Layouts are row-major in the order of the index list.
+struct Tables {
+  Sizes s;
+  // stage-kernel tables
+  std::vector<double> Bv;    // [QV][N]        psi^_i(xi_q)
+  std::vector<double> Gv;    // [QV][N][D]     d_a psi^_i(xi_q)
+  std::vector<double> Ef;    // [NF][NFM][N]   psi^_i restricted to facet f, on the facet basis
+  std::vector<double> Qt;    // [QF][NFM]      facet basis at the facet points
+  // wind preparation
+  std::vector<double> wv;    // [QV]           volume weights (sum 1/D!)
+  std::vector<double> wf;    // [QF]           facet-parameter weights (sum 1/(D-1)!)
+  std::vector<double> Bf;    // [NF][QF][N]    psi^_i at the facet points of facet f
+  std::vector<double> Cb;    // [NW][NW]       BDM basis on the vector Dubiner basis, [b][j]
+  // DOFs of curls of potentials (Lagrange P^{k+1})
+  std::vector<double> lag_nodes;  // [NLAG][D]
+  std::vector<double> Lg_int;     // [QD][NLAG][D]     grad^ of Lagrange fns at interior points
+  std::vector<double> Lg_fac;     // [NF][QFD][NLAG][D] at the facet DOF points
+  std::vector<double> Tint;       // [QD][NINT][D]     interior test fields (unit L2 norm)
+  std::vector<double> wd;         // [QD]
+  std::vector<double> wfd;        // [QFD]
+  std::vector<double> Qfd;        // [QFD][NFM]        facet basis at facet DOF points
+  // projection of point values onto V_h
+  std::vector<double> xd;         // [QD][D]  interior DOF / projection points
+  std::vector<double> Bd;         // [QD][N]
+  // rule points (for introspection)
+  std::vector<double> xfd;        // [NF][QFD][D]  facet DOF points on each local facet
+  std::vector<double> xv;         // [QV][D]
+  std::vector<double> sf;         // [QF][D-1]
+};
+
+const Tables& tables(int D, int K);   // cached, thread-safe build
+bool supported(int D, int K);
+
+// Facet connectivity of a conforming simplicial mesh (elements' vertex ids
+// sorted in place).  Returns an empty string on success, else the reason.
+struct Connectivity {
+  int n_facets = 0;
+  std::vector<int> facet_id, nbr, sides;
+  std::vector<signed char> orient;
+};
+std::string build_connectivity(int D, int n_vert, int n_elem, std::vector<int>& elems, Connectivity& out);
+
+}  // namespace dgc

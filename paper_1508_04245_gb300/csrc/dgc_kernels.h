@@ -1,0 +1,58 @@
+// Launch wrappers of the dgconv kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dgc_internal.h"
+
+namespace dgc {
+
+struct StageArgs;
+
+// Device view of a mesh and of its FP64 reference tables.
+struct DevMesh {
+  Sizes s;
+  int E, nF, nV;
+  const double* verts;        // [nV][D]
+  const int* elems;           // [E][NF], sorted vertex ids
+  double* J;                  // [E][D][D]
+  double* detJ;               // [E]
+  const int* nbr;             // [E][NF]  (e' << 2) | f', or -1
+  const int* facet_id;        // [E][NF]
+  const signed char* orient;  // [E][NF]  +1 owner / boundary, -1 otherwise
+  const int* facet_sides;     // [nF][2]  (e << 2) | f, second entry -1 on the boundary
+  // FP64 tables
+  const double* Bv;
+  const double* wv;
+  const double* wf;
+  const double* Bf;
+  const double* Cb;
+  const double* Lg_int;
+  const double* Lg_fac;
+  const double* Tint;
+  const double* wd;
+  const double* wfd;
+  const double* Qfd;
+  const double* Bd;
+};
+
+// a == nullptr prepares the kernel (shared-memory attribute) without launching
+cudaError_t launch_stage_2d(int K, bool fp32, const StageArgs* a, cudaStream_t s);
+cudaError_t launch_stage_3d(int K, bool fp32, const StageArgs* a, cudaStream_t s);
+
+cudaError_t launch_geometry(const DevMesh& m, cudaStream_t s);
+// frozen-wind data of the stage kernels: Uw [QV*D][E], Fw [NF*QF][E] in float or double
+cudaError_t launch_wind_prep(const DevMesh& m, const double* u_hdiv, void* Uw, void* Fw, bool fp32,
+                             cudaStream_t s);
+cudaError_t launch_transfer(const DevMesh& m, const double* u_hdiv, double* w_dg, cudaStream_t s);
+cudaError_t launch_transfer_T(const DevMesh& m, const double* f_dg, double* g_hdiv, double* zbuf,
+                              cudaStream_t s);
+cudaError_t launch_mass(const DevMesh& m, const double* v, double* out, bool inverse, cudaStream_t s);
+cudaError_t launch_wind_from_potential(const DevMesh& m, const double* pot, double* u_hdiv, cudaStream_t s);
+// BDM DOFs of a physical field given at the DOF points: vals [E][NF*QFD + QD][D]
+cudaError_t launch_hdiv_interpolate(const DevMesh& m, const double* vals, double* u_hdiv, cudaStream_t s);
+cudaError_t launch_project(const DevMesh& m, const double* vals, double* w_dg, cudaStream_t s);
+cudaError_t launch_max_speed(const DevMesh& m, const double* u_hdiv, unsigned long long* out_bits,
+                             cudaStream_t s);
+
+}  // namespace dgc

@@ -1,0 +1,36 @@
+"""Shared setup of the GPU parity tests: seeded meshes, winds and states, and
+the oracle's side of every comparison (the oracle never sees CUDA output)."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import dg as ODG
+from oracle import hdiv as OH
+from oracle import mesh as OM
+from paper_1508_04245_gb300 import workloads as W
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def maxrel(got, ref) -> float:
+    """Max-norm relative error over the whole vector (reading A17)."""
+    got = np.asarray(got, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    return float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def make_case(dim, k, n, jitter=0.1, seed=1, potential=None):
+    verts, elems = W.square_mesh(n, jitter, seed) if dim == 2 else W.cube_mesh(n, jitter, seed)
+    if potential is None:
+        potential = W.stream_random(seed + 7) if dim == 2 else W.potential_random(seed + 7)
+    omesh = OM.Mesh(verts, elems)
+    wind = OH.wind_from_potential(omesh, k, potential)
+    return verts, elems, potential, omesh, wind
+
+
+def oracle_state(omesh, k, seed=3):
+    return W.uniform_coeffs(seed, omesh.n_elem, omesh.dim, k)
+
+
+def oracle_ds(omesh, k, wind, cfl=0.2):
+    return ODG.cfl_ds(omesh, k, wind, cfl)
