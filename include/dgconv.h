@@ -159,6 +159,27 @@ dgc_status dgc_max_wind_speed(dgc_mesh* mesh, const double* wind_hdiv, double* o
 /* Shortest element edge of the mesh (host value, from the upload). */
 dgc_status dgc_min_edge(const dgc_mesh* mesh, double* out);
 
+/* Maximum scratch of dgc_transfer_T_noalloc, in doubles (16 MiB). */
+#define DGC_NOALLOC_SCRATCH_DOUBLES 2097152LL
+
+/* g = I^T f exactly as dgc_transfer_T, for callers that cannot allocate
+ * device memory when they call: code that runs while a stream is captured
+ * into a CUDA graph, or applications that fix their device memory at start-up
+ * (dgc_transfer_T allocates its facet scratch on the handle at its first call).
+ * The paper has no counterpart; this is a library service.
+ * Scratch: a fixed file-scope device array of DGC_NOALLOC_SCRATCH_DOUBLES
+ * doubles, held on every GPU that loads the library until the process exits.
+ * The mesh must need at most that many (n_elem * (dim+1) * n_fm); larger
+ * meshes get DGC_ERR_ARG and a message, and nothing is launched.  The call
+ * performs no allocation (no cudaMalloc / cudaFree).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) for that
+ * device; make that first call before any stream capture.  All calls share
+ * the one array, so calls that overlap on the GPU (different streams, or
+ * different handles concurrently) race; serialise them.  Every scratch entry a
+ * call reads is written by the same call first.  Arguments, layouts and
+ * errors as dgc_transfer_T. */
+dgc_status dgc_transfer_T_noalloc(dgc_mesh* mesh, const double* f_dg, double* g_hdiv, void* stream);
+
 /* Host-only introspection (no GPU needed) -------------------------------- */
 
 /* Reference table `name` of the (dim, k) element, host double array.

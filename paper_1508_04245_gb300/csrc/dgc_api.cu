@@ -238,6 +238,16 @@ dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, in
 
 }  // namespace
 
+namespace dgc {
+// helpers for entry points defined in other translation units
+bool mesh_view(const dgc_mesh* mesh, DevMesh* out) {
+  if (!mesh) return false;
+  *out = mesh->view();
+  return true;
+}
+dgc_status set_error(dgc_status code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace dgc
+
 extern "C" {
 
 dgc_status dgc_last_error(char* buf, int len) {

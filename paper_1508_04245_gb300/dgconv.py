@@ -30,6 +30,7 @@ SIGNATURES = {
     "dgc_geometry": [_vp, _vp],
     "dgc_transfer": [_vp, _vp, _vp, _vp],
     "dgc_transfer_T": [_vp, _vp, _vp, _vp],
+    "dgc_transfer_T_noalloc": [_vp, _vp, _vp, _vp],
     "dgc_mass_apply": [_vp, _vp, _vp, ctypes.c_int, _vp],
     "dgc_conv_apply": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp],
     "dgc_rk_substeps": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
