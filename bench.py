@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dgconv", choices=["dgconv", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "tf32x3"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--substeps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -338,7 +338,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "DOF-stage updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3"}[args.prec], "data": "synthetic",
         "config": {"workload": wl.name, "elements": wl.n_elem, "dim": wl.dim, "k": wl.k, "substeps": substeps,
                    "scheme": "SSP-RK3", "prec": args.prec, "l2": "flushed between timed steps",
                    "step": "a1 geometry, a2 I, 100x RK3 (a3-a7), M^V, a8 I^T"},

@@ -60,7 +60,15 @@ typedef int dgc_status;
 #define DGC_ERR_NONFINITE (-5)    /* a NaN or Inf was produced */
 #define DGC_ERR_ALLOC (-6)        /* device or host allocation failed */
 
-typedef enum { DGC_FP64 = 0, DGC_FP32 = 1, DGC_BF16X3 = 2 } dgc_prec;
+/* Contraction precision of the convection stages; the state and the RK stage
+ * combinations are FP64 in every mode.
+ *   DGC_FP64    FP64 on CUDA cores
+ *   DGC_FP32    FP32 on CUDA cores
+ *   DGC_BF16X3  reserved (not available)
+ *   DGC_TF32X3  tcgen05 tensor cores, kind::tf32, each operand split into a
+ *               TF32 head and tail, three products, FP32 accumulation
+ *               (triangles, k <= 4) */
+typedef enum { DGC_FP64 = 0, DGC_FP32 = 1, DGC_BF16X3 = 2, DGC_TF32X3 = 3 } dgc_prec;
 typedef enum { DGC_SSPRK2 = 2, DGC_SSPRK3 = 3 } dgc_scheme;
 
 /* Build a mesh handle: connectivity on the host, then geometry on the device
@@ -109,8 +117,8 @@ dgc_status dgc_mass_apply(dgc_mesh* mesh, const double* v_dg, double* out_dg, in
  * Sec. 2.3 with wind u in W_h (hdiv vector, exactly divergence-free for the
  * stability statement of Sec. 2.3 to hold) and zero inflow datum on the domain
  * boundary.  wind_hdiv: device [n_hdiv]; w_dg, out_dg: device [n_dg], must not
- * overlap.  prec selects the contraction precision (DGC_FP64 or DGC_FP32; the
- * result is written in FP64). */
+ * overlap.  prec selects the contraction precision (see dgc_prec; the result is
+ * written in FP64). */
 dgc_status dgc_conv_apply(dgc_mesh* mesh, const double* wind_hdiv, const double* w_dg, double* out_dg,
                           dgc_prec prec, void* stream);
 
@@ -155,6 +163,11 @@ dgc_status dgc_project(dgc_mesh* mesh, const double* vals, double* w_dg, void* s
 /* max |u(x_q)| over the volume quadrature points (degree 3k-1 rule) of all
  * elements.  Synchronizes `stream`; result in *out (host). */
 dgc_status dgc_max_wind_speed(dgc_mesh* mesh, const double* wind_hdiv, double* out, void* stream);
+
+/* Device-side status of the handle: synchronizes `stream`, returns
+ * DGC_ERR_TIMEOUT (and clears the word) if a bounded wait inside a kernel gave
+ * up since the last check, DGC_OK otherwise. */
+dgc_status dgc_check(dgc_mesh* mesh, void* stream);
 
 /* Shortest element edge of the mesh (host value, from the upload). */
 dgc_status dgc_min_edge(const dgc_mesh* mesh, double* out);

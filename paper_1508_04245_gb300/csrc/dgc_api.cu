@@ -15,6 +15,7 @@
 #include "../../include/dgconv.h"
 #include "dgc_kernels.h"
 #include "dgc_stage.cuh"
+#include "dgc_stage_tc.cuh"
 
 using dgc::DevMesh;
 using dgc::Sizes;
@@ -89,7 +90,8 @@ struct dgc_mesh {
   DevBuf<double> Bv, wv, wf, Bf, Cb, Lg_int, Lg_fac, Tint, wd, wfd, Qfd, Bd;
   // stage-table blobs
   DevBuf<double> tab64;
-  DevBuf<float> tab32;
+  DevBuf<float> tab32, tcblob, wcoef;
+  DevBuf<int> status;
   // scratch
   DevBuf<double> Uw64, Fw64, stage1, stage2, zbuf;
   DevBuf<float> Uw32, Fw32;
@@ -138,6 +140,9 @@ struct dgc_mesh {
     for (auto* b : {&elems, &nbr, &facet_id, &facet_sides}) b->release();
     orient.release();
     tab32.release();
+    tcblob.release();
+    wcoef.release();
+    status.release();
     Uw32.release();
     Fw32.release();
     reduce.release();
@@ -206,31 +211,86 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
   return DGC_OK;
 }
 
-dgc_status check_prec(dgc_prec prec) {
+dgc_status check_prec(const dgc_mesh* m, dgc_prec prec) {
   if (prec == DGC_FP64 || prec == DGC_FP32) return DGC_OK;
+  if (prec == DGC_TF32X3) {
+    if (dgc::tc_supported(m->s.D, m->s.K)) return DGC_OK;
+    return fail(DGC_ERR_UNSUPPORTED, "DGC_TF32X3 is available for triangles with k <= 4 (dim %d, k %d)", m->s.D,
+                m->s.K);
+  }
   if (prec == DGC_BF16X3) return fail(DGC_ERR_UNSUPPORTED, "precision DGC_BF16X3 is not available in this build");
   return fail(DGC_ERR_ARG, "unknown precision %d", (int)prec);
 }
 
-// The launch sequence of dgc_rk_substeps (also what gets captured).
-dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, int nsteps, int scheme, bool fp32,
-                       cudaStream_t st) {
-  cudaError_t err = dgc::launch_wind_prep(m->view(), wind, fp32 ? (void*)m->Uw32.ptr : (void*)m->Uw64.ptr,
-                                          fp32 ? (void*)m->Fw32.ptr : (void*)m->Fw64.ptr, fp32, st);
+dgc_status ensure_tc_scratch(dgc_mesh* m) {
+  cudaError_t perr = dgc::launch_stage_tc(m->s.D, m->s.K, nullptr, nullptr);
+  if (perr != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage setup failed: %s", cudaGetErrorString(perr));
+  DGC_CUDA(m->wcoef.alloc((size_t)m->E * m->s.D * dgc::tc_nk(m->s.D, m->s.K)));
+  return DGC_OK;
+}
+
+dgc_status launch_stage_tc(dgc_mesh* m, const double* vin, const double* vn, double* vout, double alpha,
+                           double beta, double gamma, cudaStream_t st) {
+  dgc::StageTcArgs a;
+  a.vin = vin;
+  a.vn = vn;
+  a.vout = vout;
+  a.wcoef = m->wcoef.ptr;
+  a.nbr = m->nbr.ptr;
+  a.blob = m->tcblob.ptr;
+  a.status = m->status.ptr;
+  a.E = m->E;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.gamma = gamma;
+  cudaError_t err = dgc::launch_stage_tc(m->s.D, m->s.K, &a, st);
+  if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed: %s", cudaGetErrorString(err));
+  return DGC_OK;
+}
+
+// one stage vout = alpha vn + beta vin + gamma L(vin), any precision
+dgc_status stage(dgc_mesh* m, dgc_prec prec, const double* vin, const double* vn, double* vout, double alpha,
+                 double beta, double gamma, cudaStream_t st) {
+  if (prec == DGC_TF32X3) return launch_stage_tc(m, vin, vn, vout, alpha, beta, gamma, st);
+  return launch_stage(m, prec == DGC_FP32, vin, vn, vout, alpha, beta, gamma, st);
+}
+
+// frozen-wind data for the chosen precision
+dgc_status prepare_wind(dgc_mesh* m, dgc_prec prec, const double* wind, cudaStream_t st) {
+  cudaError_t err;
+  if (prec == DGC_TF32X3) {
+    err = dgc::launch_wind_coeffs(m->view(), wind, m->wcoef.ptr, dgc::tc_nk(m->s.D, m->s.K), st);
+  } else {
+    const bool fp32 = prec == DGC_FP32;
+    err = dgc::launch_wind_prep(m->view(), wind, fp32 ? (void*)m->Uw32.ptr : (void*)m->Uw64.ptr,
+                                fp32 ? (void*)m->Fw32.ptr : (void*)m->Fw64.ptr, fp32, st);
+  }
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "wind preparation failed: %s", cudaGetErrorString(err));
+  return DGC_OK;
+}
+
+dgc_status ensure_prec_scratch(dgc_mesh* m, dgc_prec prec) {
+  if (prec == DGC_TF32X3) return ensure_tc_scratch(m);
+  return ensure_wind_scratch(m, prec == DGC_FP32);
+}
+
+// The launch sequence of dgc_rk_substeps (also what gets captured).
+dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, int nsteps, int scheme, dgc_prec prec,
+                       cudaStream_t st) {
+  if (dgc_status rc = prepare_wind(m, prec, wind, st)) return rc;
   double* v1 = m->stage1.ptr;
   double* v2 = m->stage2.ptr;
   for (int n = 0; n < nsteps; ++n) {
     dgc_status rc;
     if (scheme == DGC_SSPRK2) {
       // v1 = v + ds L(v);  v = 1/2 v + 1/2 (v1 + ds L(v1))
-      if ((rc = launch_stage(m, fp32, v, nullptr, v1, 0.0, 1.0, ds, st))) return rc;
-      if ((rc = launch_stage(m, fp32, v1, v, v, 0.5, 0.5, 0.5 * ds, st))) return rc;
+      if ((rc = stage(m, prec, v, nullptr, v1, 0.0, 1.0, ds, st))) return rc;
+      if ((rc = stage(m, prec, v1, v, v, 0.5, 0.5, 0.5 * ds, st))) return rc;
     } else {
       // Shu-Osher SSP-RK3
-      if ((rc = launch_stage(m, fp32, v, nullptr, v1, 0.0, 1.0, ds, st))) return rc;
-      if ((rc = launch_stage(m, fp32, v1, v, v2, 0.75, 0.25, 0.25 * ds, st))) return rc;
-      if ((rc = launch_stage(m, fp32, v2, v, v, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * ds, st))) return rc;
+      if ((rc = stage(m, prec, v, nullptr, v1, 0.0, 1.0, ds, st))) return rc;
+      if ((rc = stage(m, prec, v1, v, v2, 0.75, 0.25, 0.25 * ds, st))) return rc;
+      if ((rc = stage(m, prec, v2, v, v, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * ds, st))) return rc;
     }
   }
   return DGC_OK;
@@ -323,7 +383,9 @@ dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int 
             up(m->Lg_int.upload(t.Lg_int)) && up(m->Lg_fac.upload(t.Lg_fac)) && up(m->Tint.upload(t.Tint)) &&
             up(m->wd.upload(t.wd)) && up(m->wfd.upload(t.wfd)) && up(m->Qfd.upload(t.Qfd)) &&
             up(m->Bd.upload(t.Bd)) && up(m->tab64.upload(stage_blob<double>(t))) &&
-            up(m->tab32.upload(stage_blob<float>(t)));
+            up(m->tab32.upload(stage_blob<float>(t))) && up(m->status.alloc(1)) &&
+            up(cudaMemset(m->status.ptr, 0, sizeof(int))) &&
+            (!dgc::tc_supported(dim, k) || up(m->tcblob.upload(dgc::tc_blob(dim, k, t))));
   if (!ok) {
     cudaError_t err = cudaGetLastError();
     m->release_all();
@@ -395,31 +457,28 @@ dgc_status dgc_mass_apply(dgc_mesh* mesh, const double* v_dg, double* out_dg, in
 dgc_status dgc_conv_apply(dgc_mesh* mesh, const double* wind_hdiv, const double* w_dg, double* out_dg,
                           dgc_prec prec, void* stream) {
   if (dgc_status rc = check_mesh(mesh)) return rc;
-  if (dgc_status rc = check_prec(prec)) return rc;
+  if (dgc_status rc = check_prec(mesh, prec)) return rc;
   if (!wind_hdiv || !w_dg || !out_dg) return fail(DGC_ERR_ARG, "NULL vector");
   const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
   if (out_dg < w_dg + n && w_dg < out_dg + n) return fail(DGC_ERR_ARG, "out_dg overlaps w_dg");
-  const bool fp32 = prec == DGC_FP32;
-  if (dgc_status rc = ensure_wind_scratch(mesh, fp32)) return rc;
+  if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
   cudaStream_t st = as_stream(stream);
-  DGC_CUDA(dgc::launch_wind_prep(mesh->view(), wind_hdiv, fp32 ? (void*)mesh->Uw32.ptr : (void*)mesh->Uw64.ptr,
-                                 fp32 ? (void*)mesh->Fw32.ptr : (void*)mesh->Fw64.ptr, fp32, st));
+  if (dgc_status rc = prepare_wind(mesh, prec, wind_hdiv, st)) return rc;
   // out = -L(w) = (M^V)^-1 C^V w
-  return launch_stage(mesh, fp32, w_dg, nullptr, out_dg, 0.0, 0.0, -1.0, st);
+  return stage(mesh, prec, w_dg, nullptr, out_dg, 0.0, 0.0, -1.0, st);
 }
 
 dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg, double ds, int nsteps,
                            dgc_scheme scheme, dgc_prec prec, void* stream) {
   if (dgc_status rc = check_mesh(mesh)) return rc;
-  if (dgc_status rc = check_prec(prec)) return rc;
+  if (dgc_status rc = check_prec(mesh, prec)) return rc;
   if (!wind_hdiv || !v_dg) return fail(DGC_ERR_ARG, "NULL vector");
   if (scheme != DGC_SSPRK2 && scheme != DGC_SSPRK3) return fail(DGC_ERR_ARG, "unknown scheme %d", (int)scheme);
   if (nsteps < 0) return fail(DGC_ERR_ARG, "nsteps must be >= 0 (got %d)", nsteps);
   if (!(ds > 0.0) || !std::isfinite(ds)) return fail(DGC_ERR_ARG, "ds must be positive and finite (got %g)", ds);
   if (nsteps == 0) return DGC_OK;
-  const bool fp32 = prec == DGC_FP32;
   const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
-  if (dgc_status rc = ensure_wind_scratch(mesh, fp32)) return rc;
+  if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
   DGC_CUDA(mesh->stage1.alloc(n));
   DGC_CUDA(mesh->stage2.alloc(n));
   cudaStream_t st = as_stream(stream);
@@ -429,7 +488,7 @@ dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg
     mesh->graph = nullptr;
     if (!mesh->capture_stream) DGC_CUDA(cudaStreamCreateWithFlags(&mesh->capture_stream, cudaStreamNonBlocking));
     DGC_CUDA(cudaStreamBeginCapture(mesh->capture_stream, cudaStreamCaptureModeThreadLocal));
-    dgc_status rc = rk_sequence(mesh, wind_hdiv, v_dg, ds, nsteps, (int)scheme, fp32, mesh->capture_stream);
+    dgc_status rc = rk_sequence(mesh, wind_hdiv, v_dg, ds, nsteps, (int)scheme, prec, mesh->capture_stream);
     cudaGraph_t g = nullptr;
     cudaError_t err = cudaStreamEndCapture(mesh->capture_stream, &g);
     if (rc != DGC_OK) {
@@ -555,6 +614,20 @@ dgc_status dgc_connectivity(int dim, int n_vert, int n_elem, const int32_t* elem
     if (orient) orient[j] = con.orient[j];
   }
   if (n_facets) *n_facets = con.n_facets;
+  return DGC_OK;
+}
+
+dgc_status dgc_check(dgc_mesh* mesh, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  cudaStream_t st = as_stream(stream);
+  int word = 0;
+  DGC_CUDA(cudaMemcpyAsync(&word, mesh->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DGC_CUDA(cudaStreamSynchronize(st));
+  if (word) {
+    DGC_CUDA(cudaMemsetAsync(mesh->status.ptr, 0, sizeof(int), st));
+    DGC_CUDA(cudaStreamSynchronize(st));
+    return fail(DGC_ERR_TIMEOUT, "a bounded device-side wait gave up (status word 0x%x)", word);
+  }
   return DGC_OK;
 }
 

@@ -99,6 +99,19 @@ __global__ void wind_prep_kernel(DevMesh m, const double* __restrict__ u, T* __r
     }
 }
 
+// wind on the vector Dubiner basis scaled by 1/det J, float, zero padded to nk
+__global__ void wind_coeffs_kernel(DevMesh m, const double* __restrict__ u, float* __restrict__ wc, int nk) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const Sizes& s = m.s;
+  double ut[MAXW], uc[MAXW];
+  gather_local(m, e, u, ut);
+  bdm_to_dubiner(m, ut, uc);
+  const double inv = 1.0 / m.detJ[e];
+  for (int a = 0; a < s.D; ++a)
+    for (int i = 0; i < nk; ++i) wc[((long)e * s.D + a) * nk + i] = i < s.N ? (float)(inv * uc[a * s.N + i]) : 0.f;
+}
+
 // w_{c,i} = (1/det J) sum_a J[c][a] uc[a][i]   (= (1/|det J|) int_T u_c psi_i)
 __global__ void transfer_kernel(DevMesh m, const double* __restrict__ u, double* __restrict__ w) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -371,6 +384,12 @@ cudaError_t launch_wind_prep(const DevMesh& m, const double* u, void* Uw, void* 
     wind_prep_kernel<float><<<grid_for(m.E), BLOCK, 0, s>>>(m, u, (float*)Uw, (float*)Fw);
   else
     wind_prep_kernel<double><<<grid_for(m.E), BLOCK, 0, s>>>(m, u, (double*)Uw, (double*)Fw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wind_coeffs(const DevMesh& m, const double* u, float* wc, int nk, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  wind_coeffs_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, u, wc, nk);
   return cudaGetLastError();
 }
 

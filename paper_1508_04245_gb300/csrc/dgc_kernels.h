@@ -3,11 +3,14 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "dgc_internal.h"
 
 namespace dgc {
 
 struct StageArgs;
+struct StageTcArgs;
 
 // Device view of a mesh and of its FP64 reference tables.
 struct DevMesh {
@@ -39,6 +42,14 @@ struct DevMesh {
 // a == nullptr prepares the kernel (shared-memory attribute) without launching
 cudaError_t launch_stage_2d(int K, bool fp32, const StageArgs* a, cudaStream_t s);
 cudaError_t launch_stage_3d(int K, bool fp32, const StageArgs* a, cudaStream_t s);
+
+// tensor-core stage kernel (triangles, k <= 4); a == nullptr prepares the kernel
+bool tc_supported(int D, int K);
+int tc_nk(int D, int K);
+std::vector<float> tc_blob(int D, int K, const Tables& t);
+cudaError_t launch_stage_tc(int D, int K, const StageTcArgs* a, cudaStream_t s);
+// wind on the Dubiner basis scaled by 1/det J, float [E][D][nk] (zero padded)
+cudaError_t launch_wind_coeffs(const DevMesh& m, const double* u_hdiv, float* wc, int nk, cudaStream_t s);
 
 cudaError_t launch_geometry(const DevMesh& m, cudaStream_t s);
 // frozen-wind data of the stage kernels: Uw [QV*D][E], Fw [NF*QF][E] in float or double

@@ -1,0 +1,107 @@
+// Tensor-core stage kernel: host table blob (operand layout, head/tail TF32
+// split of the FP64 reference tables) and launcher, triangles k = 1..4.
+#include <cstring>
+#include <vector>
+
+#include "dgc_kernels.h"
+#include "dgc_stage_tc.cuh"
+
+namespace dgc {
+namespace {
+
+// round to TF32, nearest with ties away from zero (as cvt.rna.tf32.f32)
+float tf32_rna(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0x1000u;
+  u &= 0xFFFFE000u;
+  std::memcpy(&x, &u, 4);
+  return x;
+}
+
+size_t koff(int row, int k, unsigned sbo) {   // float offset in a K-major operand (LBO 128 B)
+  return ((row & 7) * 16 + (row >> 3) * sbo + (k & 3) * 4 + (k >> 2) * 128) / 4;
+}
+
+// write value x of element (row, k) as head at base[], tail at base[size + ...]
+void put_split(std::vector<float>& b, size_t base, size_t size, int row, int k, unsigned sbo, double x) {
+  const float h = tf32_rna((float)x);
+  const float t = tf32_rna((float)(x - (double)h));
+  b[base + koff(row, k, sbo)] = h;
+  b[base + size + koff(row, k, sbo)] = t;
+}
+
+template <int K>
+std::vector<float> blob_t(const Tables& t) {
+  using L = TcLayout2D<K>;
+  const int N = L::N, QV = L::QV, QF = L::QF, NFM = L::NFM;
+  std::vector<float> b(L::BLOB, 0.f);
+  for (int n = 0; n < QV; ++n)
+    for (int k = 0; k < N; ++k) {
+      put_split(b, L::oTAs, L::szTAs, n, k, L::SBO_NK, t.Bv[n * N + k]);
+      put_split(b, L::oTAw, L::szTAw, n, k, L::SBO_NK, t.wv[n] * t.Bv[n * N + k]);
+    }
+  for (int f = 0; f < L::NF; ++f)
+    for (int q = 0; q < QF; ++q)
+      for (int k = 0; k < N; ++k)
+        put_split(b, L::oTAw, L::szTAw, QV + f * QF + q, k, L::SBO_NK, t.wf[q] * t.Bf[(f * QF + q) * N + k]);
+  for (int i = 0; i < N; ++i) {
+    for (int kk = 0; kk < L::NF * NFM; ++kk) put_split(b, L::oTB, L::szTB, i, kk, L::SBO_KB, t.Ef[kk * N + i]);
+    for (int q = 0; q < QV; ++q)
+      for (int dd = 0; dd < 2; ++dd)
+        put_split(b, L::oTB, L::szTB, i, L::KF + 2 * q + dd, L::SBO_KB, t.Gv[(q * N + i) * 2 + dd]);
+  }
+  for (size_t j = 0; j < t.Ef.size(); ++j) b[L::oEf + j] = (float)t.Ef[j];
+  for (size_t j = 0; j < t.Qt.size(); ++j) b[L::oQt + j] = (float)t.Qt[j];
+  return b;
+}
+
+template <int K>
+cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
+  using L = TcLayout2D<K>;
+  auto kern = stage_tc_kernel<K>;
+  if (!a) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_BYTES);
+  const int grid = (a->E + 127) / 128;
+  if (grid == 0) return cudaSuccess;
+  kern<<<grid, 128, L::SMEM_BYTES, s>>>(*a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_supported(int D, int K) { return D == 2 && K >= 1 && K <= 4; }
+
+int tc_nk(int D, int K) {
+  if (D != 2) return 0;
+  switch (K) {
+    case 1: return TcLayout2D<1>::NK;
+    case 2: return TcLayout2D<2>::NK;
+    case 3: return TcLayout2D<3>::NK;
+    case 4: return TcLayout2D<4>::NK;
+    default: return 0;
+  }
+}
+
+std::vector<float> tc_blob(int D, int K, const Tables& t) {
+  if (D != 2) return {};
+  switch (K) {
+    case 1: return blob_t<1>(t);
+    case 2: return blob_t<2>(t);
+    case 3: return blob_t<3>(t);
+    case 4: return blob_t<4>(t);
+    default: return {};
+  }
+}
+
+cudaError_t launch_stage_tc(int D, int K, const StageTcArgs* a, cudaStream_t s) {
+  if (D != 2) return cudaErrorInvalidValue;
+  switch (K) {
+    case 1: return launch_t<1>(a, s);
+    case 2: return launch_t<2>(a, s);
+    case 3: return launch_t<3>(a, s);
+    case 4: return launch_t<4>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dgc

@@ -15,9 +15,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdgconv.so")
 
-DGC_FP64, DGC_FP32, DGC_BF16X3 = 0, 1, 2
+DGC_FP64, DGC_FP32, DGC_BF16X3, DGC_TF32X3 = 0, 1, 2, 3
 DGC_SSPRK2, DGC_SSPRK3 = 2, 3
-PREC = {"fp64": DGC_FP64, "fp32": DGC_FP32, "bf16x3": DGC_BF16X3}
+PREC = {"fp64": DGC_FP64, "fp32": DGC_FP32, "bf16x3": DGC_BF16X3, "tf32x3": DGC_TF32X3}
 
 # symbol name -> (restype, argtypes); mirrors include/dgconv.h
 _vp, _dp, _i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
@@ -40,6 +40,7 @@ SIGNATURES = {
     "dgc_hdiv_interpolate": [_vp, _vp, _vp, _vp],
     "dgc_max_wind_speed": [_vp, _vp, _dp, _vp],
     "dgc_min_edge": [_vp, _dp],
+    "dgc_check": [_vp, _vp],
     "dgc_table": [ctypes.c_int, ctypes.c_int, ctypes.c_char_p, _vp, _i64p],
     "dgc_connectivity": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
                          ctypes.POINTER(ctypes.c_int32)],
@@ -200,6 +201,10 @@ class Mesh:
         v = ctypes.c_double()
         check(lib().dgc_max_wind_speed(self._h, _ptr(wind, self.n_hdiv, "wind"), ctypes.byref(v), _stream(stream)))
         return v.value
+
+    def check(self, stream=None):
+        """Raise if a bounded device-side wait gave up since the last check (synchronizes)."""
+        check(lib().dgc_check(self._h, _stream(stream)))
 
     def min_edge(self) -> float:
         v = ctypes.c_double()

@@ -8,7 +8,7 @@ Tolerances are max-norm relative errors (reading A17): 1e-12 for FP64,
 import numpy as np
 import pytest
 
-from gpu_common import TOL, make_case, maxrel, oracle_ds, oracle_state
+from gpu_common import TOL, make_case, maxrel, oracle_ds, oracle_state, tc_ok
 from oracle import dg as ODG
 from oracle import hdiv as OH
 from paper_1508_04245_gb300 import build, dgconv
@@ -73,19 +73,25 @@ def test_transfer_T(cases, dim, k):
     assert maxrel(host(gm.transfer_T(cu(f))), ODG.transfer_T(om, k, f)) < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 @pytest.mark.parametrize("dim,k", ORDERS)
 def test_conv_apply(cases, dim, k, prec):
+    if prec == "tf32x3" and not tc_ok(dim, k):
+        pytest.skip("tensor-core path covers triangles with k <= 4")
     verts, elems, pot, om, wind, gm = cases(dim, k)
     w = oracle_state(om, k)
     ref = ODG.ConvectionOracle(om, k, wind).apply(w)
     got = host(gm.conv_apply(cu(wind), cu(w), prec=prec))
     assert maxrel(got, ref) < TOL[prec]
+    gm.check()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("dim,k,scheme", [(2, 2, 2), (2, 4, 3), (2, 6, 3), (3, 1, 2), (3, 3, 3), (3, 4, 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("dim,k,scheme", [(2, 1, 3), (2, 2, 2), (2, 3, 3), (2, 4, 3), (2, 6, 3), (3, 1, 2), (3, 3, 3),
+                                          (3, 4, 3)])
 def test_rk_substeps(cases, dim, k, scheme, prec):
+    if prec == "tf32x3" and not tc_ok(dim, k):
+        pytest.skip("tensor-core path covers triangles with k <= 4")
     verts, elems, pot, om, wind, gm = cases(dim, k)
     v0 = oracle_state(om, k, seed=5)
     ds = oracle_ds(om, k, wind)
@@ -94,6 +100,7 @@ def test_rk_substeps(cases, dim, k, scheme, prec):
     v = cu(v0)
     gm.rk_substeps(cu(wind), v, ds, 4, scheme, prec)
     assert maxrel(host(v), ref) < TOL[prec]
+    gm.check()
 
 
 def test_rk_graph_replay_matches_fresh_launch(cases):
@@ -108,6 +115,15 @@ def test_rk_graph_replay_matches_fresh_launch(cases):
     a.copy_(cu(v0))
     gm.rk_substeps(wt, a, ds, 3, 3, "fp64")
     assert np.array_equal(host(a), first)
+
+
+def test_tc_unsupported_orders_are_rejected(cases):
+    verts, elems, pot, om, wind, gm = cases(3, 2)
+    w = cu(oracle_state(om, 2))
+    with pytest.raises(dgconv.DgcError):
+        gm.conv_apply(cu(wind), w, prec="tf32x3")
+    with pytest.raises(dgconv.DgcError):
+        gm.conv_apply(cu(wind), w, prec="bf16x3")
 
 
 def test_mass_and_geometry(cases):
