@@ -51,8 +51,10 @@ std::vector<float> blob_t(const Tables& t) {
       for (int dd = 0; dd < 2; ++dd)
         put_split(b, L::oTB, L::szTB, i, L::KF + 2 * q + dd, L::SBO_KB, t.Gv[(q * N + i) * 2 + dd]);
   }
-  for (size_t j = 0; j < t.Ef.size(); ++j) b[L::oEf + j] = (float)t.Ef[j];
-  for (size_t j = 0; j < t.Qt.size(); ++j) b[L::oQt + j] = (float)t.Qt[j];
+  for (int fm = 0; fm < L::NF * NFM; ++fm)
+    for (int i = 0; i < N; ++i) b[L::oEf + fm * L::NP4 + i] = (float)t.Ef[fm * N + i];
+  for (int q = 0; q < QF; ++q)
+    for (int m = 0; m < NFM; ++m) b[L::oQt + q * L::NFM4 + m] = (float)t.Qt[q * NFM + m];
   return b;
 }
 
@@ -61,8 +63,17 @@ cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
   using L = TcLayout2D<K>;
   auto kern = stage_tc_kernel<K>;
   if (!a) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_BYTES);
-  const int grid = (a->E + 127) / 128;
-  if (grid == 0) return cudaSuccess;
+  const int tiles = (a->E + 127) / 128;
+  if (tiles == 0) return cudaSuccess;
+  // persistent: two resident CTAs per SM (shared memory and TMEM allow two)
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int grid = tiles < 2 * sms ? tiles : 2 * sms;
   kern<<<grid, 128, L::SMEM_BYTES, s>>>(*a);
   return cudaGetLastError();
 }

@@ -51,7 +51,9 @@ struct TcLayout2D {
 
   // table blob (floats), sections in operand layout, each a multiple of 4 floats
   static constexpr int szTAs = NAS * NK, szTAw = NAW * NK, szTB = NB * KB;
-  static constexpr int szEf = pad(NF * NFM * N, 4), szQt = pad(QF * NFM, 4);
+  static constexpr int NP4 = pad(N, 4);                // Ef rows padded for 16-byte loads
+  static constexpr int NFM4 = pad(NFM, 4);             // Qt rows padded for 16-byte loads
+  static constexpr int szEf = NF * NFM * NP4, szQt = QF * NFM4;
   static constexpr int oTAs = 0;                       // head, tail
   static constexpr int oTAw = oTAs + 2 * szTAs;
   static constexpr int oTB = oTAw + 2 * szTAw;
