@@ -90,7 +90,8 @@ struct dgc_mesh {
   DevBuf<double> Bv, wv, wf, Bf, Cb, Lg_int, Lg_fac, Tint, wd, wfd, Qfd, Bd;
   // stage-table blobs
   DevBuf<double> tab64;
-  DevBuf<float> tab32, tcblob, wcoef;
+  DevBuf<float> tab32, tcblob, wcoef, trA, trB;
+  DevBuf<double> ts0, ts1, ts2;   // tile-blocked state vectors of the tensor-core path
   DevBuf<int> status;
   // scratch
   DevBuf<double> Uw64, Fw64, stage1, stage2, zbuf;
@@ -142,6 +143,11 @@ struct dgc_mesh {
     tab32.release();
     tcblob.release();
     wcoef.release();
+    trA.release();
+    trB.release();
+    ts0.release();
+    ts1.release();
+    ts2.release();
     status.release();
     Uw32.release();
     Fw32.release();
@@ -226,15 +232,23 @@ dgc_status ensure_tc_scratch(dgc_mesh* m) {
   cudaError_t perr = dgc::launch_stage_tc(m->s.D, m->s.K, nullptr, nullptr);
   if (perr != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage setup failed: %s", cudaGetErrorString(perr));
   DGC_CUDA(m->wcoef.alloc((size_t)m->E * m->s.D * dgc::tc_nk(m->s.D, m->s.K)));
+  const size_t nt = dgc::tc_tsoa_len(m->s.D, m->s.K, m->E), nr = dgc::tc_tr_len(m->s.D, m->s.K, m->E);
+  DGC_CUDA(m->ts0.alloc(nt));
+  DGC_CUDA(m->ts1.alloc(nt));
+  DGC_CUDA(m->ts2.alloc(nt));
+  DGC_CUDA(m->trA.alloc(nr));
+  DGC_CUDA(m->trB.alloc(nr));
   return DGC_OK;
 }
 
-dgc_status launch_stage_tc(dgc_mesh* m, const double* vin, const double* vn, double* vout, double alpha,
-                           double beta, double gamma, cudaStream_t st) {
+dgc_status launch_stage_tc(dgc_mesh* m, const double* vin, const float* trin, const double* vn, double* vout,
+                           float* trout, double alpha, double beta, double gamma, cudaStream_t st) {
   dgc::StageTcArgs a;
   a.vin = vin;
   a.vn = vn;
   a.vout = vout;
+  a.trin = trin;
+  a.trout = trout;
   a.wcoef = m->wcoef.ptr;
   a.nbr = m->nbr.ptr;
   a.blob = m->tcblob.ptr;
@@ -248,10 +262,42 @@ dgc_status launch_stage_tc(dgc_mesh* m, const double* vin, const double* vn, dou
   return DGC_OK;
 }
 
+dgc_status tc_transpose_in(dgc_mesh* m, const double* v, double* vt, float* tr, cudaStream_t st) {
+  cudaError_t err = dgc::launch_tsoa_in(m->s.D, m->s.K, v, vt, tr, m->tcblob.ptr, m->E, st);
+  if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "layout transpose failed: %s", cudaGetErrorString(err));
+  return DGC_OK;
+}
+
+dgc_status tc_transpose_out(dgc_mesh* m, const double* vt, double* v, cudaStream_t st) {
+  cudaError_t err = dgc::launch_tsoa_out(m->s.D, m->s.K, vt, v, m->E, st);
+  if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "layout transpose failed: %s", cudaGetErrorString(err));
+  return DGC_OK;
+}
+
+// SSP-RK substeps on the tensor-core path: ABI -> TSOA once, stages ping-pong the
+// trace buffers, TSOA -> ABI at the end
+dgc_status rk_sequence_tc(dgc_mesh* m, double* v, double ds, int nsteps, int scheme, cudaStream_t st) {
+  double *T0 = m->ts0.ptr, *T1 = m->ts1.ptr, *T2 = m->ts2.ptr;
+  float *cur = m->trA.ptr, *oth = m->trB.ptr;
+  if (dgc_status rc = tc_transpose_in(m, v, T0, cur, st)) return rc;
+  for (int n = 0; n < nsteps; ++n) {
+    dgc_status rc;
+    if (scheme == DGC_SSPRK2) {
+      if ((rc = launch_stage_tc(m, T0, cur, nullptr, T1, oth, 0.0, 1.0, ds, st))) return rc;
+      if ((rc = launch_stage_tc(m, T1, oth, T0, T0, cur, 0.5, 0.5, 0.5 * ds, st))) return rc;
+    } else {
+      if ((rc = launch_stage_tc(m, T0, cur, nullptr, T1, oth, 0.0, 1.0, ds, st))) return rc;
+      if ((rc = launch_stage_tc(m, T1, oth, T0, T2, cur, 0.75, 0.25, 0.25 * ds, st))) return rc;
+      if ((rc = launch_stage_tc(m, T2, cur, T0, T0, oth, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * ds, st))) return rc;
+      std::swap(cur, oth);
+    }
+  }
+  return tc_transpose_out(m, T0, v, st);
+}
+
 // one stage vout = alpha vn + beta vin + gamma L(vin), any precision
 dgc_status stage(dgc_mesh* m, dgc_prec prec, const double* vin, const double* vn, double* vout, double alpha,
                  double beta, double gamma, cudaStream_t st) {
-  if (prec == DGC_TF32X3) return launch_stage_tc(m, vin, vn, vout, alpha, beta, gamma, st);
   return launch_stage(m, prec == DGC_FP32, vin, vn, vout, alpha, beta, gamma, st);
 }
 
@@ -278,6 +324,7 @@ dgc_status ensure_prec_scratch(dgc_mesh* m, dgc_prec prec) {
 dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, int nsteps, int scheme, dgc_prec prec,
                        cudaStream_t st) {
   if (dgc_status rc = prepare_wind(m, prec, wind, st)) return rc;
+  if (prec == DGC_TF32X3) return rk_sequence_tc(m, v, ds, nsteps, scheme, st);
   double* v1 = m->stage1.ptr;
   double* v2 = m->stage2.ptr;
   for (int n = 0; n < nsteps; ++n) {
@@ -465,6 +512,13 @@ dgc_status dgc_conv_apply(dgc_mesh* mesh, const double* wind_hdiv, const double*
   cudaStream_t st = as_stream(stream);
   if (dgc_status rc = prepare_wind(mesh, prec, wind_hdiv, st)) return rc;
   // out = -L(w) = (M^V)^-1 C^V w
+  if (prec == DGC_TF32X3) {
+    if (dgc_status rc = tc_transpose_in(mesh, w_dg, mesh->ts0.ptr, mesh->trA.ptr, st)) return rc;
+    if (dgc_status rc = launch_stage_tc(mesh, mesh->ts0.ptr, mesh->trA.ptr, nullptr, mesh->ts1.ptr, mesh->trB.ptr,
+                                        0.0, 0.0, -1.0, st))
+      return rc;
+    return tc_transpose_out(mesh, mesh->ts1.ptr, out_dg, st);
+  }
   return stage(mesh, prec, w_dg, nullptr, out_dg, 0.0, 0.0, -1.0, st);
 }
 

@@ -74,11 +74,59 @@ cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
     if (sms <= 0) sms = 1;
   }
   const int grid = tiles < 2 * sms ? tiles : 2 * sms;
-  kern<<<grid, 128, L::SMEM_BYTES, s>>>(*a);
+  kern<<<grid, 256, L::SMEM_BYTES, s>>>(*a);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t tsoa_in_t(const double* v, double* vt, float* tr, const float* blob, int E, cudaStream_t s) {
+  const long n = 2L * E;
+  if (n == 0) return cudaSuccess;
+  tsoa_in_kernel<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, vt, tr, blob, E);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t tsoa_out_t(const double* vt, double* v, int E, cudaStream_t s) {
+  const long n = 2L * E * TcLayout2D<K>::N;
+  if (n == 0) return cudaSuccess;
+  tsoa_out_kernel<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(vt, v, E);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+size_t tc_tsoa_len(int D, int K, int E) {
+  const size_t tiles = ((size_t)E + 127) / 128;
+  return tiles * 128 * D * ((size_t)(K + 1) * (K + 2) / 2);
+}
+size_t tc_tr_len(int D, int K, int E) {
+  const size_t tiles = ((size_t)E + 127) / 128;
+  return tiles * 128 * D * (D + 1) * (size_t)(K + 1);
+}
+
+cudaError_t launch_tsoa_in(int D, int K, const double* v, double* vt, float* tr, const float* blob, int E,
+                           cudaStream_t s) {
+  if (D != 2) return cudaErrorInvalidValue;
+  switch (K) {
+    case 1: return tsoa_in_t<1>(v, vt, tr, blob, E, s);
+    case 2: return tsoa_in_t<2>(v, vt, tr, blob, E, s);
+    case 3: return tsoa_in_t<3>(v, vt, tr, blob, E, s);
+    case 4: return tsoa_in_t<4>(v, vt, tr, blob, E, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_tsoa_out(int D, int K, const double* vt, double* v, int E, cudaStream_t s) {
+  if (D != 2) return cudaErrorInvalidValue;
+  switch (K) {
+    case 1: return tsoa_out_t<1>(vt, v, E, s);
+    case 2: return tsoa_out_t<2>(vt, v, E, s);
+    case 3: return tsoa_out_t<3>(vt, v, E, s);
+    case 4: return tsoa_out_t<4>(vt, v, E, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 bool tc_supported(int D, int K) { return D == 2 && K >= 1 && K <= 4; }
 

@@ -2,8 +2,8 @@
 // contractions of the upwind DG operator on tcgen05 (kind::tf32, three-pass
 // head/tail split, FP32 accumulation in TMEM) and the FP64 stage combination.
 //
-// Per tile of 128 elements (one CTA, 128 threads, thread t = element t =
-// GEMM row t = TMEM lane t):
+// Per tile of 128 elements (one CTA, 256 threads: thread (r, c) handles
+// velocity component c of element r; element r = GEMM row r = TMEM lane r):
 //   1. bulk copies (TMA) bring the table blob and the tile's wind
 //      coefficients into shared memory; every thread loads its element's FP64
 //      state and writes the head/tail TF32 operands of the state fields;
@@ -19,9 +19,11 @@
 //      thread issues the MMAs as chunks fill;
 //   5. epilogue: r from TMEM, vout = alpha vn + beta vin - gamma r in FP64.
 // The kernel is persistent (two CTAs per SM loop over tiles): the tables are
-// loaded once per CTA, the next tile's wind block is bulk-copied as soon as
-// the staging buffer is free, and the next tile's FP64 state blocks are
-// prefetched into L2.  Every mbarrier wait is bounded; a timeout sets bit 1
+// loaded once per CTA and the next tile's wind block is bulk-copied as soon as
+// the staging buffer is free.  State vectors use a tile-blocked SoA layout
+// (TSOA) so every warp access is coalesced, and each stage writes the facet
+// traces of its output (TR) for the next stage, which reads its own and its
+// neighbours' traces instead of recomputing them from FP64 coefficients.  Every mbarrier wait is bounded; a timeout sets bit 1
 // of the status word and the CTA stops (TMEM is still released).
 #pragma once
 
@@ -32,10 +34,22 @@
 
 namespace dgc {
 
+// Internal layouts of the tensor-core path (tile = 128 consecutive elements,
+// r = element % 128): state "TSOA" [tile][c][i][128] FP64 and facet traces
+// "TR" [tile][c][f][m][128] FP32, so a warp touches 32 consecutive elements.
+__host__ __device__ __forceinline__ size_t tsoa_index(int e, int c, int i, int N) {
+  return ((size_t)(e >> 7) * 2 * N + (size_t)c * N + i) * 128 + (e & 127);
+}
+__host__ __device__ __forceinline__ size_t tr_index(int e, int c, int f, int m, int NFM) {
+  return ((size_t)(e >> 7) * 2 * 3 * NFM + ((size_t)c * 3 + f) * NFM + m) * 128 + (e & 127);
+}
+
 struct StageTcArgs {
-  const double* vin;    // [E][2][N]
-  const double* vn;     // substep start state or null (alpha == 0); may equal vout
-  double* vout;
+  const double* vin;    // TSOA stage input
+  const double* vn;     // TSOA substep start state or null (alpha == 0); may equal vout
+  double* vout;         // TSOA stage output
+  const float* trin;    // TR traces of vin on the facet bases
+  float* trout;         // TR traces of vout
   const float* wcoef;   // [E][2][NK] wind on the Dubiner basis, scaled by 1/det J
   const int* nbr;       // [E][3]
   const float* blob;    // TcLayout2D<K> table blob
@@ -66,8 +80,26 @@ __device__ __forceinline__ void tmem_load(uint32_t taddr, float* v) {
 
 }  // namespace tcimpl
 
+// own facet traces of one component on the facet bases: tr[f][m] = sum_i Ef[f][m][i] x[i]
+template <int N, int NF, int NFM, int NP4>
+__device__ __forceinline__ void facet_traces(const float* Ef, const float* x, float (*tr)[NFM]) {
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int m = 0; m < NFM; ++m) {
+      float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+      for (int i4 = 0; i4 < NP4 / 4; ++i4) {
+        const float4 y = *reinterpret_cast<const float4*>(Ef + (f * NFM + m) * NP4 + 4 * i4);
+        a0 += y.x * x[4 * i4] + y.y * x[4 * i4 + 1];
+        a1 += y.z * x[4 * i4 + 2] + y.w * x[4 * i4 + 3];
+      }
+      tr[f][m] = a0 + a1;
+    }
+}
+
 template <int K>
-__global__ void __launch_bounds__(128, 1) stage_tc_kernel(StageTcArgs a) {
+__global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
   using L = TcLayout2D<K>;
   constexpr int N = L::N, QV = L::QV, QF = L::QF, NFM = L::NFM, NF = L::NF, NK = L::NK;
   constexpr int NP4 = L::NP4, NFM4 = L::NFM4;
@@ -85,19 +117,15 @@ __global__ void __launch_bounds__(128, 1) stage_tc_kernel(StageTcArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4 + 2 * L::NSLOT);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
+  // thread = (element row r of the tile, velocity component c); warps 0-3 and
+  // 4-7 read the same TMEM lanes (a warp sees lanes 32 (warp % 4) .. + 31)
   const int t = threadIdx.x;
   const int warp = t >> 5;
+  const int r = t & 127;
+  const int c = t >> 7;
   const int ntiles = (a.E + 127) / 128;
-  const bool vin_al = (reinterpret_cast<uintptr_t>(a.vin) & 15) == 0;
-  const bool vn_al = a.vn && (reinterpret_cast<uintptr_t>(a.vn) & 15) == 0;
-  auto tile_valid = [&](int tile) { return min(128, a.E - tile * 128); };
-  auto prefetch_state = [&](int tile) {   // next tile's FP64 state blocks into L2
-    const uint32_t bytes = (uint32_t)tile_valid(tile) * 2 * N * 8;
-    if (vin_al) tc::bulk_prefetch_l2(a.vin + (size_t)tile * 128 * 2 * N, bytes);
-    if (vn_al) tc::bulk_prefetch_l2(a.vn + (size_t)tile * 128 * 2 * N, bytes);
-  };
-  auto load_wind = [&](int tile) {        // tile's wind coefficients into the staging buffer
-    const uint32_t bytes = (uint32_t)tile_valid(tile) * 2 * NK * 4;
+  auto load_wind = [&](int tile) {        // a tile's wind coefficients into the staging buffer
+    const uint32_t bytes = (uint32_t)min(128, a.E - tile * 128) * 2 * NK * 4;
     tc::mbar_arrive_expect_tx(bar_w, bytes);
     tc::bulk_g2s(wst, a.wcoef + (size_t)tile * 128 * 2 * NK, bytes, bar_w);
   };
@@ -108,7 +136,7 @@ __global__ void __launch_bounds__(128, 1) stage_tc_kernel(StageTcArgs a) {
     tc::mbar_init(bar_A, 1);
     tc::mbar_init(bar_B, 1);
     for (int s = 0; s < L::NSLOT; ++s) {
-      tc::mbar_init(full + s, 128);
+      tc::mbar_init(full + s, 256);
       tc::mbar_init(empty + s, 1);
     }
     *abort_flag = 0;
@@ -119,7 +147,6 @@ __global__ void __launch_bounds__(128, 1) stage_tc_kernel(StageTcArgs a) {
     tc::mbar_arrive_expect_tx(bar_tab, L::BLOB * 4);
     tc::bulk_g2s(blob, a.blob, L::BLOB * 4, bar_tab);
     load_wind(blockIdx.x);
-    prefetch_state(blockIdx.x);
   }
   if (warp == 0) {
     tc::tmem_alloc(tslot, L::TMEM_COLS);
@@ -129,62 +156,89 @@ __global__ void __launch_bounds__(128, 1) stage_tc_kernel(StageTcArgs a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
-  const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+  const uint32_t lane_base = tbase + ((uint32_t)((warp & 3) * 32) << 16);
   if (!tc::mbar_wait(bar_tab, 0)) *abort_flag = 1;
   const float* Ef = blob + L::oEf;   // [NF][NFM][NP4]
   const float* Qt = blob + L::oQt;   // [QF][NFM4]
   const uint32_t op_s = tc::smem_u32(op);
   const uint32_t bl_s = tc::smem_u32(blob);
   const uint32_t tb_s = tc::smem_u32(blob + L::oTB);
+  const uint32_t idescB = tc::idesc_tf32(128, L::NB);
   uint32_t chunk_ctr = 0;
+
+  // thread 0: wait until chunk g's slot is full, issue its MMAs, release the slot
+  auto issue_chunk = [&](uint32_t g, int j) {
+    const int s = (int)(g % L::NSLOT);
+    if (!tc::mbar_wait(full + s, (g / L::NSLOT) & 1)) {
+      *abort_flag = 1;
+      return;
+    }
+    tc::fence_after_sync();
+    const uint32_t sl = op_s + 4u * (s * 2 * 2 * L::szChunk);
+    for (int cc = 0; cc < 2; ++cc)
+      for (int pass = 0; pass < 3; ++pass) {
+        const uint32_t a_op = sl + 4u * ((cc * 2 + (pass == 2 ? 1 : 0)) * L::szChunk);
+        const uint32_t b_op = tb_s + (pass == 1 ? 4u * L::szTB : 0u) + j * 2 * L::LBO;
+        tc::mma_tf32(tbase + L::cB + cc * L::NB, tc::smem_desc(a_op, L::LBO, L::SBO_CH),
+                     tc::smem_desc(b_op, L::LBO, L::SBO_KB), idescB, (j > 0 || pass > 0) ? 1u : 0u);
+      }
+    tc::mma_commit(empty + s);
+    if (j == L::NCH - 1) tc::mma_commit(bar_B);
+  };
+  // every thread: wait until chunk g's slot is free again
+  auto claim_chunk = [&](uint32_t g) -> float* {
+    const int s = (int)(g % L::NSLOT);
+    const uint32_t use = g / L::NSLOT;
+    if (use > 0 && *abort_flag == 0 && !tc::mbar_wait(empty + s, (use - 1) & 1)) *abort_flag = 1;
+    return op + s * (2 * 2 * L::szChunk) + c * 2 * L::szChunk;
+  };
+  // head / tail of 4 consecutive K values of this thread's row into a chunk operand
+  auto store4 = [&](float* slot, int k4, float v0, float v1, float v2, float v3) {
+    float h[4], tl[4];
+    tcimpl::split(v0, h[0], tl[0]);
+    tcimpl::split(v1, h[1], tl[1]);
+    tcimpl::split(v2, h[2], tl[2]);
+    tcimpl::split(v3, h[3], tl[3]);
+    const uint32_t o = tc::kmajor_off32(r, k4, L::LBO, L::SBO_CH) / 4;
+    tc::st_shared_v4(slot + o, h[0], h[1], h[2], h[3]);
+    tc::st_shared_v4(slot + L::szChunk + o, tl[0], tl[1], tl[2], tl[3]);
+  };
 
   int it = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int e = tile * 128 + t;
+    const int e = tile * 128 + r;
     const bool valid = e < a.E;
     const int next = tile + gridDim.x;
-    if (t == 0 && next < ntiles) prefetch_state(next);
 
-    // ---- own FP64 state -> registers, state operands (head / tail) ---------------
-    float w[2][NP4];
-    {
-      const double* vin_e = a.vin + (size_t)e * 2 * N;
+    // ---- own state (coalesced TSOA loads) -> state operand of component c ----------
+    float w[NP4];
 #pragma unroll
-      for (int c = 0; c < 2; ++c)
+    for (int i = 0; i < NP4; ++i)
+      w[i] = (valid && i < N) ? tc::f64_to_f32_rn(a.vin[tsoa_index(e, c, i < N ? i : 0, N)]) : 0.f;
 #pragma unroll
-        for (int i = 0; i < NP4; ++i) w[c][i] = (valid && i < N) ? (float)vin_e[c * N + i] : 0.f;
+    for (int k4 = 0; k4 < NK; k4 += 4) {
+      float h[4], tl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) tcimpl::split(k4 + u < NP4 ? w[k4 + u < NP4 ? k4 + u : 0] : 0.f, h[u], tl[u]);
+      const uint32_t o = tc::kmajor_off32(r, k4, L::LBO, L::SBO_NK) / 4;
+      tc::st_shared_v4(op + (c * 2 + 0) * L::szOpA + o, h[0], h[1], h[2], h[3]);
+      tc::st_shared_v4(op + (c * 2 + 1) * L::szOpA + o, tl[0], tl[1], tl[2], tl[3]);
     }
-    // op layout: field f (0,1 state; 2,3 wind) x part (0 head, 1 tail) x [128 x NK]
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-      for (int k4 = 0; k4 < NK; k4 += 4) {
-        float h[4], tl[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float x = (k4 + u < NP4) ? w[c][(k4 + u < NP4) ? k4 + u : 0] : 0.f;
-          tcimpl::split(x, h[u], tl[u]);
-        }
-        const uint32_t o = tc::kmajor_off32(t, k4, L::LBO, L::SBO_NK) / 4;
-        tc::st_shared_v4(op + (c * 2 + 0) * L::szOpA + o, h[0], h[1], h[2], h[3]);
-        tc::st_shared_v4(op + (c * 2 + 1) * L::szOpA + o, tl[0], tl[1], tl[2], tl[3]);
-      }
-    // ---- wind operands from the staged coefficients --------------------------------
+    // ---- wind operand of dimension d = c from the staged coefficients --------------
     if (*abort_flag == 0 && !tc::mbar_wait(bar_w, it & 1)) *abort_flag = 1;
 #pragma unroll
-    for (int d = 0; d < 2; ++d)
-#pragma unroll
-      for (int k4 = 0; k4 < NK; k4 += 4) {
-        float h[4], tl[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float x = valid ? wst[(t * 2 + d) * NK + k4 + u] : 0.f;
-          tcimpl::split(x, h[u], tl[u]);
-        }
-        const uint32_t o = tc::kmajor_off32(t, k4, L::LBO, L::SBO_NK) / 4;
-        tc::st_shared_v4(op + ((2 + d) * 2 + 0) * L::szOpA + o, h[0], h[1], h[2], h[3]);
-        tc::st_shared_v4(op + ((2 + d) * 2 + 1) * L::szOpA + o, tl[0], tl[1], tl[2], tl[3]);
-      }
+    for (int k4 = 0; k4 < NK; k4 += 4) {
+      const float4 x = valid ? *reinterpret_cast<const float4*>(wst + (r * 2 + c) * NK + k4)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+      float h[4], tl[4];
+      tcimpl::split(x.x, h[0], tl[0]);
+      tcimpl::split(x.y, h[1], tl[1]);
+      tcimpl::split(x.z, h[2], tl[2]);
+      tcimpl::split(x.w, h[3], tl[3]);
+      const uint32_t o = tc::kmajor_off32(r, k4, L::LBO, L::SBO_NK) / 4;
+      tc::st_shared_v4(op + ((2 + c) * 2 + 0) * L::szOpA + o, h[0], h[1], h[2], h[3]);
+      tc::st_shared_v4(op + ((2 + c) * 2 + 1) * L::szOpA + o, tl[0], tl[1], tl[2], tl[3]);
+    }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -204,82 +258,61 @@ __global__ void __launch_bounds__(128, 1) stage_tc_kernel(StageTcArgs a) {
           const uint32_t a_op = op_s + 4u * ((f * 2 + (pass == 2 ? 1 : 0)) * L::szOpA);
           const uint32_t b_op = tab + (pass == 1 ? tsz : 0u);
           for (int ks = 0; ks < NK / 8; ++ks) {
-            const uint64_t ad = tc::smem_desc(a_op + ks * 2 * L::LBO, L::LBO, L::SBO_NK);
-            const uint64_t bd = tc::smem_desc(b_op + ks * 2 * L::LBO, L::LBO, L::SBO_NK);
-            tc::mma_tf32(tbase + dcol, ad, bd, idesc, acc);
+            tc::mma_tf32(tbase + dcol, tc::smem_desc(a_op + ks * 2 * L::LBO, L::LBO, L::SBO_NK),
+                         tc::smem_desc(b_op + ks * 2 * L::LBO, L::LBO, L::SBO_NK), idesc, acc);
             acc = 1;
           }
         }
       }
       tc::mma_commit(bar_A);
     }
-
-    // ---- facet traces on the facet basis (CUDA cores) -----------------------------
-    float town[2][NF][NFM], tnb[2][NF][NFM];
+    __syncwarp();
+    // ---- own and neighbour facet traces from the trace buffer (while GEMM A runs) ---
+    float to[NF][NFM], tn[NF][NFM];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const int code = valid ? a.nbr[(size_t)e * NF + f] : -1;
-      float wn[2][NP4];
-      if (code >= 0) {
-        const double* src = a.vin + (size_t)(code >> 2) * 2 * N;
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-          for (int i = 0; i < NP4; ++i) wn[c][i] = i < N ? (float)src[c * N + (i < N ? i : 0)] : 0.f;
-      } else {
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-          for (int i = 0; i < NP4; ++i) wn[c][i] = 0.f;
-      }
-      const int fn = code >= 0 ? (code & 3) : 0;
+      const int ne = code >> 2, fn = code & 3;
 #pragma unroll
       for (int m = 0; m < NFM; ++m) {
-        const float4* eo = reinterpret_cast<const float4*>(Ef + (f * NFM + m) * NP4);
-        const float4* en = reinterpret_cast<const float4*>(Ef + (fn * NFM + m) * NP4);
-        float ao[2] = {0.f, 0.f}, an[2] = {0.f, 0.f};
-#pragma unroll
-        for (int i4 = 0; i4 < NP4 / 4; ++i4) {
-          const float4 x = eo[i4], y = en[i4];
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            ao[c] += x.x * w[c][4 * i4] + x.y * w[c][4 * i4 + 1] + x.z * w[c][4 * i4 + 2] + x.w * w[c][4 * i4 + 3];
-            an[c] += y.x * wn[c][4 * i4] + y.y * wn[c][4 * i4 + 1] + y.z * wn[c][4 * i4 + 2] +
-                     y.w * wn[c][4 * i4 + 3];
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          town[c][f][m] = ao[c];
-          tnb[c][f][m] = an[c];
-        }
+        to[f][m] = valid ? a.trin[tr_index(e, c, f, m, NFM)] : 0.f;
+        tn[f][m] = code >= 0 ? a.trin[tr_index(ne, c, fn, m, NFM)] : 0.f;
       }
     }
-
-    // ---- wait for GEMM A -------------------------------------------------------------
     if (run && *abort_flag == 0 && !tc::mbar_wait(bar_A, it & 1)) *abort_flag = 1;
     tc::fence_after_sync();
     __syncthreads();
     const bool run2 = *abort_flag == 0;
 
-    // ---- upwind facet fluxes projected on the facet basis ---------------------------
-    float phi[2][NF * NFM];
-#pragma unroll
-    for (int j = 0; j < NF * NFM; ++j) phi[0][j] = phi[1][j] = 0.f;
+    // ---- facets: upwind flux at the facet points, projection (chunks 0 .. NCHF-1) ---
     if (run2) {
-      constexpr int NFP = NF * QF;                   // facet points
-      constexpr int c0 = QV / 8 * 8, skip = QV - c0;
-      constexpr int NL = (skip + NFP + 7) / 8 * 8;
-      float uf[2][NL];
+      float* fslot[L::NCHF];
 #pragma unroll
-      for (int d = 0; d < 2; ++d) tcimpl::tmem_load<NL>(lane_base + L::cW + d * L::NAW + c0, uf[d]);
+      for (int j = 0; j < L::NCHF; ++j) fslot[j] = claim_chunk(chunk_ctr + j);
+      float phi[L::KF];
 #pragma unroll
-      for (int f = 0; f < NF; ++f)
+      for (int j = 0; j < L::KF; ++j) phi[j] = 0.f;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        // wind at this facet's points: (1/det J) w_q u^_dd, columns QV + f QF + q
+        float u0[QF], u1[QF];
 #pragma unroll
         for (int q = 0; q < QF; ++q) {
-          // (1/det J) w_q (u^ . -grad lambda_f): -grad lambda_0 = (1,1), _1 = (-1,0), _2 = (0,-1)
-          const float u0 = uf[0][skip + f * QF + q], u1 = uf[1][skip + f * QF + q];
-          const float fw = f == 0 ? u0 + u1 : (f == 1 ? -u0 : -u1);
+          uint32_t x0, x1;
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                       : "=r"(x0)
+                       : "r"(lane_base + L::cW + QV + f * QF + q));
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                       : "=r"(x1)
+                       : "r"(lane_base + L::cW + L::NAW + QV + f * QF + q));
+          u0[q] = __uint_as_float(x0);
+          u1[q] = __uint_as_float(x1);
+        }
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < QF; ++q) {
+          // -grad lambda_0 = (1,1), -grad lambda_1 = (-1,0), -grad lambda_2 = (0,-1)
+          const float fw = f == 0 ? u0[q] + u1[q] : (f == 1 ? -u0[q] : -u1[q]);
           float qq[NFM4];
 #pragma unroll
           for (int m4 = 0; m4 < NFM4; m4 += 4) {
@@ -289,124 +322,103 @@ __global__ void __launch_bounds__(128, 1) stage_tc_kernel(StageTcArgs a) {
             qq[m4 + 2] = x.z;
             qq[m4 + 3] = x.w;
           }
+          float o = 0.f, nb = 0.f;
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            float o = 0.f, nb = 0.f;
-#pragma unroll
-            for (int m = 0; m < NFM; ++m) {
-              o += qq[m] * town[c][f][m];
-              nb += qq[m] * tnb[c][f][m];
-            }
-            const float val = fw * (fw >= 0.f ? o : nb);
-#pragma unroll
-            for (int m = 0; m < NFM; ++m) phi[c][f * NFM + m] += qq[m] * val;
+          for (int m = 0; m < NFM; ++m) {
+            o += qq[m] * to[f][m];
+            nb += qq[m] * tn[f][m];
           }
-        }
-    }
-
-    // ---- GEMM B: produce K-chunks into the slot ring, thread 0 issues ----------------
-    const uint32_t idescB = tc::idesc_tf32(128, L::NB);
-    float wq[2][8], uq[2][8];
+          const float val = valid ? fw * (fw >= 0.f ? o : nb) : 0.f;
 #pragma unroll
-    for (int j = 0; j < L::NCH; ++j) {
-      if (!run2) break;
-      const uint32_t g = chunk_ctr + j;
-      const int s = (int)(g % L::NSLOT);
-      const uint32_t use = g / L::NSLOT;
-      if (use > 0 && *abort_flag == 0 && !tc::mbar_wait(empty + s, (use - 1) & 1)) *abort_flag = 1;
-      float vals[2][8];
-      if (j < L::NCHF) {
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          const int idx = j * 8 + kk;
-#pragma unroll
-          for (int c = 0; c < 2; ++c) vals[c][kk] = idx < NF * NFM ? phi[c][idx < NF * NFM ? idx : 0] : 0.f;
-        }
-      } else {
-        // volume chunk: K index 2 q + dd for q = 4 jv .. 4 jv + 3
-        const int jv = j - L::NCHF;
-        if ((jv & 1) == 0) {
-          const int q0 = jv * 4;
-#pragma unroll
-          for (int c = 0; c < 2; ++c) tcimpl::tmem_load<8>(lane_base + L::cS + c * L::NAS + q0, wq[c]);
-#pragma unroll
-          for (int d = 0; d < 2; ++d) tcimpl::tmem_load<8>(lane_base + L::cW + d * L::NAW + q0, uq[d]);
-        }
-        const int qo = (jv & 1) * 4;
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          const int ql = qo + kk / 2, d = kk & 1;
-          const int q = jv * 4 + kk / 2;
-#pragma unroll
-          for (int c = 0; c < 2; ++c) vals[c][kk] = (q < QV && valid) ? -uq[d][ql] * wq[c][ql] : 0.f;
+          for (int m = 0; m < NFM; ++m) phi[f * NFM + m] += qq[m] * val;
         }
       }
-      float* slot = op + s * (2 * 2 * L::szChunk);
 #pragma unroll
-      for (int c = 0; c < 2; ++c)
+      for (int j = 0; j < L::NCHF; ++j) {
+        store4(fslot[j], 0, phi[8 * j], phi[8 * j + 1], phi[8 * j + 2], phi[8 * j + 3]);
+        store4(fslot[j], 4, phi[8 * j + 4], phi[8 * j + 5], phi[8 * j + 6], phi[8 * j + 7]);
+        tc::fence_proxy_async_smem();
+        tcimpl::mbar_arrive(full + (chunk_ctr + j) % L::NSLOT);
+        if (t == 0 && *abort_flag == 0) issue_chunk(chunk_ctr + j, j);
+        __syncwarp();   // warp 0 reconverges before its next warp-collective TMEM load
+      }
+
+      // ---- volume chunks, in pairs sharing one TMEM load of 8 volume points --------
+      constexpr int NCHV = L::NCH - L::NCHF;
+#pragma unroll 1
+      for (int jp = 0; jp < NCHV; jp += 2) {
+        const int q0 = jp * 4;
+        float wq[8], uq0[8], uq1[8];
+        tcimpl::tmem_load<8>(lane_base + L::cS + c * L::NAS + q0, wq);
+        tcimpl::tmem_load<8>(lane_base + L::cW + q0, uq0);
+        tcimpl::tmem_load<8>(lane_base + L::cW + L::NAW + q0, uq1);
 #pragma unroll
-        for (int k4 = 0; k4 < 8; k4 += 4) {
-          float h[4], tl[4];
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int jv = jp + h2;
+          if (jv >= NCHV) break;
+          const int j = L::NCHF + jv;
+          float* slot = claim_chunk(chunk_ctr + j);
+          float v[8];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) tcimpl::split(vals[c][k4 + u], h[u], tl[u]);
-          const uint32_t o = tc::kmajor_off32(t, k4, L::LBO, L::SBO_CH) / 4;
-          tc::st_shared_v4(slot + (c * 2 + 0) * L::szChunk + o, h[0], h[1], h[2], h[3]);
-          tc::st_shared_v4(slot + (c * 2 + 1) * L::szChunk + o, tl[0], tl[1], tl[2], tl[3]);
-        }
-      tc::fence_proxy_async_smem();
-      tcimpl::mbar_arrive(full + s);
-      if (t == 0 && *abort_flag == 0) {
-        if (!tc::mbar_wait(full + s, use & 1)) {
-          *abort_flag = 1;
-        } else {
-          tc::fence_after_sync();
-          const uint32_t sl = op_s + 4u * (s * 2 * 2 * L::szChunk);
-          for (int c = 0; c < 2; ++c)
-            for (int pass = 0; pass < 3; ++pass) {
-              const uint32_t a_op = sl + 4u * ((c * 2 + (pass == 2 ? 1 : 0)) * L::szChunk);
-              const uint32_t b_op = tb_s + (pass == 1 ? 4u * L::szTB : 0u) + j * 2 * L::LBO;
-              tc::mma_tf32(tbase + L::cB + c * L::NB, tc::smem_desc(a_op, L::LBO, L::SBO_CH),
-                           tc::smem_desc(b_op, L::LBO, L::SBO_KB), idescB, (j > 0 || pass > 0) ? 1u : 0u);
-            }
-          tc::mma_commit(empty + s);
-          if (j == L::NCH - 1) tc::mma_commit(bar_B);
+          for (int kk = 0; kk < 8; ++kk) {
+            const int ql = h2 * 4 + kk / 2;
+            const float u = (kk & 1) ? uq1[ql] : uq0[ql];
+            v[kk] = (q0 + ql < QV && valid) ? -u * wq[ql] : 0.f;
+          }
+          store4(slot, 0, v[0], v[1], v[2], v[3]);
+          store4(slot, 4, v[4], v[5], v[6], v[7]);
+          tc::fence_proxy_async_smem();
+          tcimpl::mbar_arrive(full + (chunk_ctr + j) % L::NSLOT);
+          if (t == 0 && *abort_flag == 0) issue_chunk(chunk_ctr + j, j);
+          __syncwarp();
         }
       }
     }
     chunk_ctr += L::NCH;
 
-    // ---- epilogue: FP64 stage combination ---------------------------------------------
-    const double* vin_e = a.vin + (size_t)e * 2 * N;
-    const double* vn_e = a.vn ? a.vn + (size_t)e * 2 * N : nullptr;
-    if (valid) {   // pull this element's lines into L1 while the last MMAs finish
+    // ---- epilogue: FP64 stage combination, output traces ------------------------------
+    double xin[N], xn[N];
+    const bool has_vn = a.vn != nullptr;
 #pragma unroll
-      for (int b = 0; b < 2 * N * 8; b += 128) {
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(vin_e) + b));
-        if (vn_e) asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(vn_e) + b));
-      }
+    for (int i = 0; i < N; ++i) {   // coalesced loads, issued before waiting on GEMM B
+      xin[i] = valid ? a.vin[tsoa_index(e, c, i, N)] : 0.0;
+      xn[i] = (valid && has_vn) ? a.vn[tsoa_index(e, c, i, N)] : 0.0;
     }
     if (run2 && *abort_flag == 0 && !tc::mbar_wait(bar_B, it & 1)) *abort_flag = 1;
     tc::fence_after_sync();
     __syncthreads();
     const bool fin = run2 && *abort_flag == 0;   // uniform after the barrier
-    if (fin) {
-      float r[2][L::NB];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) tcimpl::tmem_load<L::NB>(lane_base + L::cB + c * L::NB, r[c]);
-      if (valid) {
-        double* vout_e = a.vout + (size_t)e * 2 * N;
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            double x = a.beta * vin_e[c * N + i] - a.gamma * (double)r[c][i];
-            if (vn_e) x += a.alpha * vn_e[c * N + i];
-            vout_e[c * N + i] = x;
-          }
-      }
-    } else {
+    if (!fin) {
       if (t == 0) atomicOr(a.status, 2);   // a bounded wait gave up: this CTA stops
       break;
+    }
+    float rr[L::NB];
+    tcimpl::tmem_load<L::NB>(lane_base + L::cB + c * L::NB, rr);
+    if (valid) {
+      // vout = alpha vn + beta vin + gamma L, L = -r: the increment -gamma r is
+      // formed in FP32 (r carries FP32 accuracy) and accumulated in FP64
+      const float mg = (float)(-a.gamma);
+      float xo[NP4];
+#pragma unroll
+      for (int i = 0; i < NP4; ++i) xo[i] = 0.f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const double inc = tc::f32_to_f64(mg * rr[i]);
+        double x;
+        if (a.beta == 1.0 && !has_vn) x = xin[i] + inc;
+        else {
+          x = fma(a.beta, xin[i], inc);
+          if (has_vn) x = fma(a.alpha, xn[i], x);
+        }
+        a.vout[tsoa_index(e, c, i, N)] = x;
+        xo[i] = tc::f64_to_f32_rn(x);
+      }
+      float tr[NF][NFM];
+      facet_traces<N, NF, NFM, NP4>(Ef, xo, tr);
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int m = 0; m < NFM; ++m) a.trout[tr_index(e, c, f, m, NFM)] = tr[f][m];
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -415,6 +427,44 @@ __global__ void __launch_bounds__(128, 1) stage_tc_kernel(StageTcArgs a) {
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, L::TMEM_COLS);
+}
+
+// ABI layout [E][2][N] -> TSOA, plus the facet traces of the state (TR)
+template <int K>
+__global__ void __launch_bounds__(256) tsoa_in_kernel(const double* __restrict__ v, double* __restrict__ vt,
+                                                      float* __restrict__ tr, const float* __restrict__ blob, int E) {
+  using L = TcLayout2D<K>;
+  constexpr int N = L::N, NF = L::NF, NFM = L::NFM, NP4 = L::NP4;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = (int)(gid >> 1), c = (int)(gid & 1);
+  if (e >= E) return;
+  float x[NP4];
+#pragma unroll
+  for (int i = 0; i < NP4; ++i) x[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double d = v[((size_t)e * 2 + c) * N + i];
+    vt[tsoa_index(e, c, i, N)] = d;
+    x[i] = tc::f64_to_f32_rn(d);
+  }
+  float t[NF][NFM];
+  facet_traces<N, NF, NFM, NP4>(blob + L::oEf, x, t);
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int m = 0; m < NFM; ++m) tr[tr_index(e, c, f, m, NFM)] = t[f][m];
+}
+
+// TSOA -> ABI layout
+template <int K>
+__global__ void __launch_bounds__(256) tsoa_out_kernel(const double* __restrict__ vt, double* __restrict__ v, int E) {
+  constexpr int N = TcLayout2D<K>::N;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long)E * 2 * N) return;
+  const int i = (int)(gid % N);
+  const int c = (int)((gid / N) % 2);
+  const int e = (int)(gid / (2 * N));
+  v[gid] = vt[tsoa_index(e, c, i, N)];
 }
 
 }  // namespace dgc

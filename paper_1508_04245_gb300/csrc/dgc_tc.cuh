@@ -159,6 +159,31 @@ __device__ __forceinline__ void bulk_wait_read0() {
 }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// FP64 -> FP32, round to nearest even, with integer operations only (the FP64
+// pipe of this GPU is narrow).  Magnitudes below the FP32 normal range flush
+// to a signed zero; the coefficients converted here are far inside the range.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  // 23 kept mantissa bits and the 29 dropped ones
+  uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const uint32_t rest = lo & 0x1FFFFFFFu;
+  uint32_t mag = ((uint32_t)e << 23) + m;
+  mag += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;   // carry may raise e
+  return __uint_as_float(e <= 0 ? sign : (e >= 255 ? (sign | 0x7F800000u) : (sign | mag)));
+}
+// FP32 -> FP64 (exact), integer operations only; FP32 subnormals flush to zero
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
+  const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  const uint32_t lo = (u & 0x7u) << 29;
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
 // round to TF32 (nearest, ties away) and the FP32 remainder
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
