@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dgconv", choices=["dgconv", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "tf32x3"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp32", "fp64", "tf32x3"])
+    ap.add_argument("--no-other-precisions", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--substeps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -248,7 +249,8 @@ def main():
         mesh.rk_substeps(wnd, v, ds, substeps, 3, args.prec)   # a3..a7
         mesh.mass(v, out=mv)                              # a6 (M^V)
         mesh.transfer_T(mv, out=g)                        # a8
-    launches_per_step = 1 + 1 + (1 + 3 * substeps) + 1 + 2
+    # geometry, transfer, [wind prep (+ layout in/out on the tensor-core path), stages], mass, transfer_T (2)
+    launches_per_step = 1 + 1 + (1 + 3 * substeps + (2 if args.prec == "tf32x3" else 0)) + 1 + 2
 
     for _ in range(args.warmup):
         step()
@@ -349,6 +351,39 @@ def main():
         "roofline": roof,
         "clocks": clk,
     }
+    if not args.no_other_precisions:
+        # the same step at the other contraction precisions (1 warm-up, 2 timed steps each)
+        others = {}
+        for prec in ("fp64", "fp32", "tf32x3"):
+            if prec == args.prec:
+                continue
+
+            def step_p(p=prec):
+                mesh.geometry()
+                mesh.transfer(u_n, out=v)
+                mesh.rk_substeps(wind, v, ds, substeps, 3, p)
+                mesh.mass(v, out=mv)
+                mesh.transfer_T(mv, out=g)
+            step_p()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(2):
+                flush.zero_()
+                a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                step_p()
+                b0.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a0.elapsed_time(b0))
+            v64 = mesh.transfer(u_n)
+            mesh.rk_substeps(wind, v64, ds, substeps, 3, "fp64")
+            vp = mesh.transfer(u_n)
+            mesh.rk_substeps(wind, vp, ds, substeps, 3, prec)
+            torch.cuda.synchronize()
+            e_p = float((vp - v64).abs().max() / v64.abs().max())
+            others[prec] = {"value": world * units_per_step / (statistics.mean(ts) * 1e-3),
+                            "ms_per_step": statistics.mean(ts), "max_rel_err_vs_fp64": e_p}
+        line["other_precisions"] = others
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         runner = OracleRunner(wl)
         rate, dt = runner.stages(3)

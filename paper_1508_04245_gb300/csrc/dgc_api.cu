@@ -91,7 +91,8 @@ struct dgc_mesh {
   // stage-table blobs
   DevBuf<double> tab64;
   DevBuf<float> tab32, tcblob, wcoef, trA, trB;
-  DevBuf<double> ts0, ts1, ts2;   // tile-blocked state vectors of the tensor-core path
+  DevBuf<double> ts0;              // tile-blocked FP64 state of the tensor-core path
+  DevBuf<float> tsf, d1, d2;       // its FP32 copy and the FP32 stage increments
   DevBuf<int> status;
   // scratch
   DevBuf<double> Uw64, Fw64, stage1, stage2, zbuf;
@@ -146,8 +147,9 @@ struct dgc_mesh {
     trA.release();
     trB.release();
     ts0.release();
-    ts1.release();
-    ts2.release();
+    tsf.release();
+    d1.release();
+    d2.release();
     status.release();
     Uw32.release();
     Fw32.release();
@@ -234,36 +236,40 @@ dgc_status ensure_tc_scratch(dgc_mesh* m) {
   DGC_CUDA(m->wcoef.alloc((size_t)m->E * m->s.D * dgc::tc_nk(m->s.D, m->s.K)));
   const size_t nt = dgc::tc_tsoa_len(m->s.D, m->s.K, m->E), nr = dgc::tc_tr_len(m->s.D, m->s.K, m->E);
   DGC_CUDA(m->ts0.alloc(nt));
-  DGC_CUDA(m->ts1.alloc(nt));
-  DGC_CUDA(m->ts2.alloc(nt));
+  DGC_CUDA(m->tsf.alloc(nt));
+  DGC_CUDA(m->d1.alloc(nt));
+  DGC_CUDA(m->d2.alloc(nt));
   DGC_CUDA(m->trA.alloc(nr));
   DGC_CUDA(m->trB.alloc(nr));
   return DGC_OK;
 }
 
-dgc_status launch_stage_tc(dgc_mesh* m, const double* vin, const float* trin, const double* vn, double* vout,
-                           float* trout, double alpha, double beta, double gamma, cudaStream_t st) {
+// one tensor-core stage in increment form (see dgc::StageTcArgs)
+dgc_status launch_stage_tc(dgc_mesh* m, int mode, const float* din, const float* trin, float* dout, float* trout,
+                           double p, double q, double* v, cudaStream_t st) {
   dgc::StageTcArgs a;
-  a.vin = vin;
-  a.vn = vn;
-  a.vout = vout;
+  a.vf = m->tsf.ptr;
+  a.din = din;
   a.trin = trin;
+  a.dout = dout;
+  a.v = v;
+  a.vf_out = m->tsf.ptr;
   a.trout = trout;
   a.wcoef = m->wcoef.ptr;
   a.nbr = m->nbr.ptr;
   a.blob = m->tcblob.ptr;
   a.status = m->status.ptr;
   a.E = m->E;
-  a.alpha = alpha;
-  a.beta = beta;
-  a.gamma = gamma;
+  a.mode = mode;
+  a.p = (float)p;
+  a.q = (float)q;
   cudaError_t err = dgc::launch_stage_tc(m->s.D, m->s.K, &a, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed: %s", cudaGetErrorString(err));
   return DGC_OK;
 }
 
-dgc_status tc_transpose_in(dgc_mesh* m, const double* v, double* vt, float* tr, cudaStream_t st) {
-  cudaError_t err = dgc::launch_tsoa_in(m->s.D, m->s.K, v, vt, tr, m->tcblob.ptr, m->E, st);
+dgc_status tc_transpose_in(dgc_mesh* m, const double* v, float* tr, cudaStream_t st) {
+  cudaError_t err = dgc::launch_tsoa_in(m->s.D, m->s.K, v, m->ts0.ptr, m->tsf.ptr, tr, m->tcblob.ptr, m->E, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "layout transpose failed: %s", cudaGetErrorString(err));
   return DGC_OK;
 }
@@ -274,25 +280,28 @@ dgc_status tc_transpose_out(dgc_mesh* m, const double* vt, double* v, cudaStream
   return DGC_OK;
 }
 
-// SSP-RK substeps on the tensor-core path: ABI -> TSOA once, stages ping-pong the
-// trace buffers, TSOA -> ABI at the end
+// SSP-RK substeps on the tensor-core path, increment form: v^(i) = v^n + d_i,
+//   RK3: d1 = ds L(v),  d2 = d1/4 + ds/4 L(v + d1),  v += 2/3 d2 + 2/3 ds L(v + d2)
+//   RK2: d1 = ds L(v),  v += d1/2 + ds/2 L(v + d1)
+// (identical to the Shu-Osher / Heun forms); the state v is accumulated in FP64
+// once per substep, the increments are FP32.  ABI -> TSOA once, back at the end.
 dgc_status rk_sequence_tc(dgc_mesh* m, double* v, double ds, int nsteps, int scheme, cudaStream_t st) {
-  double *T0 = m->ts0.ptr, *T1 = m->ts1.ptr, *T2 = m->ts2.ptr;
   float *cur = m->trA.ptr, *oth = m->trB.ptr;
-  if (dgc_status rc = tc_transpose_in(m, v, T0, cur, st)) return rc;
+  if (dgc_status rc = tc_transpose_in(m, v, cur, st)) return rc;
   for (int n = 0; n < nsteps; ++n) {
     dgc_status rc;
     if (scheme == DGC_SSPRK2) {
-      if ((rc = launch_stage_tc(m, T0, cur, nullptr, T1, oth, 0.0, 1.0, ds, st))) return rc;
-      if ((rc = launch_stage_tc(m, T1, oth, T0, T0, cur, 0.5, 0.5, 0.5 * ds, st))) return rc;
+      if ((rc = launch_stage_tc(m, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr, st))) return rc;
+      if ((rc = launch_stage_tc(m, 1, m->d1.ptr, oth, nullptr, cur, 0.5, 0.5 * ds, m->ts0.ptr, st))) return rc;
     } else {
-      if ((rc = launch_stage_tc(m, T0, cur, nullptr, T1, oth, 0.0, 1.0, ds, st))) return rc;
-      if ((rc = launch_stage_tc(m, T1, oth, T0, T2, cur, 0.75, 0.25, 0.25 * ds, st))) return rc;
-      if ((rc = launch_stage_tc(m, T2, cur, T0, T0, oth, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * ds, st))) return rc;
+      if ((rc = launch_stage_tc(m, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr, st))) return rc;
+      if ((rc = launch_stage_tc(m, 0, m->d1.ptr, oth, m->d2.ptr, cur, 0.25, 0.25 * ds, nullptr, st))) return rc;
+      if ((rc = launch_stage_tc(m, 1, m->d2.ptr, cur, nullptr, oth, 2.0 / 3.0, 2.0 / 3.0 * ds, m->ts0.ptr, st)))
+        return rc;
       std::swap(cur, oth);
     }
   }
-  return tc_transpose_out(m, T0, v, st);
+  return tc_transpose_out(m, m->ts0.ptr, v, st);
 }
 
 // one stage vout = alpha vn + beta vin + gamma L(vin), any precision
@@ -513,11 +522,11 @@ dgc_status dgc_conv_apply(dgc_mesh* mesh, const double* wind_hdiv, const double*
   if (dgc_status rc = prepare_wind(mesh, prec, wind_hdiv, st)) return rc;
   // out = -L(w) = (M^V)^-1 C^V w
   if (prec == DGC_TF32X3) {
-    if (dgc_status rc = tc_transpose_in(mesh, w_dg, mesh->ts0.ptr, mesh->trA.ptr, st)) return rc;
-    if (dgc_status rc = launch_stage_tc(mesh, mesh->ts0.ptr, mesh->trA.ptr, nullptr, mesh->ts1.ptr, mesh->trB.ptr,
-                                        0.0, 0.0, -1.0, st))
+    if (dgc_status rc = tc_transpose_in(mesh, w_dg, mesh->trA.ptr, st)) return rc;
+    // mode 2 with q = -1: v <- -L(w) = (M^V)^-1 C^V w
+    if (dgc_status rc = launch_stage_tc(mesh, 2, nullptr, mesh->trA.ptr, nullptr, nullptr, 0.0, -1.0, mesh->ts0.ptr, st))
       return rc;
-    return tc_transpose_out(mesh, mesh->ts1.ptr, out_dg, st);
+    return tc_transpose_out(mesh, mesh->ts0.ptr, out_dg, st);
   }
   return stage(mesh, prec, w_dg, nullptr, out_dg, 0.0, 0.0, -1.0, st);
 }

@@ -52,8 +52,8 @@ cudaError_t launch_stage_tc(int D, int K, const StageTcArgs* a, cudaStream_t s);
 // (the inward one also writes the facet traces of the state)
 size_t tc_tsoa_len(int D, int K, int E);
 size_t tc_tr_len(int D, int K, int E);
-cudaError_t launch_tsoa_in(int D, int K, const double* v, double* vt, float* tr, const float* blob, int E,
-                           cudaStream_t s);
+cudaError_t launch_tsoa_in(int D, int K, const double* v, double* vt, float* vft, float* tr, const float* blob,
+                           int E, cudaStream_t s);
 cudaError_t launch_tsoa_out(int D, int K, const double* vt, double* v, int E, cudaStream_t s);
 // wind on the Dubiner basis scaled by 1/det J, float [E][D][nk] (zero padded)
 cudaError_t launch_wind_coeffs(const DevMesh& m, const double* u_hdiv, float* wc, int nk, cudaStream_t s);

@@ -74,15 +74,16 @@ cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
     if (sms <= 0) sms = 1;
   }
   const int grid = tiles < 2 * sms ? tiles : 2 * sms;
-  kern<<<grid, 256, L::SMEM_BYTES, s>>>(*a);
+  kern<<<grid, 288, L::SMEM_BYTES, s>>>(*a);
   return cudaGetLastError();
 }
 
 template <int K>
-cudaError_t tsoa_in_t(const double* v, double* vt, float* tr, const float* blob, int E, cudaStream_t s) {
+cudaError_t tsoa_in_t(const double* v, double* vt, float* vft, float* tr, const float* blob, int E,
+                      cudaStream_t s) {
   const long n = 2L * E;
   if (n == 0) return cudaSuccess;
-  tsoa_in_kernel<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, vt, tr, blob, E);
+  tsoa_in_kernel<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, vt, vft, tr, blob, E);
   return cudaGetLastError();
 }
 
@@ -105,14 +106,14 @@ size_t tc_tr_len(int D, int K, int E) {
   return tiles * 128 * D * (D + 1) * (size_t)(K + 1);
 }
 
-cudaError_t launch_tsoa_in(int D, int K, const double* v, double* vt, float* tr, const float* blob, int E,
-                           cudaStream_t s) {
+cudaError_t launch_tsoa_in(int D, int K, const double* v, double* vt, float* vft, float* tr, const float* blob,
+                           int E, cudaStream_t s) {
   if (D != 2) return cudaErrorInvalidValue;
   switch (K) {
-    case 1: return tsoa_in_t<1>(v, vt, tr, blob, E, s);
-    case 2: return tsoa_in_t<2>(v, vt, tr, blob, E, s);
-    case 3: return tsoa_in_t<3>(v, vt, tr, blob, E, s);
-    case 4: return tsoa_in_t<4>(v, vt, tr, blob, E, s);
+    case 1: return tsoa_in_t<1>(v, vt, vft, tr, blob, E, s);
+    case 2: return tsoa_in_t<2>(v, vt, vft, tr, blob, E, s);
+    case 3: return tsoa_in_t<3>(v, vt, vft, tr, blob, E, s);
+    case 4: return tsoa_in_t<4>(v, vt, vft, tr, blob, E, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -44,18 +44,27 @@ __host__ __device__ __forceinline__ size_t tr_index(int e, int c, int f, int m, 
   return ((size_t)(e >> 7) * 2 * 3 * NFM + ((size_t)c * 3 + f) * NFM + m) * 128 + (e & 127);
 }
 
+// One SSP-RK stage in increment form: the stage input is v^n + din, the
+// kernel forms inc = p din + q L(v^n + din) with L = -(M^V)^{-1} C^V, and
+//   mode 0: writes inc (FP32) and the facet traces of v^n + inc;
+//   mode 1: v <- v + inc in FP64 (the substep's state accumulation), writes
+//           the FP32 copy of the new v and its facet traces;
+//   mode 2: v <- inc in FP64 (the operator itself, for conv_apply).
 struct StageTcArgs {
-  const double* vin;    // TSOA stage input
-  const double* vn;     // TSOA substep start state or null (alpha == 0); may equal vout
-  double* vout;         // TSOA stage output
-  const float* trin;    // TR traces of vin on the facet bases
-  float* trout;         // TR traces of vout
+  const float* vf;      // TSOA FP32 copy of v^n
+  const float* din;     // TSOA FP32 increment of the stage input, null = none
+  const float* trin;    // TR facet traces of the stage input
+  float* dout;          // mode 0: TSOA FP32 increment out
+  double* v;            // modes 1, 2: TSOA FP64 state
+  float* vf_out;        // mode 1: FP32 copy of the new state (may equal vf)
+  float* trout;         // modes 0, 1: facet traces of the stage output
   const float* wcoef;   // [E][2][NK] wind on the Dubiner basis, scaled by 1/det J
   const int* nbr;       // [E][3]
   const float* blob;    // TcLayout2D<K> table blob
   int* status;          // device status word
   int E;
-  double alpha, beta, gamma;
+  int mode;
+  float p, q;
 };
 
 namespace tcimpl {
@@ -99,7 +108,7 @@ __device__ __forceinline__ void facet_traces(const float* Ef, const float* x, fl
 }
 
 template <int K>
-__global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
+__global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   using L = TcLayout2D<K>;
   constexpr int N = L::N, QV = L::QV, QF = L::QF, NFM = L::NFM, NF = L::NF, NK = L::NK;
   constexpr int NP4 = L::NP4, NFM4 = L::NFM4;
@@ -117,13 +126,24 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4 + 2 * L::NSLOT);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
-  // thread = (element row r of the tile, velocity component c); warps 0-3 and
-  // 4-7 read the same TMEM lanes (a warp sees lanes 32 (warp % 4) .. + 31)
+  // threads 0..255: (element row r of the tile, velocity component c); warps
+  // 0-3 and 4-7 read the same TMEM lanes (a warp sees lanes 32 (warp % 4) ..
+  // + 31).  Warp 8 only issues the MMAs and bulk copies (thread 256).
   const int t = threadIdx.x;
   const int warp = t >> 5;
+  const bool producer = t < 256;
   const int r = t & 127;
-  const int c = t >> 7;
+  const int c = (t >> 7) & 1;
+  const int issuer_t = 256;
   const int ntiles = (a.E + 127) / 128;
+  // the next tile's contiguous TSOA / TR blocks into L2 ahead of use
+  auto prefetch_tile = [&](int tile) {
+    const uint32_t nst = 128u * 2 * N;        // values per tile in TSOA
+    const uint32_t ntr = 128u * 2 * NF * NFM;  // values per tile in TR
+    tc::bulk_prefetch_l2(a.vf + (size_t)tile * nst, nst * 4);
+    if (a.din) tc::bulk_prefetch_l2(a.din + (size_t)tile * nst, nst * 4);
+    tc::bulk_prefetch_l2(a.trin + (size_t)tile * ntr, ntr * 4);
+  };
   auto load_wind = [&](int tile) {        // a tile's wind coefficients into the staging buffer
     const uint32_t bytes = (uint32_t)min(128, a.E - tile * 128) * 2 * NK * 4;
     tc::mbar_arrive_expect_tx(bar_w, bytes);
@@ -143,10 +163,11 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
     tc::mbar_fence_init();
   }
   __syncthreads();
-  if (t == 0) {
+  if (t == issuer_t) {
     tc::mbar_arrive_expect_tx(bar_tab, L::BLOB * 4);
     tc::bulk_g2s(blob, a.blob, L::BLOB * 4, bar_tab);
     load_wind(blockIdx.x);
+    prefetch_tile(blockIdx.x);
   }
   if (warp == 0) {
     tc::tmem_alloc(tslot, L::TMEM_COLS);
@@ -210,11 +231,14 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
     const bool valid = e < a.E;
     const int next = tile + gridDim.x;
 
-    // ---- own state (coalesced TSOA loads) -> state operand of component c ----------
+    // ---- stage input v^n + din (coalesced TSOA loads) -> state operand of component c
+    if (producer) {
     float w[NP4];
 #pragma unroll
-    for (int i = 0; i < NP4; ++i)
-      w[i] = (valid && i < N) ? tc::f64_to_f32_rn(a.vin[tsoa_index(e, c, i < N ? i : 0, N)]) : 0.f;
+    for (int i = 0; i < NP4; ++i) {
+      const size_t ix = tsoa_index(e, c, i < N ? i : 0, N);
+      w[i] = (valid && i < N) ? a.vf[ix] + (a.din ? a.din[ix] : 0.f) : 0.f;
+    }
 #pragma unroll
     for (int k4 = 0; k4 < NK; k4 += 4) {
       float h[4], tl[4];
@@ -239,12 +263,13 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
       tc::st_shared_v4(op + ((2 + c) * 2 + 0) * L::szOpA + o, h[0], h[1], h[2], h[3]);
       tc::st_shared_v4(op + ((2 + c) * 2 + 1) * L::szOpA + o, tl[0], tl[1], tl[2], tl[3]);
     }
+    }   // producer
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const bool run = *abort_flag == 0;
-    if (t == 0 && run) {
+    if (t == issuer_t && run) {
       if (next < ntiles) load_wind(next);   // the staging buffer is free again
       // ---- GEMM A ------------------------------------------------------------------
       for (int f = 0; f < 4; ++f) {
@@ -266,26 +291,32 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
       }
       tc::mma_commit(bar_A);
     }
-    __syncwarp();
     // ---- own and neighbour facet traces from the trace buffer (while GEMM A runs) ---
     float to[NF][NFM], tn[NF][NFM];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      const int code = valid ? a.nbr[(size_t)e * NF + f] : -1;
+      const int code = (producer && valid) ? a.nbr[(size_t)e * NF + f] : -1;
       const int ne = code >> 2, fn = code & 3;
 #pragma unroll
       for (int m = 0; m < NFM; ++m) {
-        to[f][m] = valid ? a.trin[tr_index(e, c, f, m, NFM)] : 0.f;
+        to[f][m] = (producer && valid) ? a.trin[tr_index(e, c, f, m, NFM)] : 0.f;
         tn[f][m] = code >= 0 ? a.trin[tr_index(ne, c, fn, m, NFM)] : 0.f;
       }
     }
-    if (run && *abort_flag == 0 && !tc::mbar_wait(bar_A, it & 1)) *abort_flag = 1;
+    if (producer && run && *abort_flag == 0 && !tc::mbar_wait(bar_A, it & 1)) *abort_flag = 1;
     tc::fence_after_sync();
     __syncthreads();
     const bool run2 = *abort_flag == 0;
+    // ---- issuer: next tile's inputs toward L2 (this tile's loads are done), then the
+    //      GEMM B chunk MMAs as the producers fill the slots --------------------------
+    if (!producer) {
+      if (t == issuer_t && next < ntiles) prefetch_tile(next);
+      if (t == issuer_t && run2)
+        for (int j = 0; j < L::NCH && *abort_flag == 0; ++j) issue_chunk(chunk_ctr + j, j);
+    }
 
     // ---- facets: upwind flux at the facet points, projection (chunks 0 .. NCHF-1) ---
-    if (run2) {
+    if (run2 && producer) {
       float* fslot[L::NCHF];
 #pragma unroll
       for (int j = 0; j < L::NCHF; ++j) fslot[j] = claim_chunk(chunk_ctr + j);
@@ -339,8 +370,6 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
         store4(fslot[j], 4, phi[8 * j + 4], phi[8 * j + 5], phi[8 * j + 6], phi[8 * j + 7]);
         tc::fence_proxy_async_smem();
         tcimpl::mbar_arrive(full + (chunk_ctr + j) % L::NSLOT);
-        if (t == 0 && *abort_flag == 0) issue_chunk(chunk_ctr + j, j);
-        __syncwarp();   // warp 0 reconverges before its next warp-collective TMEM load
       }
 
       // ---- volume chunks, in pairs sharing one TMEM load of 8 volume points --------
@@ -369,22 +398,23 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
           store4(slot, 4, v[4], v[5], v[6], v[7]);
           tc::fence_proxy_async_smem();
           tcimpl::mbar_arrive(full + (chunk_ctr + j) % L::NSLOT);
-          if (t == 0 && *abort_flag == 0) issue_chunk(chunk_ctr + j, j);
-          __syncwarp();
         }
       }
     }
     chunk_ctr += L::NCH;
 
-    // ---- epilogue: FP64 stage combination, output traces ------------------------------
-    double xin[N], xn[N];
-    const bool has_vn = a.vn != nullptr;
+    // ---- epilogue: increment, FP64 accumulation (mode 1), output traces --------------
+    // operands of the epilogue are loaded before waiting on GEMM B
+    float ed[N], ev[N];
+    double ex[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) {   // coalesced loads, issued before waiting on GEMM B
-      xin[i] = valid ? a.vin[tsoa_index(e, c, i, N)] : 0.0;
-      xn[i] = (valid && has_vn) ? a.vn[tsoa_index(e, c, i, N)] : 0.0;
+    for (int i = 0; i < N; ++i) {
+      const size_t ix = tsoa_index(e, c, i, N);
+      ed[i] = (producer && valid && a.din) ? a.din[ix] : 0.f;
+      ev[i] = (producer && valid && a.mode == 0) ? a.vf[ix] : 0.f;
+      ex[i] = (producer && valid && a.mode == 1) ? a.v[ix] : 0.0;
     }
-    if (run2 && *abort_flag == 0 && !tc::mbar_wait(bar_B, it & 1)) *abort_flag = 1;
+    if (producer && run2 && *abort_flag == 0 && !tc::mbar_wait(bar_B, it & 1)) *abort_flag = 1;
     tc::fence_after_sync();
     __syncthreads();
     const bool fin = run2 && *abort_flag == 0;   // uniform after the barrier
@@ -393,32 +423,36 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
       break;
     }
     float rr[L::NB];
-    tcimpl::tmem_load<L::NB>(lane_base + L::cB + c * L::NB, rr);
-    if (valid) {
-      // vout = alpha vn + beta vin + gamma L, L = -r: the increment -gamma r is
-      // formed in FP32 (r carries FP32 accuracy) and accumulated in FP64
-      const float mg = (float)(-a.gamma);
+    if (producer) tcimpl::tmem_load<L::NB>(lane_base + L::cB + c * L::NB, rr);
+    if (producer && valid) {
+      // inc = p din + q L, L = -r (r carries FP32 accuracy)
       float xo[NP4];
 #pragma unroll
       for (int i = 0; i < NP4; ++i) xo[i] = 0.f;
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const double inc = tc::f32_to_f64(mg * rr[i]);
-        double x;
-        if (a.beta == 1.0 && !has_vn) x = xin[i] + inc;
-        else {
-          x = fma(a.beta, xin[i], inc);
-          if (has_vn) x = fma(a.alpha, xn[i], x);
+        const size_t ix = tsoa_index(e, c, i, N);
+        const float inc = fmaf(a.p, ed[i], -a.q * rr[i]);
+        if (a.mode == 0) {
+          a.dout[ix] = inc;
+          xo[i] = ev[i] + inc;
+        } else if (a.mode == 1) {
+          const double x = ex[i] + tc::f32_to_f64(inc);   // FP64 state accumulation
+          a.v[ix] = x;
+          xo[i] = tc::f64_to_f32_rn(x);
+          a.vf_out[ix] = xo[i];
+        } else {
+          a.v[ix] = tc::f32_to_f64(inc);
         }
-        a.vout[tsoa_index(e, c, i, N)] = x;
-        xo[i] = tc::f64_to_f32_rn(x);
       }
-      float tr[NF][NFM];
-      facet_traces<N, NF, NFM, NP4>(Ef, xo, tr);
+      if (a.mode != 2) {
+        float tr[NF][NFM];
+        facet_traces<N, NF, NFM, NP4>(Ef, xo, tr);
 #pragma unroll
-      for (int f = 0; f < NF; ++f)
+        for (int f = 0; f < NF; ++f)
 #pragma unroll
-        for (int m = 0; m < NFM; ++m) a.trout[tr_index(e, c, f, m, NFM)] = tr[f][m];
+          for (int m = 0; m < NFM; ++m) a.trout[tr_index(e, c, f, m, NFM)] = tr[f][m];
+      }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -429,10 +463,11 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(StageTcArgs a) {
   if (warp == 0) tc::tmem_dealloc(tbase, L::TMEM_COLS);
 }
 
-// ABI layout [E][2][N] -> TSOA, plus the facet traces of the state (TR)
+// ABI layout [E][2][N] -> TSOA (FP64 and its FP32 copy), plus the facet traces (TR)
 template <int K>
 __global__ void __launch_bounds__(256) tsoa_in_kernel(const double* __restrict__ v, double* __restrict__ vt,
-                                                      float* __restrict__ tr, const float* __restrict__ blob, int E) {
+                                                      float* __restrict__ vft, float* __restrict__ tr,
+                                                      const float* __restrict__ blob, int E) {
   using L = TcLayout2D<K>;
   constexpr int N = L::N, NF = L::NF, NFM = L::NFM, NP4 = L::NP4;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -446,6 +481,7 @@ __global__ void __launch_bounds__(256) tsoa_in_kernel(const double* __restrict__
     const double d = v[((size_t)e * 2 + c) * N + i];
     vt[tsoa_index(e, c, i, N)] = d;
     x[i] = tc::f64_to_f32_rn(d);
+    vft[tsoa_index(e, c, i, N)] = x[i];
   }
   float t[NF][NFM];
   facet_traces<N, NF, NFM, NP4>(blob + L::oEf, x, t);
