@@ -151,6 +151,29 @@ def stage_bytes_flops(wl):
     return byts, flops, N
 
 
+def ncu_traffic(wl, prec):
+    """DRAM bytes per stage launch from the committed ncu capture, if it still applies.
+
+    The capture records the sha1 of the kernel source it measured; after any
+    change of that source the figure is stale and None is returned.
+    """
+    if prec != "tf32x3" or wl.name != "square256_k4":
+        return None
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "stage_tc_kernel_square256_k4.md")
+    src = os.path.join(ROOT, "paper_1508_04245_gb300", "csrc", "dgc_stage_tc.cuh")
+    try:
+        text = open(prof).read()
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    fields = dict(ln.split(":", 1) for ln in text.splitlines()
+                  if ln.startswith(("kernel_source_sha1:", "traffic_bytes_per_launch:")))
+    if fields.get("kernel_source_sha1", "").split()[0:1] != [sha]:
+        return None
+    return float(fields["traffic_bytes_per_launch"].strip())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -334,7 +357,8 @@ def main():
     hbm, hbm_src = peaks()
     achieved = byts * wl.n_elem / (stage_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "peak_source": hbm_src, "kernel": "stage_kernel",
+            "traffic": ncu_traffic(wl, args.prec), "peak_source": hbm_src,
+            "kernel": "stage_tc_kernel" if args.prec == "tf32x3" else "stage_kernel",
             "stage_ms": stage_ms, "alg_bytes_per_elem_stage": byts, "alg_flops_per_elem_stage": flops,
             "achieved_tflops": flops * wl.n_elem / (stage_ms * 1e-3) / 1e12}
     line = {
