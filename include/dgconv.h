@@ -131,6 +131,21 @@ dgc_status dgc_conv_apply(dgc_mesh* mesh, const double* wind_hdiv, const double*
 dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg, double ds, int nsteps,
                            dgc_scheme scheme, dgc_prec prec, void* stream);
 
+/* Many independent propagation problems (Sec. 3.2.2) in one call: instance i
+ * advances states[i] (device [n_dg of meshes[i]], FP64, in place) by
+ * nsteps[i] substeps of size ds[i] with the frozen wind winds[i] (device
+ * [n_hdiv of meshes[i]]), exactly as dgc_rk_substeps would.  Meshes may
+ * differ in size and order but must be distinct handles (each owns its
+ * scratch).  All instances are captured into one CUDA graph whose branches
+ * run concurrently; the graph is cached (keyed by every argument) and
+ * replayed by later identical calls, and dropped when one of its meshes is
+ * freed.  meshes, winds, states, ds, nsteps: host arrays of n_inst entries.
+ * With DGC_TF32X3, instances whose order the tensor-core path does not cover
+ * (see dgc_prec) run their contractions in FP32 on CUDA cores. */
+dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const double* const* winds,
+                                 double* const* states, const double* ds, const int* nsteps, dgc_scheme scheme,
+                                 dgc_prec prec, void* stream);
+
 /* Points at which callers evaluate input fields, host [count][dim]:
  * kind 0: the element-wise equispaced P^{k+1} Lagrange nodes used by
  *         dgc_wind_from_potential ([E][n_lagrange][dim]);

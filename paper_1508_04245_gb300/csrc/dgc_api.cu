@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <array>
 #include <cmath>
 #include <cstdarg>
@@ -75,6 +76,21 @@ struct GraphKey {
   }
 };
 
+}  // namespace
+
+struct dgc_mesh;
+
+namespace {
+// cached graphs of dgc_batch_rk_substeps: key = every argument of the call
+struct BatchGraph {
+  std::vector<uint64_t> key;
+  std::vector<dgc_mesh*> meshes;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch_cache;
+constexpr int kBatchBranches = 8;
+cudaStream_t g_batch_streams[kBatchBranches + 1] = {nullptr};
 }  // namespace
 
 struct dgc_mesh {
@@ -461,6 +477,18 @@ dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int 
 
 dgc_status dgc_mesh_free(dgc_mesh* mesh) {
   if (!mesh) return DGC_OK;
+  {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (size_t j = 0; j < g_batch_cache.size();) {
+      BatchGraph& b = g_batch_cache[j];
+      if (std::find(b.meshes.begin(), b.meshes.end(), mesh) != b.meshes.end()) {
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        g_batch_cache.erase(g_batch_cache.begin() + j);
+      } else {
+        ++j;
+      }
+    }
+  }
   mesh->release_all();
   delete mesh;
   return DGC_OK;
@@ -568,6 +596,93 @@ dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg
     mesh->graph_key = key;
   }
   DGC_CUDA(cudaGraphLaunch(mesh->graph, st));
+  return DGC_OK;
+}
+
+dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const double* const* winds,
+                                 double* const* states, const double* ds, const int* nsteps, dgc_scheme scheme,
+                                 dgc_prec prec, void* stream) {
+  if (n_inst < 0) return fail(DGC_ERR_ARG, "n_inst must be >= 0");
+  if (n_inst == 0) return DGC_OK;
+  if (!meshes || !winds || !states || !ds || !nsteps) return fail(DGC_ERR_ARG, "NULL argument array");
+  if (scheme != DGC_SSPRK2 && scheme != DGC_SSPRK3) return fail(DGC_ERR_ARG, "unknown scheme %d", (int)scheme);
+  if (prec != DGC_FP64 && prec != DGC_FP32 && prec != DGC_TF32X3)
+    return fail(prec == DGC_BF16X3 ? DGC_ERR_UNSUPPORTED : DGC_ERR_ARG, "precision %d not available", (int)prec);
+  std::vector<dgc_prec> pr(n_inst);
+  std::vector<uint64_t> key = {(uint64_t)n_inst, (uint64_t)scheme, (uint64_t)prec};
+  for (int i = 0; i < n_inst; ++i) {
+    dgc_mesh* m = meshes[i];
+    if (!m || !winds[i] || !states[i]) return fail(DGC_ERR_ARG, "instance %d: NULL mesh or vector", i);
+    if (!(ds[i] > 0.0) || !std::isfinite(ds[i])) return fail(DGC_ERR_ARG, "instance %d: ds must be positive", i);
+    if (nsteps[i] < 0) return fail(DGC_ERR_ARG, "instance %d: nsteps must be >= 0", i);
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == m) return fail(DGC_ERR_ARG, "instances %d and %d share a mesh handle (scratch)", j, i);
+    // the tensor-core path covers triangles k <= 4; other orders run their stages in FP32
+    pr[i] = (prec == DGC_TF32X3 && !dgc::tc_supported(m->s.D, m->s.K)) ? DGC_FP32 : prec;
+    if (dgc_status rc = ensure_prec_scratch(m, pr[i])) return rc;
+    const size_t n = (size_t)m->E * m->s.D * m->s.N;
+    DGC_CUDA(m->stage1.alloc(n));
+    DGC_CUDA(m->stage2.alloc(n));
+    uint64_t dsbits;
+    std::memcpy(&dsbits, &ds[i], 8);
+    key.insert(key.end(), {(uint64_t)(uintptr_t)m, (uint64_t)(uintptr_t)winds[i], (uint64_t)(uintptr_t)states[i],
+                           dsbits, (uint64_t)nsteps[i]});
+  }
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  BatchGraph* hit = nullptr;
+  for (BatchGraph& b : g_batch_cache)
+    if (b.key == key) hit = &b;
+  if (!hit) {
+    for (auto& st : g_batch_streams)
+      if (!st) DGC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaStream_t main_st = g_batch_streams[0];
+    std::vector<cudaEvent_t> evs;
+    auto new_event = [&](cudaEvent_t* e) {
+      cudaError_t err = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+      if (err == cudaSuccess) evs.push_back(*e);
+      return err;
+    };
+    auto cleanup = [&]() {
+      for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    };
+    DGC_CUDA(cudaStreamBeginCapture(main_st, cudaStreamCaptureModeThreadLocal));
+    cudaEvent_t fork;
+    cudaError_t err = new_event(&fork);
+    if (err == cudaSuccess) err = cudaEventRecord(fork, main_st);
+    dgc_status rc = DGC_OK;
+    const int branches = std::min(n_inst, kBatchBranches);
+    for (int b = 0; b < branches && err == cudaSuccess; ++b) err = cudaStreamWaitEvent(g_batch_streams[1 + b], fork, 0);
+    // instance i runs on branch i % branches; branches are independent graph paths
+    for (int i = 0; i < n_inst && err == cudaSuccess && rc == DGC_OK; ++i) {
+      if (nsteps[i] == 0) continue;
+      rc = rk_sequence(meshes[i], winds[i], states[i], ds[i], nsteps[i], (int)scheme, pr[i],
+                       g_batch_streams[1 + i % branches]);
+    }
+    for (int b = 0; b < branches && err == cudaSuccess; ++b) {
+      cudaEvent_t join;
+      err = new_event(&join);
+      if (err == cudaSuccess) err = cudaEventRecord(join, g_batch_streams[1 + b]);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(main_st, join, 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t err2 = cudaStreamEndCapture(main_st, &g);
+    cleanup();
+    if (rc != DGC_OK || err != cudaSuccess || err2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (rc != DGC_OK) return rc;
+      return fail(DGC_ERR_CUDA, "batch graph capture failed: %s",
+                  cudaGetErrorString(err != cudaSuccess ? err : err2));
+    }
+    BatchGraph bg;
+    bg.key = key;
+    bg.meshes.assign(meshes, meshes + n_inst);
+    err = cudaGraphInstantiate(&bg.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(err));
+    g_batch_cache.push_back(bg);
+    hit = &g_batch_cache.back();
+  }
+  DGC_CUDA(cudaGraphLaunch(hit->exec, as_stream(stream)));
   return DGC_OK;
 }
 

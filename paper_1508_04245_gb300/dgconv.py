@@ -34,6 +34,7 @@ SIGNATURES = {
     "dgc_mass_apply": [_vp, _vp, _vp, ctypes.c_int, _vp],
     "dgc_conv_apply": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp],
     "dgc_rk_substeps": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
+    "dgc_batch_rk_substeps": [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp],
     "dgc_point_coords": [_vp, ctypes.c_int, _vp, _i64p],
     "dgc_wind_from_potential": [_vp, _vp, _vp, _vp],
     "dgc_project": [_vp, _vp, _vp, _vp],
@@ -214,6 +215,20 @@ class Mesh:
     def cfl_ds(self, wind, cfl: float) -> float:
         """Substep size cfl * min h_T / ((2k+1) max |u|)  (CFL rule; the paper gives none)."""
         return cfl * self.min_edge() / ((2 * self.k + 1) * self.max_wind_speed(wind))
+
+
+def batch_rk_substeps(meshes, winds, states, ds, nsteps, scheme: int = 3, prec="tf32x3", stream=None):
+    """Advance many independent instances in one graph launch (see dgc_batch_rk_substeps)."""
+    n = len(meshes)
+    if not (len(winds) == len(states) == len(ds) == len(nsteps) == n):
+        raise ValueError("batch arrays differ in length")
+    hm = (ctypes.c_void_p * n)(*[m._h.value for m in meshes])
+    hw = (ctypes.c_void_p * n)(*[_ptr(w, m.n_hdiv, "wind").value for m, w in zip(meshes, winds)])
+    hs = (ctypes.c_void_p * n)(*[_ptr(v, m.n_dg, "state").value for m, v in zip(meshes, states)])
+    hd = (ctypes.c_double * n)(*[float(x) for x in ds])
+    hn = (ctypes.c_int * n)(*[int(x) for x in nsteps])
+    check(lib().dgc_batch_rk_substeps(n, hm, hw, hs, hd, hn, int(scheme), PREC[prec], _stream(stream)))
+    return states
 
 
 def table(dim: int, k: int, name: str) -> np.ndarray:
