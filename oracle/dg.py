@@ -115,6 +115,27 @@ class ConvectionOracle:
         fac = np.einsum("sfqc,sfqi->sci", flux, self.psi_own)
         return (vol + fac) / self.absdet[:, None, None]
 
+    def magnitude(self, w) -> np.ndarray:
+        """The summand scale of ``apply``: the same sums taken over the absolute
+        values of their summands, sum |a| / |det J| per output entry.
+
+        A sum evaluated in floating point with unit roundoff eps is off by at most
+        about (number of terms) * eps * sum |a|; this is the scale against which
+        two evaluations of ``apply`` are compared when the result is a cancellation
+        (smooth states on fine meshes, where the volume and facet parts are each
+        about 1/h times the residual)."""
+        w = np.asarray(w)
+        ws = w[self.sel]
+        Wq = np.einsum("sci,qi->scq", ws, self.Psi)
+        vol = np.einsum("scq,sqa,qia->sci", np.abs(Wq), np.abs(self.vol_g), np.abs(self.dPsi), optimize=True)
+        w_own = np.einsum("sci,sfqi->sfqc", ws, self.psi_own)
+        nbw = w[np.maximum(self.nbr, 0)]
+        w_nb = np.einsum("sfci,sfqi->sfqc", nbw, self.psi_nb)
+        hat = np.where((self.un >= 0)[..., None], w_own, w_nb)
+        flux = np.abs((self.wt * self.un)[..., None] * hat)
+        fac = np.einsum("sfqc,sfqi->sci", flux, np.abs(self.psi_own))
+        return (vol + fac) / self.absdet[:, None, None]
+
 
 def rk_substeps(op: ConvectionOracle, v, ds: float, nsteps: int, scheme: int) -> np.ndarray:
     """nsteps explicit substeps of dv/ds = L v, L = -(M^V)^{-1} C^V (Sec. 3.2.2)."""

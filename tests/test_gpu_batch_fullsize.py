@@ -5,7 +5,8 @@
   the same result, and instances are checked against the oracle;
 * the benchmark workload (131072 jittered triangles, k = 4) at full size, in
   the launch configuration bench.py times: conv_apply on sampled elements
-  against the oracle, and after 100 SSP-RK3 substeps the invariants that hold
+  against the oracle (error against the summand scale of the residual, which
+  on this smooth state is a strong cancellation), and after 100 SSP-RK3 substeps the invariants that hold
   at any size (mass conservation, non-increasing upwind energy) and the
   tensor-core path against the FP64 path;
 * the 3D workloads at full size (196608 and 663552 tetrahedra): invariants.
@@ -15,7 +16,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_common import make_case, maxrel, oracle_ds, oracle_state
+from gpu_common import TOL, make_case, maxrel, oracle_ds, oracle_state
 from oracle import dg as ODG
 from oracle import hdiv as OH
 from oracle import mesh as OM
@@ -119,10 +120,16 @@ def test_square256_conv_apply_sampled_against_oracle(square256):
     w = gm.transfer(u_n)
     sel = np.random.default_rng(0).choice(om.n_elem, size=300, replace=False)
     sel = np.unique(np.concatenate([sel, [0, 1, om.n_elem - 1]]))
-    ref = ODG.ConvectionOracle(om, wl.k, wind_o, sel=sel).apply(host(w))
-    for prec, tol in (("fp64", 1e-12), ("fp32", 1e-5), ("tf32x3", 1e-5)):
-        got = host(gm.conv_apply(wind, w, prec=prec))[sel]
-        assert maxrel(got, ref) < tol, prec
+    op = ODG.ConvectionOracle(om, wl.k, wind_o, sel=sel)
+    ref, scale = op.apply(host(w)), op.magnitude(host(w)).max()
+    # The state is smooth and h = 1/256: the volume and facet sums are each ~1/h
+    # times the residual (summand scale / max |r| is about 640 here), so the
+    # error of either evaluation is a rounding error of the summands and is
+    # measured against their scale (the forward-error bound of a sum).
+    assert scale > 100 * np.abs(ref).max()
+    for prec in ("fp64", "fp32", "tf32x3"):
+        got = host(gm.conv_apply(cu(wind_o), w, prec=prec))[sel]
+        assert np.abs(got - ref).max() < TOL[prec] * scale, prec
 
 
 def _mass_energy(gm, v):
@@ -142,12 +149,20 @@ def test_square256_rk_bench_configuration(square256):
     vtc = gm.transfer(u_n)
     gm.rk_substeps(wind, vtc, ds, wl.substeps, 3, "tf32x3")
     gm.check()
+    energies = []
     for v, mtol in ((v64, 1e-13), (vtc, 1e-6)):
         m1, s1, e1 = _mass_energy(gm, v)
         # the wind is tangential on the boundary: the total of each component is conserved
         assert np.all(np.abs(m1 - m0) < mtol * s0)
-        assert e1 <= e0 * (1 + 1e-12)
-    assert maxrel(host(vtc), host(v64)) < 1e-6
+        energies.append(e1)
+    # On this smooth state the upwind dissipation (jumps ~ h^(k+1)) and the
+    # damping of SSP-RK3 on the skew part ((lambda ds)^4 / 12 per substep) are
+    # below the tensor-core path's rounding; only the FP64 run can show the
+    # energy not increasing, and the tensor-core energy follows from its state error.
+    assert energies[0] <= e0 * (1 + 1e-12)
+    err = maxrel(host(vtc), host(v64))
+    assert err < 1e-6
+    assert abs(energies[1] - energies[0]) <= 3 * err * energies[0]
 
 
 @pytest.mark.parametrize("name,prec", [("cube32_k3", "fp32"), ("cube48_k4", "fp32")])

@@ -7,7 +7,9 @@
 * mass conservation when u.n = 0 on the boundary;
 * the mean mode of a piecewise-constant state is the textbook first-order
   upwind finite-volume residual (golden fixture, derived by hand);
-* linearity; consistency with u . grad w at the expected rate;
+* linearity; consistency with u . grad w at the expected rate; the summand
+  scale of the residual (a rounding-error scale) bounds it and grows like 1/h
+  relative to it on a smooth state;
 * an RK substep equals the Taylor polynomial of the assembled operator
   (SSP-RK2/3 are exact for linear autonomous ODEs up to their order);
   energy does not increase at CFL 0.2.
@@ -162,6 +164,33 @@ def test_consistency_rate_against_u_grad_w(k):
         errs.append(math.sqrt(np.sum(np.abs(mesh.detJ) * np.sum((r - target) ** 2, axis=1))))
     rate = math.log2(errs[0] / errs[1])
     assert rate > k - 0.6, (errs, rate)
+
+
+def test_summand_magnitude_bounds_and_scales_with_one_over_h():
+    """The summand scale bounds the residual entrywise, is absolutely homogeneous,
+    and for a fixed smooth state grows like 1/h over the residual (the volume and
+    facet parts each scale like |u| |w| / h while their sum stays ~ u . grad w)."""
+    def rot(x):
+        return 2 * np.pi * np.stack([-(x[:, 1] - 0.5), x[:, 0] - 0.5], axis=1)
+
+    k = 2
+    ratios = []
+    for n in (8, 16, 32):
+        mesh = OM.Mesh(*W.square_mesh(n, 0.0))
+        u = H.dofs_of_function(mesh, k, rot)
+        op = dg.ConvectionOracle(mesh, k, u)
+        xq, wq = simplex_rule(2, 2 * k + 6)
+        psi = B.dubiner_values(2, k, xq)
+        E = mesh.n_elem
+        X = mesh.to_physical(np.repeat(np.arange(E), len(wq)), np.tile(xq, (E, 1)))
+        vals = np.stack([np.sin(2 * X[:, 0] + X[:, 1]), np.cos(X[:, 0] - 3 * X[:, 1])], axis=1).reshape(E, -1, 2)
+        w = np.einsum("q,eqc,qi->eci", wq, vals, psi)
+        r, m = op.apply(w), op.magnitude(w)
+        assert np.all(np.abs(r) <= m * (1 + 1e-14))
+        assert np.allclose(op.magnitude(-3.0 * w), 3.0 * m, rtol=1e-14)
+        inner = np.all(mesh.nbr >= 0, axis=1)          # the zero inflow datum makes r ~ 1/h at the boundary
+        ratios.append(m[inner].max() / np.abs(r[inner]).max())
+    assert 1.6 < ratios[1] / ratios[0] < 2.4 and 1.6 < ratios[2] / ratios[1] < 2.4, ratios
 
 
 @pytest.mark.parametrize("scheme", [2, 3])
