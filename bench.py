@@ -18,6 +18,7 @@ host memory and g copied back inside the timed region.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -58,6 +59,31 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# several GPUs: one independent problem per rank (weak scaling, no data-path
+# collective); the step time of the job is the slowest rank's
+# ---------------------------------------------------------------------------
+def rank_workload(wl, rank: int):
+    """The workload of one rank: same sizes, its own seeds (rank 0 keeps the configured ones)."""
+    return wl if rank == 0 else dataclasses.replace(wl, seed=wl.seed + 7919 * rank)
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The maximum of a per-rank time over all ranks (an all-reduce on the default group)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step: float, world: int, ms_max: float) -> float:
+    """Whole-job units per second: all ranks' units over the slowest rank's step time."""
+    return world * units_per_rank_step / (ms_max * 1e-3)
 
 
 # ---------------------------------------------------------------------------
@@ -257,7 +283,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    wl = W.WORKLOADS[args.workload]
+    wl = rank_workload(W.WORKLOADS[args.workload], rank)
     substeps = args.substeps or wl.substeps
     mesh, wind, u_n, ds = make_inputs(wl, torch, dgconv)
     stream = torch.cuda.current_stream()
@@ -292,6 +318,8 @@ def main():
         step()
         ends[i].record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
     # stage-kernel duration: difference of two graph lengths cancels the per-call kernels
@@ -345,15 +373,12 @@ def main():
         torch.cuda.synchronize()
         err = float((vmx - v64).abs().max() / v64.abs().max())
 
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms), world, "cuda")
+    e2e_ms_max = max_over_ranks(statistics.mean(e2e_ms), world, "cuda")
     byts, flops, N = stage_bytes_flops(wl)
     units_per_step = wl.n_elem * N * wl.dim * 3 * substeps
-    value = world * units_per_step / (ms * 1e-3)
-    e2e_val = world * units_per_step / (statistics.mean(e2e_ms) * 1e-3)
+    value = job_throughput(units_per_step, world, ms)
+    e2e_val = job_throughput(units_per_step, world, e2e_ms_max)
     hbm, hbm_src = peaks()
     achieved = byts * wl.n_elem / (stage_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -405,8 +430,9 @@ def main():
             mesh.rk_substeps(wind, vp, ds, substeps, 3, prec)
             torch.cuda.synchronize()
             e_p = float((vp - v64).abs().max() / v64.abs().max())
-            others[prec] = {"value": world * units_per_step / (statistics.mean(ts) * 1e-3),
-                            "ms_per_step": statistics.mean(ts), "max_rel_err_vs_fp64": e_p}
+            ms_p = max_over_ranks(statistics.mean(ts), world, "cuda")
+            others[prec] = {"value": job_throughput(units_per_step, world, ms_p),
+                            "ms_per_step": ms_p, "max_rel_err_vs_fp64": e_p}
         line["other_precisions"] = others
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         runner = OracleRunner(wl)
