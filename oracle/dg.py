@@ -14,6 +14,9 @@ Definitions followed (Lehrenfeld & Schoeberl, arXiv:1508.04245):
 * Sec. 3.2.2: the propagation problem dv/ds + (M^V)^{-1} C^V v = 0 with a
   frozen wind; integrated here by SSP-RK2 (Heun) or SSP-RK3 (Shu-Osher)
   (reading A6).
+* Sec. 3.3.2: the implicit convection problem v + tau (M^V)^{-1} C^V v = g
+  of the modified fractional-step-theta scheme, solved by the pseudo-time
+  (Richardson) iteration (readings A9, A23, A24).
 * Sec. 2.4: the embedding I: W_h -> V_h through the L2 problem
   int (I u) v = int u v for all v in V_h, and its transpose I^T.
 
@@ -253,3 +256,50 @@ def max_wind_speed(mesh, k, u_hdiv) -> float:
 def cfl_ds(mesh, k, u_hdiv, cfl: float) -> float:
     """Substep size (reading A7): cfl * min_T h_T / ((2k+1) max |u|), h_T the shortest edge."""
     return cfl * float(mesh.shortest_edge().min()) / ((2 * k + 1) * max_wind_speed(mesh, k, u_hdiv))
+
+
+# ---------------------------------------------------------------------------------
+# implicit convection step by pseudo-time stepping (Sec. 3.3.2)
+# ---------------------------------------------------------------------------------
+def dg_norm(mesh, x) -> float:
+    """L2 norm of a DG function in the orthonormal basis: sqrt(sum_T |det J_T| sum_{c,i} x^2)."""
+    x = np.asarray(x)
+    return math.sqrt(float(np.sum(np.abs(mesh.detJ) * np.sum(x.reshape(x.shape[0], -1) ** 2, axis=1))))
+
+
+def richardson(op: ConvectionOracle, g, v0, tau: float, ds: float, reduction: float, max_iter: int):
+    """Solve v + tau (M^V)^{-1} C^V v = g (Sec. 3.3.2) by explicit Euler steps in
+    pseudo-time s of dv/ds + v + tau (M^V)^{-1} C^V v = g, i.e. the Richardson
+    iteration (reading A9 of the garbled sign)
+
+        rho_i = g - v_i - tau (M^V)^{-1} C^V v_i,     v_{i+1} = v_i + ds rho_i,
+
+    stopped at the first i with ||rho_i|| <= reduction ||rho_0|| or i = max_iter
+    (reading A23: the DG L2 norm ``dg_norm``).
+
+    Returns (v_i, i, [||rho_0||, ..., ||rho_i||]).
+    """
+    assert op.sel.size == op.mesh.n_elem
+    v = np.array(v0, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    history = []
+    i = 0
+    while True:
+        rho = g - v - tau * op.apply(v)
+        history.append(dg_norm(op.mesh, rho))
+        if history[-1] <= reduction * history[0] or i == max_iter:
+            return v, i, history
+        v = v + ds * rho
+        i += 1
+
+
+def richardson_ds(mesh, k, u_hdiv, tau: float) -> float:
+    """Pseudo-time step (reading A24): 1 / (1 + beta^2), beta = tau (2k+1) max|u| / min_T h_T.
+
+    The eigenvalues 1 + tau mu of Id + tau (M^V)^{-1} C^V have Re mu >= 0 (upwind
+    energy) and |Im mu| up to about (2k+1) max|u| / h; an explicit Euler step
+    ds contracts such a mode while ds < 2 Re(1 + tau mu) / |1 + tau mu|^2,
+    which 1 / (1 + beta^2) satisfies for Re mu = 0 and |Im mu| <= beta / tau.
+    """
+    beta = tau * (2 * k + 1) * max_wind_speed(mesh, k, u_hdiv) / float(mesh.shortest_edge().min())
+    return 1.0 / (1.0 + beta * beta)
