@@ -13,6 +13,8 @@
  *            mass matrix of an L2-orthonormal basis
  *   Q        explicit SSP Runge-Kutta substeps of the propagation problem
  *            dv/ds + (M^V)^-1 C^V(u) v = 0 with a frozen wind u   (Sec. 3.2.2)
+ *   (Id + tau M^-1 C)^-1   the implicit convection step, by pseudo-time
+ *            (Richardson) iteration                              (Sec. 3.3.2)
  *
  * Conventions shared by every call
  * --------------------------------
@@ -146,6 +148,29 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
                                  double* const* states, const double* ds, const int* nsteps, dgc_scheme scheme,
                                  dgc_prec prec, void* stream);
 
+/* Implicit convection step of the modified fractional-step-theta scheme
+ * (Sec. 3.3.2): solves  v + tau (M^V)^-1 C^V(u) v = g  by explicit Euler steps
+ * in pseudo-time (a Richardson iteration),
+ *   rho_i = g - v_i - tau (M^V)^-1 C^V v_i,     v_{i+1} = v_i + ds rho_i,
+ * stopped at the first i with ||rho_i|| <= reduction * ||rho_0|| or at
+ * i = max_iter; ||x|| = sqrt(sum_T |det J_T| sum x^2), the L2 norm of the DG
+ * function.  wind_hdiv: device [n_hdiv] (frozen u); g_dg: device [n_dg];
+ * v_dg: device [n_dg], FP64, in: v_0 (initial guess), out: the returned v_i;
+ * it must not overlap g_dg.  tau > 0 and ds in (0, 2) finite, reduction >= 0,
+ * max_iter >= 0.  iters_dev: device int32[1], receives i; res_dev: device
+ * [max_iter + 1] or NULL, receives ||rho_0|| .. ||rho_i|| (later entries
+ * untouched).  prec selects the precision of the operator evaluation as in
+ * dgc_conv_apply; residual, norm and update are FP64.  The iteration runs on
+ * the device (a CUDA graph with a conditional WHILE node, cached on the handle
+ * and replayed for identical arguments): nothing synchronizes, and iters_dev /
+ * res_dev are valid once `stream` reaches the end of the call.  A non-finite
+ * residual norm stops the iteration and makes the next dgc_check return
+ * DGC_ERR_NONFINITE.  A stable ds is 1 / (1 + beta^2) with
+ * beta = tau (2k+1) max|u| / (shortest edge). */
+dgc_status dgc_richardson(dgc_mesh* mesh, const double* wind_hdiv, const double* g_dg, double* v_dg, double tau,
+                          double ds, double reduction, int max_iter, dgc_prec prec, int32_t* iters_dev,
+                          double* res_dev, void* stream);
+
 /* Points at which callers evaluate input fields, host [count][dim]:
  * kind 0: the element-wise equispaced P^{k+1} Lagrange nodes used by
  *         dgc_wind_from_potential ([E][n_lagrange][dim]);
@@ -180,8 +205,9 @@ dgc_status dgc_project(dgc_mesh* mesh, const double* vals, double* w_dg, void* s
 dgc_status dgc_max_wind_speed(dgc_mesh* mesh, const double* wind_hdiv, double* out, void* stream);
 
 /* Device-side status of the handle: synchronizes `stream`, returns
- * DGC_ERR_TIMEOUT (and clears the word) if a bounded wait inside a kernel gave
- * up since the last check, DGC_OK otherwise. */
+ * DGC_ERR_TIMEOUT if a bounded wait inside a kernel gave up since the last
+ * check, else DGC_ERR_NONFINITE if dgc_richardson met a non-finite residual
+ * norm, else DGC_OK; a reported word is cleared. */
 dgc_status dgc_check(dgc_mesh* mesh, void* stream);
 
 /* Shortest element edge of the mesh (host value, from the upload). */

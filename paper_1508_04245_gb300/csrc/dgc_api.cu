@@ -117,6 +117,11 @@ struct dgc_mesh {
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   GraphKey graph_key{};
+  // pseudo-time solve: residual, operator output, norm partials, [norm0, i], its graph
+  DevBuf<double> rho, rop, partials, rstate;
+  cudaStream_t body_stream = nullptr;
+  cudaGraphExec_t rich_graph = nullptr;
+  std::vector<uint64_t> rich_key;
 
   DevMesh view() const {
     DevMesh m;
@@ -150,8 +155,13 @@ struct dgc_mesh {
   void release_all() {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
+    if (rich_graph) cudaGraphExecDestroy(rich_graph);
+    rich_graph = nullptr;
     if (capture_stream) cudaStreamDestroy(capture_stream);
     capture_stream = nullptr;
+    if (body_stream) cudaStreamDestroy(body_stream);
+    body_stream = nullptr;
+    for (auto* b : {&rho, &rop, &partials, &rstate}) b->release();
     for (auto* b : {&verts, &J, &detJ, &Bv, &wv, &wf, &Bf, &Cb, &Lg_int, &Lg_fac, &Tint, &wd, &wfd, &Qfd,
                     &Bd, &tab64, &Uw64, &Fw64, &stage1, &stage2, &zbuf})
       b->release();
@@ -368,6 +378,94 @@ dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, in
   return DGC_OK;
 }
 
+// out = (M^V)^-1 C^V w = -L(w) with the wind prepared for prec
+dgc_status apply_operator(dgc_mesh* m, dgc_prec prec, const double* w, double* out, cudaStream_t st) {
+  if (prec == DGC_TF32X3) {
+    if (dgc_status rc = tc_transpose_in(m, w, m->trA.ptr, st)) return rc;
+    // mode 2 with q = -1: v <- -L(w)
+    if (dgc_status rc = launch_stage_tc(m, 2, nullptr, m->trA.ptr, nullptr, nullptr, 0.0, -1.0, m->ts0.ptr, st))
+      return rc;
+    return tc_transpose_out(m, m->ts0.ptr, out, st);
+  }
+  return stage(m, prec, w, nullptr, out, 0.0, 0.0, -1.0, st);
+}
+
+// rho = g - v - tau A v with the norm partials, then the control kernel
+dgc_status rich_step(dgc_mesh* m, dgc_prec prec, const double* g, const double* v, double tau, double reduction,
+                     int max_iter, bool first, cudaGraphConditionalHandle h, int32_t* iters, double* res,
+                     cudaStream_t st) {
+  const long n = (long)m->E * m->s.D * m->s.N;
+  const int nb = dgc::rich_blocks(n);
+  if (dgc_status rc = apply_operator(m, prec, v, m->rop.ptr, st)) return rc;
+  DGC_CUDA(dgc::launch_rich_resid(g, v, m->rop.ptr, tau, m->rho.ptr, m->detJ.ptr, m->s.D * m->s.N, n,
+                                  m->partials.ptr, nb, st));
+  DGC_CUDA(dgc::launch_rich_control(m->partials.ptr, nb, m->rstate.ptr, iters, res, reduction, max_iter, first, h,
+                                    m->status.ptr, st));
+  return DGC_OK;
+}
+
+// Graph of the whole solve: wind, first residual and decision, then
+// WHILE(continue) { v += ds rho; residual; decision }.
+dgc_status rich_build(dgc_mesh* m, const double* wind, const double* g, double* v, double tau, double ds,
+                      double reduction, int max_iter, dgc_prec prec, int32_t* iters, double* res,
+                      cudaGraphExec_t* out) {
+  if (!m->capture_stream) DGC_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
+  if (!m->body_stream) DGC_CUDA(cudaStreamCreateWithFlags(&m->body_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = m->capture_stream, bs = m->body_stream;
+  const long n = (long)m->E * m->s.D * m->s.N;
+  DGC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t graph = nullptr;
+  dgc_status rc = DGC_OK;
+  cudaError_t err = cudaSuccess;
+  cudaGraphConditionalHandle h = 0;
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t cond;
+  do {
+    if ((err = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, nullptr, nullptr, nullptr)) != cudaSuccess) break;
+    if ((err = cudaGraphConditionalHandleCreate(&h, graph, 0, 0)) != cudaSuccess) break;
+    if ((rc = prepare_wind(m, prec, wind, cs))) break;
+    if ((rc = rich_step(m, prec, g, v, tau, reduction, max_iter, true, h, iters, res, cs))) break;
+    if ((err = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps)) != cudaSuccess) break;
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if ((err = cudaGraphAddNode(&cond, graph, deps, nullptr, ndeps, &cp)) != cudaSuccess) break;
+    if ((err = cudaStreamUpdateCaptureDependencies(cs, &cond, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+      break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((err = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+      break;
+    cudaError_t e1 = dgc::launch_rich_update(v, m->rho.ptr, ds, n, bs);
+    dgc_status rc1 = e1 == cudaSuccess ? rich_step(m, prec, g, v, tau, reduction, max_iter, false, h, iters, res, bs)
+                                       : DGC_OK;
+    cudaError_t e2 = cudaStreamEndCapture(bs, &body);
+    if (rc1) rc = rc1;
+    else if (e1 != cudaSuccess) err = e1;
+    else if (e2 != cudaSuccess) err = e2;
+  } while (false);
+  cudaGraph_t done = nullptr;
+  cudaError_t e3 = cudaStreamEndCapture(cs, &done);
+  if (rc != DGC_OK || err != cudaSuccess || e3 != cudaSuccess) {
+    if (done) cudaGraphDestroy(done);
+    if (rc != DGC_OK) return rc;
+    return fail(DGC_ERR_CUDA, "pseudo-time graph construction failed: %s",
+                cudaGetErrorString(err != cudaSuccess ? err : e3));
+  }
+  err = cudaGraphInstantiate(out, done, 0);
+  cudaGraphDestroy(done);
+  if (err != cudaSuccess) {
+    *out = nullptr;
+    return fail(DGC_ERR_CUDA, "pseudo-time graph instantiation failed: %s", cudaGetErrorString(err));
+  }
+  return DGC_OK;
+}
+
 }  // namespace
 
 namespace dgc {
@@ -548,15 +646,7 @@ dgc_status dgc_conv_apply(dgc_mesh* mesh, const double* wind_hdiv, const double*
   if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
   cudaStream_t st = as_stream(stream);
   if (dgc_status rc = prepare_wind(mesh, prec, wind_hdiv, st)) return rc;
-  // out = -L(w) = (M^V)^-1 C^V w
-  if (prec == DGC_TF32X3) {
-    if (dgc_status rc = tc_transpose_in(mesh, w_dg, mesh->trA.ptr, st)) return rc;
-    // mode 2 with q = -1: v <- -L(w) = (M^V)^-1 C^V w
-    if (dgc_status rc = launch_stage_tc(mesh, 2, nullptr, mesh->trA.ptr, nullptr, nullptr, 0.0, -1.0, mesh->ts0.ptr, st))
-      return rc;
-    return tc_transpose_out(mesh, mesh->ts0.ptr, out_dg, st);
-  }
-  return stage(mesh, prec, w_dg, nullptr, out_dg, 0.0, 0.0, -1.0, st);
+  return apply_operator(mesh, prec, w_dg, out_dg, st);
 }
 
 dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg, double ds, int nsteps,
@@ -596,6 +686,44 @@ dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg
     mesh->graph_key = key;
   }
   DGC_CUDA(cudaGraphLaunch(mesh->graph, st));
+  return DGC_OK;
+}
+
+dgc_status dgc_richardson(dgc_mesh* mesh, const double* wind_hdiv, const double* g_dg, double* v_dg, double tau,
+                          double ds, double reduction, int max_iter, dgc_prec prec, int32_t* iters_dev,
+                          double* res_dev, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (dgc_status rc = check_prec(mesh, prec)) return rc;
+  if (!wind_hdiv || !g_dg || !v_dg || !iters_dev) return fail(DGC_ERR_ARG, "NULL argument");
+  if (!(tau > 0.0) || !std::isfinite(tau)) return fail(DGC_ERR_ARG, "tau must be positive and finite (got %g)", tau);
+  if (!(ds > 0.0 && ds < 2.0)) return fail(DGC_ERR_ARG, "ds must lie in (0, 2) (got %g)", ds);
+  if (!(reduction >= 0.0) || !std::isfinite(reduction))
+    return fail(DGC_ERR_ARG, "reduction must be finite and >= 0 (got %g)", reduction);
+  if (max_iter < 0) return fail(DGC_ERR_ARG, "max_iter must be >= 0 (got %d)", max_iter);
+  const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
+  if (g_dg < v_dg + n && v_dg < g_dg + n) return fail(DGC_ERR_ARG, "v_dg overlaps g_dg");
+  if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
+  DGC_CUDA(mesh->rho.alloc(n));
+  DGC_CUDA(mesh->rop.alloc(n));
+  DGC_CUDA(mesh->partials.alloc((size_t)dgc::rich_blocks((long)n)));
+  DGC_CUDA(mesh->rstate.alloc(2));
+  std::vector<uint64_t> key = {(uint64_t)(uintptr_t)wind_hdiv, (uint64_t)(uintptr_t)g_dg, (uint64_t)(uintptr_t)v_dg,
+                               (uint64_t)(uintptr_t)iters_dev, (uint64_t)(uintptr_t)res_dev, (uint64_t)max_iter,
+                               (uint64_t)prec};
+  for (double x : {tau, ds, reduction}) {
+    uint64_t b;
+    std::memcpy(&b, &x, 8);
+    key.push_back(b);
+  }
+  if (!(mesh->rich_graph && mesh->rich_key == key)) {
+    if (mesh->rich_graph) cudaGraphExecDestroy(mesh->rich_graph);
+    mesh->rich_graph = nullptr;
+    if (dgc_status rc = rich_build(mesh, wind_hdiv, g_dg, v_dg, tau, ds, reduction, max_iter, prec, iters_dev,
+                                   res_dev, &mesh->rich_graph))
+      return rc;
+    mesh->rich_key = key;
+  }
+  DGC_CUDA(cudaGraphLaunch(mesh->rich_graph, as_stream(stream)));
   return DGC_OK;
 }
 
@@ -804,7 +932,8 @@ dgc_status dgc_check(dgc_mesh* mesh, void* stream) {
   if (word) {
     DGC_CUDA(cudaMemsetAsync(mesh->status.ptr, 0, sizeof(int), st));
     DGC_CUDA(cudaStreamSynchronize(st));
-    return fail(DGC_ERR_TIMEOUT, "a bounded device-side wait gave up (status word 0x%x)", word);
+    if (word & 2) return fail(DGC_ERR_TIMEOUT, "a bounded device-side wait gave up (status word 0x%x)", word);
+    return fail(DGC_ERR_NONFINITE, "non-finite residual norm in the pseudo-time iteration (status word 0x%x)", word);
   }
   return DGC_OK;
 }

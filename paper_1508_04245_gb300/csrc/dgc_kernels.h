@@ -73,4 +73,13 @@ cudaError_t launch_project(const DevMesh& m, const double* vals, double* w_dg, c
 cudaError_t launch_max_speed(const DevMesh& m, const double* u_hdiv, unsigned long long* out_bits,
                              cudaStream_t s);
 
+// pseudo-time (Richardson) solve: residual + deterministic norm partials, update, control
+int rich_blocks(long n);
+cudaError_t launch_rich_resid(const double* g, const double* v, const double* r, double tau, double* rho,
+                              const double* detJ, int DN, long n, double* partials, int nblocks, cudaStream_t s);
+cudaError_t launch_rich_update(double* v, const double* rho, double ds, long n, cudaStream_t s);
+cudaError_t launch_rich_control(const double* partials, int np, double* state, int* iters, double* res,
+                                double reduction, int max_iter, bool first, cudaGraphConditionalHandle h,
+                                int* status, cudaStream_t s);
+
 }  // namespace dgc

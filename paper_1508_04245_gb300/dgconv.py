@@ -34,6 +34,8 @@ SIGNATURES = {
     "dgc_mass_apply": [_vp, _vp, _vp, ctypes.c_int, _vp],
     "dgc_conv_apply": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp],
     "dgc_rk_substeps": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
+    "dgc_richardson": [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                       ctypes.c_int, _vp, _vp, _vp],
     "dgc_batch_rk_substeps": [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp],
     "dgc_point_coords": [_vp, ctypes.c_int, _vp, _i64p],
     "dgc_wind_from_potential": [_vp, _vp, _vp, _vp],
@@ -169,6 +171,30 @@ class Mesh:
         check(lib().dgc_rk_substeps(self._h, _ptr(wind, self.n_hdiv, "wind"), _ptr(v_dg, self.n_dg, "v_dg"),
                                     float(ds), int(nsteps), int(scheme), PREC[prec], _stream(stream)))
         return v_dg
+
+    def richardson(self, wind, g_dg, v_dg, tau: float, ds: float, reduction: float, max_iter: int, prec="fp64",
+                   iters=None, res=None, stream=None):
+        """Pseudo-time solve of v + tau (M^V)^-1 C^V v = g in place on v_dg (see dgc_richardson).
+
+        Returns the device tensors (iters int32[1], res float64[max_iter + 1]); read
+        them after the stream has reached the end of the call."""
+        import torch
+        if iters is None:
+            iters = torch.zeros(1, dtype=torch.int32, device=v_dg.device)
+        if res is None:
+            res = torch.zeros(max_iter + 1, dtype=torch.float64, device=v_dg.device)
+        if iters.dtype != torch.int32 or not iters.is_cuda or iters.numel() < 1:
+            raise TypeError("iters must be an int32 CUDA tensor with at least one entry")
+        check(lib().dgc_richardson(self._h, _ptr(wind, self.n_hdiv, "wind"), _ptr(g_dg, self.n_dg, "g_dg"),
+                                   _ptr(v_dg, self.n_dg, "v_dg"), float(tau), float(ds), float(reduction),
+                                   int(max_iter), PREC[prec], ctypes.c_void_p(iters.data_ptr()),
+                                   _ptr(res, max_iter + 1, "res"), _stream(stream)))
+        return iters, res
+
+    def richardson_ds(self, wind, tau: float) -> float:
+        """Pseudo-time step 1 / (1 + beta^2), beta = tau (2k+1) max|u| / min h_T (stable for every mode)."""
+        beta = tau * (2 * self.k + 1) * self.max_wind_speed(wind) / self.min_edge()
+        return 1.0 / (1.0 + beta * beta)
 
     # ---- inputs --------------------------------------------------------------
     def point_coords(self, kind: int) -> np.ndarray:
