@@ -434,6 +434,39 @@ def main():
             others[prec] = {"value": job_throughput(units_per_step, world, ms_p),
                             "ms_per_step": ms_p, "max_rel_err_vs_fp64": e_p}
         line["other_precisions"] = others
+    # the implicit convection step by pseudo-time iteration (Sec. 3.3.2): 20 capped
+    # Richardson iterations on the same mesh and wind, timed as one graph launch
+    rich_iters = 20
+    tau = 2.0 * mesh.cfl_ds(wind, 1.0)
+    ds_r = mesh.richardson_ds(wind, tau)
+    g_r = mesh.transfer(u_n)
+    v_r = mesh.dg_zeros()
+    it_r = torch.zeros(1, dtype=torch.int32, device="cuda")
+    res_r = torch.zeros(rich_iters + 1, dtype=torch.float64, device="cuda")
+    rich = {}
+    for prec in ("fp64", "fp32", "tf32x3"):
+        if prec == "tf32x3" and not (wl.dim == 2 and wl.k <= 4):
+            continue
+        ts = []
+        for rep in range(4):
+            v_r.zero_()
+            flush.zero_()
+            a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            mesh.richardson(wind, g_r, v_r, tau, ds_r, 0.0, rich_iters, prec=prec, iters=it_r, res=res_r)
+            b0.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:                                    # the first call builds the graph
+                ts.append(a0.elapsed_time(b0))
+        ms_it = max_over_ranks(min(ts), world, "cuda") / (rich_iters + 1)   # operator evaluations
+        rich[prec] = {"ms_per_iteration": ms_it,
+                      "value": job_throughput(wl.n_elem * N * wl.dim, world, ms_it),
+                      "roofline_frac": byts * wl.n_elem / (ms_it * 1e-3) / 1e9 / hbm,
+                      "residual_reduction": float(res_r[rich_iters] / res_r[0])}
+    line["richardson"] = {"unit": "DOF updates/s (one residual + update per iteration)", "iterations": rich_iters,
+                          "tau": tau, "ds": ds_r, "by_prec": rich,
+                          "note": "operator evaluations = iterations + 1; roofline against the same "
+                                  "algorithmic bytes per element as one stage"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         runner = OracleRunner(wl)
         rate, dt = runner.stages(3)

@@ -303,3 +303,49 @@ def richardson_ds(mesh, k, u_hdiv, tau: float) -> float:
     """
     beta = tau * (2 * k + 1) * max_wind_speed(mesh, k, u_hdiv) / float(mesh.shortest_edge().min())
     return 1.0 / (1.0 + beta * beta)
+
+
+# ---------------------------------------------------------------------------------
+# compositions on the H(div) side (Sec. 3.2, OIFS; Sec. 2.4)
+# ---------------------------------------------------------------------------------
+def extrapolation_coefs(j: int, ds: float, dt_prev: float):
+    """Weights (a, b) of u^n and u^{n-1} in the wind of substep j (reading A25): the
+    linear extrapolation u^n + theta (u^n - u^{n-1}) through the two previous
+    velocities (time levels t^n and t^n - dt_prev) evaluated at the substep's
+    midpoint t^n + (j + 1/2) ds, theta = (j + 1/2) ds / dt_prev."""
+    theta = (j + 0.5) * ds / dt_prev
+    return 1.0 + theta, -theta
+
+
+def oifs_rhs(mesh, k, u_hdiv, wind, ds: float, nsteps: int, scheme: int, wind_prev=None, dt_prev=None):
+    """The OIFS right-hand side M^{V,U} Q I u (Sec. 3.2): transfer u into V_h,
+    propagate it over nsteps substeps of the problem of Sec. 3.2.2 and map the
+    result back as a functional on W_h, I^T M^V (M^{V,U} = I^T M^V).
+
+    Without wind_prev the wind is frozen; with it, substep j uses the wind
+    extrapolated from (wind, wind_prev) to its midpoint (reading A25)."""
+    v = transfer(mesh, k, u_hdiv)
+    if wind_prev is None:
+        if nsteps > 0:
+            v = rk_substeps(ConvectionOracle(mesh, k, wind), v, ds, nsteps, scheme)
+    else:
+        for j in range(nsteps):
+            a, b = extrapolation_coefs(j, ds, dt_prev)
+            v = rk_substeps(ConvectionOracle(mesh, k, extrapolate([wind, wind_prev], [a, b])), v, ds, 1, scheme)
+    return transfer_T(mesh, k, mass(mesh, v))
+
+
+def conv_hdiv(op: ConvectionOracle, u_hdiv) -> np.ndarray:
+    """C^U u = I^T C^V I u, the convection operator on W_h (Sec. 2.4: C^U is the
+    Galerkin restriction of C^V through the embedding); C^V = M^V (M^V)^{-1} C^V."""
+    mesh, k = op.mesh, op.k
+    return transfer_T(mesh, k, mass(mesh, op.apply(transfer(mesh, k, u_hdiv))))
+
+
+def extrapolate(fields, coefs) -> np.ndarray:
+    """sum_j c_j u_j: the extrapolated convection velocity as a linear combination
+    of earlier exactly divergence-free velocities (Sec. 3.3)."""
+    out = np.zeros_like(np.asarray(fields[0], dtype=np.float64))
+    for f, c in zip(fields, coefs):
+        out = out + c * np.asarray(f, dtype=np.float64)
+    return out
