@@ -15,6 +15,8 @@
  *            dv/ds + (M^V)^-1 C^V(u) v = 0 with a frozen wind u   (Sec. 3.2.2)
  *   (Id + tau M^-1 C)^-1   the implicit convection step, by pseudo-time
  *            (Richardson) iteration                              (Sec. 3.3.2)
+ *   I^T M^V Q I, I^T C^V I   the OIFS right-hand side and the convection
+ *            operator on W_h, each as one call        (Sec. 3.2, Sec. 2.4)
  *
  * Conventions shared by every call
  * --------------------------------
@@ -170,6 +172,36 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
 dgc_status dgc_richardson(dgc_mesh* mesh, const double* wind_hdiv, const double* g_dg, double* v_dg, double tau,
                           double ds, double reduction, int max_iter, dgc_prec prec, int32_t* iters_dev,
                           double* res_dev, void* stream);
+
+/* The OIFS right-hand side M^{V,U} Q I u of Sec. 3.2 in one call:
+ *   out = I^T M^V Q I u,
+ * Q = nsteps SSP-RK substeps of size ds of the propagation problem (Sec. 3.2.2)
+ * as in dgc_rk_substeps.  The convection velocity is wind_hdiv, frozen, when
+ * wind_prev_hdiv is NULL; otherwise it is extrapolated linearly from wind_hdiv
+ * (time t^n) and wind_prev_hdiv (time t^n - dt_prev) to the midpoint of each
+ * substep, (1 + th_j) u^n - th_j u^{n-1} with th_j = (j + 1/2) ds / dt_prev,
+ * and frozen within the substep.  u_hdiv, wind_hdiv, wind_prev_hdiv: device
+ * [n_hdiv]; out_hdiv: device [n_hdiv], overwritten, must not overlap u_hdiv.
+ * nsteps >= 0 (0 gives I^T M^V I u), ds > 0, dt_prev > 0 with wind_prev_hdiv.
+ * The launch sequence is captured in a CUDA graph cached on the handle. */
+dgc_status dgc_oifs_rhs(dgc_mesh* mesh, const double* u_hdiv, const double* wind_hdiv, const double* wind_prev_hdiv,
+                        double dt_prev, double* out_hdiv, double ds, int nsteps, dgc_scheme scheme, dgc_prec prec,
+                        void* stream);
+
+/* The convection operator on W_h, C^U(u) w = I^T C^V(u) I w (Sec. 2.4), as one
+ * call: out_hdiv = I^T M^V ((M^V)^-1 C^V(wind)) I u_hdiv.  wind_hdiv, u_hdiv:
+ * device [n_hdiv]; out_hdiv: device [n_hdiv], overwritten, must not overlap
+ * u_hdiv; prec as in dgc_conv_apply. */
+dgc_status dgc_conv_apply_hdiv(dgc_mesh* mesh, const double* wind_hdiv, const double* u_hdiv, double* out_hdiv,
+                               dgc_prec prec, void* stream);
+
+/* Extrapolated convection velocity as a linear combination of earlier exactly
+ * divergence-free velocities (Sec. 3.2.2): out = sum_t coefs[t] fields[t].
+ * fields: host array of n_terms device pointers [n_hdiv]; coefs: host
+ * [n_terms]; 1 <= n_terms <= 8; out_hdiv: device [n_hdiv], may equal one of
+ * the fields (the combination is elementwise). */
+dgc_status dgc_wind_extrapolate(dgc_mesh* mesh, int n_terms, const double* const* fields, const double* coefs,
+                                double* out_hdiv, void* stream);
 
 /* Points at which callers evaluate input fields, host [count][dim]:
  * kind 0: the element-wise equispaced P^{k+1} Lagrange nodes used by

@@ -117,6 +117,10 @@ struct dgc_mesh {
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   GraphKey graph_key{};
+  // H(div)-side compositions: DG state, its mass image, the mixed wind, the OIFS graph
+  DevBuf<double> ov, omv, wmix;
+  cudaGraphExec_t oifs_graph = nullptr;
+  std::vector<uint64_t> oifs_key;
   // pseudo-time solve: residual, operator output, norm partials, [norm0, i], its graph
   DevBuf<double> rho, rop, partials, rstate;
   cudaStream_t body_stream = nullptr;
@@ -157,6 +161,9 @@ struct dgc_mesh {
     graph = nullptr;
     if (rich_graph) cudaGraphExecDestroy(rich_graph);
     rich_graph = nullptr;
+    if (oifs_graph) cudaGraphExecDestroy(oifs_graph);
+    oifs_graph = nullptr;
+    for (auto* b : {&ov, &omv, &wmix}) b->release();
     if (capture_stream) cudaStreamDestroy(capture_stream);
     capture_stream = nullptr;
     if (body_stream) cudaStreamDestroy(body_stream);
@@ -306,16 +313,43 @@ dgc_status tc_transpose_out(dgc_mesh* m, const double* vt, double* v, cudaStream
   return DGC_OK;
 }
 
+// The wind of the propagation: frozen (prev == nullptr, prepared once before the
+// substeps) or extrapolated linearly from (now, prev) to the midpoint of each
+// substep, theta_j = (j + 1/2) ds / dt_prev, wind_j = (1 + theta_j) now - theta_j prev.
+struct WindPlan {
+  const double* now = nullptr;
+  const double* prev = nullptr;
+  double dt_prev = 0.0;
+};
+
+dgc_status prepare_wind(dgc_mesh* m, dgc_prec prec, const double* wind, cudaStream_t st);
+
+dgc_status substep_wind(dgc_mesh* m, dgc_prec prec, const WindPlan& w, double ds, int j, cudaStream_t st) {
+  if (!w.prev) return DGC_OK;
+  const double theta = (j + 0.5) * ds / w.dt_prev;
+  dgc::CombineArgs a{};
+  a.x[0] = w.now;
+  a.x[1] = w.prev;
+  a.c[0] = 1.0 + theta;
+  a.c[1] = -theta;
+  a.nterms = 2;
+  const long n = (long)m->nF * m->s.NFM + (long)m->E * m->s.NINT;
+  DGC_CUDA(dgc::launch_combine(m->wmix.ptr, a, n, st));
+  return prepare_wind(m, prec, m->wmix.ptr, st);
+}
+
 // SSP-RK substeps on the tensor-core path, increment form: v^(i) = v^n + d_i,
 //   RK3: d1 = ds L(v),  d2 = d1/4 + ds/4 L(v + d1),  v += 2/3 d2 + 2/3 ds L(v + d2)
 //   RK2: d1 = ds L(v),  v += d1/2 + ds/2 L(v + d1)
 // (identical to the Shu-Osher / Heun forms); the state v is accumulated in FP64
 // once per substep, the increments are FP32.  ABI -> TSOA once, back at the end.
-dgc_status rk_sequence_tc(dgc_mesh* m, double* v, double ds, int nsteps, int scheme, cudaStream_t st) {
+dgc_status rk_sequence_tc(dgc_mesh* m, double* v, double ds, int nsteps, int scheme, const WindPlan& wp,
+                          cudaStream_t st) {
   float *cur = m->trA.ptr, *oth = m->trB.ptr;
   if (dgc_status rc = tc_transpose_in(m, v, cur, st)) return rc;
   for (int n = 0; n < nsteps; ++n) {
     dgc_status rc;
+    if ((rc = substep_wind(m, DGC_TF32X3, wp, ds, n, st))) return rc;
     if (scheme == DGC_SSPRK2) {
       if ((rc = launch_stage_tc(m, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr, st))) return rc;
       if ((rc = launch_stage_tc(m, 1, m->d1.ptr, oth, nullptr, cur, 0.5, 0.5 * ds, m->ts0.ptr, st))) return rc;
@@ -355,15 +389,22 @@ dgc_status ensure_prec_scratch(dgc_mesh* m, dgc_prec prec) {
   return ensure_wind_scratch(m, prec == DGC_FP32);
 }
 
-// The launch sequence of dgc_rk_substeps (also what gets captured).
+// The launch sequence of dgc_rk_substeps (also what gets captured); with
+// wind_prev the wind is extrapolated per substep (see WindPlan).
 dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, int nsteps, int scheme, dgc_prec prec,
-                       cudaStream_t st) {
-  if (dgc_status rc = prepare_wind(m, prec, wind, st)) return rc;
-  if (prec == DGC_TF32X3) return rk_sequence_tc(m, v, ds, nsteps, scheme, st);
+                       cudaStream_t st, const double* wind_prev = nullptr, double dt_prev = 0.0) {
+  WindPlan wp;
+  wp.now = wind;
+  wp.prev = wind_prev;
+  wp.dt_prev = dt_prev;
+  if (!wind_prev)
+    if (dgc_status rc = prepare_wind(m, prec, wind, st)) return rc;
+  if (prec == DGC_TF32X3) return rk_sequence_tc(m, v, ds, nsteps, scheme, wp, st);
   double* v1 = m->stage1.ptr;
   double* v2 = m->stage2.ptr;
   for (int n = 0; n < nsteps; ++n) {
     dgc_status rc;
+    if ((rc = substep_wind(m, prec, wp, ds, n, st))) return rc;
     if (scheme == DGC_SSPRK2) {
       // v1 = v + ds L(v);  v = 1/2 v + 1/2 (v1 + ds L(v1))
       if ((rc = stage(m, prec, v, nullptr, v1, 0.0, 1.0, ds, st))) return rc;
@@ -724,6 +765,108 @@ dgc_status dgc_richardson(dgc_mesh* mesh, const double* wind_hdiv, const double*
     mesh->rich_key = key;
   }
   DGC_CUDA(cudaGraphLaunch(mesh->rich_graph, as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_wind_extrapolate(dgc_mesh* mesh, int n_terms, const double* const* fields, const double* coefs,
+                                double* out_hdiv, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (n_terms < 1 || n_terms > dgc::kMaxTerms)
+    return fail(DGC_ERR_ARG, "n_terms must lie in 1..%d (got %d)", dgc::kMaxTerms, n_terms);
+  if (!fields || !coefs || !out_hdiv) return fail(DGC_ERR_ARG, "NULL argument");
+  dgc::CombineArgs a{};
+  for (int t = 0; t < n_terms; ++t) {
+    if (!fields[t]) return fail(DGC_ERR_ARG, "fields[%d] is NULL", t);
+    if (!std::isfinite(coefs[t])) return fail(DGC_ERR_ARG, "coefs[%d] is not finite", t);
+    a.x[t] = fields[t];
+    a.c[t] = coefs[t];
+  }
+  a.nterms = n_terms;
+  const long n = (long)mesh->nF * mesh->s.NFM + (long)mesh->E * mesh->s.NINT;
+  DGC_CUDA(dgc::launch_combine(out_hdiv, a, n, as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_conv_apply_hdiv(dgc_mesh* mesh, const double* wind_hdiv, const double* u_hdiv, double* out_hdiv,
+                               dgc_prec prec, void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (dgc_status rc = check_prec(mesh, prec)) return rc;
+  if (!wind_hdiv || !u_hdiv || !out_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
+  const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
+  const size_t nh = (size_t)mesh->nF * mesh->s.NFM + (size_t)mesh->E * mesh->s.NINT;
+  if (out_hdiv < u_hdiv + nh && u_hdiv < out_hdiv + nh) return fail(DGC_ERR_ARG, "out_hdiv overlaps u_hdiv");
+  if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
+  DGC_CUDA(mesh->ov.alloc(n));
+  DGC_CUDA(mesh->omv.alloc(n));
+  DGC_CUDA(mesh->rop.alloc(n));
+  DGC_CUDA(mesh->zbuf.alloc((size_t)mesh->E * mesh->s.NF * mesh->s.NFM));
+  cudaStream_t st = as_stream(stream);
+  // out = I^T M^V ((M^V)^-1 C^V) I u
+  DGC_CUDA(dgc::launch_transfer(mesh->view(), u_hdiv, mesh->ov.ptr, st));
+  if (dgc_status rc = prepare_wind(mesh, prec, wind_hdiv, st)) return rc;
+  if (dgc_status rc = apply_operator(mesh, prec, mesh->ov.ptr, mesh->rop.ptr, st)) return rc;
+  DGC_CUDA(dgc::launch_mass(mesh->view(), mesh->rop.ptr, mesh->omv.ptr, false, st));
+  DGC_CUDA(dgc::launch_transfer_T(mesh->view(), mesh->omv.ptr, out_hdiv, mesh->zbuf.ptr, st));
+  return DGC_OK;
+}
+
+dgc_status dgc_oifs_rhs(dgc_mesh* mesh, const double* u_hdiv, const double* wind_hdiv, const double* wind_prev_hdiv,
+                        double dt_prev, double* out_hdiv, double ds, int nsteps, dgc_scheme scheme, dgc_prec prec,
+                        void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (dgc_status rc = check_prec(mesh, prec)) return rc;
+  if (!u_hdiv || !wind_hdiv || !out_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
+  if (scheme != DGC_SSPRK2 && scheme != DGC_SSPRK3) return fail(DGC_ERR_ARG, "unknown scheme %d", (int)scheme);
+  if (nsteps < 0) return fail(DGC_ERR_ARG, "nsteps must be >= 0 (got %d)", nsteps);
+  if (!(ds > 0.0) || !std::isfinite(ds)) return fail(DGC_ERR_ARG, "ds must be positive and finite (got %g)", ds);
+  if (wind_prev_hdiv && (!(dt_prev > 0.0) || !std::isfinite(dt_prev)))
+    return fail(DGC_ERR_ARG, "dt_prev must be positive and finite with wind_prev (got %g)", dt_prev);
+  const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
+  const size_t nh = (size_t)mesh->nF * mesh->s.NFM + (size_t)mesh->E * mesh->s.NINT;
+  if (out_hdiv < u_hdiv + nh && u_hdiv < out_hdiv + nh) return fail(DGC_ERR_ARG, "out_hdiv overlaps u_hdiv");
+  if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
+  DGC_CUDA(mesh->stage1.alloc(n));
+  DGC_CUDA(mesh->stage2.alloc(n));
+  DGC_CUDA(mesh->ov.alloc(n));
+  DGC_CUDA(mesh->omv.alloc(n));
+  DGC_CUDA(mesh->wmix.alloc(nh));
+  DGC_CUDA(mesh->zbuf.alloc((size_t)mesh->E * mesh->s.NF * mesh->s.NFM));
+  uint64_t b_ds, b_dt;
+  std::memcpy(&b_ds, &ds, 8);
+  std::memcpy(&b_dt, &dt_prev, 8);
+  std::vector<uint64_t> key = {(uint64_t)(uintptr_t)u_hdiv, (uint64_t)(uintptr_t)wind_hdiv,
+                               (uint64_t)(uintptr_t)wind_prev_hdiv, (uint64_t)(uintptr_t)out_hdiv, b_ds,
+                               wind_prev_hdiv ? b_dt : 0u, (uint64_t)nsteps, (uint64_t)scheme, (uint64_t)prec};
+  if (!(mesh->oifs_graph && mesh->oifs_key == key)) {
+    if (mesh->oifs_graph) cudaGraphExecDestroy(mesh->oifs_graph);
+    mesh->oifs_graph = nullptr;
+    if (!mesh->capture_stream) DGC_CUDA(cudaStreamCreateWithFlags(&mesh->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = mesh->capture_stream;
+    DGC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    // a2: v = I u;  Q: nsteps substeps;  out = I^T M^V v
+    dgc_status rc = DGC_OK;
+    cudaError_t err = dgc::launch_transfer(mesh->view(), u_hdiv, mesh->ov.ptr, cs);
+    if (err == cudaSuccess && nsteps > 0)
+      rc = rk_sequence(mesh, wind_hdiv, mesh->ov.ptr, ds, nsteps, (int)scheme, prec, cs, wind_prev_hdiv, dt_prev);
+    if (err == cudaSuccess && rc == DGC_OK) err = dgc::launch_mass(mesh->view(), mesh->ov.ptr, mesh->omv.ptr, false, cs);
+    if (err == cudaSuccess && rc == DGC_OK)
+      err = dgc::launch_transfer_T(mesh->view(), mesh->omv.ptr, out_hdiv, mesh->zbuf.ptr, cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t err2 = cudaStreamEndCapture(cs, &g);
+    if (rc != DGC_OK || err != cudaSuccess || err2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (rc != DGC_OK) return rc;
+      return fail(DGC_ERR_CUDA, "OIFS graph capture failed: %s", cudaGetErrorString(err != cudaSuccess ? err : err2));
+    }
+    err = cudaGraphInstantiate(&mesh->oifs_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) {
+      mesh->oifs_graph = nullptr;
+      return fail(DGC_ERR_CUDA, "OIFS graph instantiation failed: %s", cudaGetErrorString(err));
+    }
+    mesh->oifs_key = key;
+  }
+  DGC_CUDA(cudaGraphLaunch(mesh->oifs_graph, as_stream(stream)));
   return DGC_OK;
 }
 

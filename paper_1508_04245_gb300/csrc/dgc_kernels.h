@@ -73,6 +73,15 @@ cudaError_t launch_project(const DevMesh& m, const double* vals, double* w_dg, c
 cudaError_t launch_max_speed(const DevMesh& m, const double* u_hdiv, unsigned long long* out_bits,
                              cudaStream_t s);
 
+// out = sum_t c[t] x[t] over n doubles
+constexpr int kMaxTerms = 8;
+struct CombineArgs {
+  const double* x[kMaxTerms];
+  double c[kMaxTerms];
+  int nterms;
+};
+cudaError_t launch_combine(double* out, const CombineArgs& a, long n, cudaStream_t s);
+
 // pseudo-time (Richardson) solve: residual + deterministic norm partials, update, control
 int rich_blocks(long n);
 cudaError_t launch_rich_resid(const double* g, const double* v, const double* r, double tau, double* rho,

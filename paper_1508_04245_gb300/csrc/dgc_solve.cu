@@ -1,4 +1,6 @@
-// Kernels of the pseudo-time (Richardson) solve of the implicit convection
+// Linear combinations of vectors (the extrapolated convection velocity of
+// Sec. 3.2.2 as a combination of earlier exactly divergence-free velocities),
+// and the kernels of the pseudo-time (Richardson) solve of the implicit convection
 // problem v + tau (M^V)^{-1} C^V v = g of the modified fractional-step-theta
 // scheme (Sec. 3.3.2):
 //
@@ -86,7 +88,23 @@ __global__ void __launch_bounds__(kBlock) rich_control_kernel(const double* __re
   cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
+// out = sum_t c_t x_t (up to kMaxTerms vectors; out may be one of the x_t)
+__global__ void __launch_bounds__(kBlock) combine_kernel(double* out, CombineArgs a, long n) {
+  for (long j = (long)blockIdx.x * kBlock + threadIdx.x; j < n; j += (long)gridDim.x * kBlock) {
+    double s = 0.0;
+    for (int t = 0; t < a.nterms; ++t) s += a.c[t] * a.x[t][j];
+    out[j] = s;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_combine(double* out, const CombineArgs& a, long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long b = (n + kBlock - 1) / kBlock;
+  combine_kernel<<<(unsigned)(b > 4096 ? 4096 : b), kBlock, 0, s>>>(out, a, n);
+  return cudaGetLastError();
+}
 
 int rich_blocks(long n) {
   long b = (n + kBlock * 4 - 1) / (kBlock * 4);

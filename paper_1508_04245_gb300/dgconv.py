@@ -36,6 +36,10 @@ SIGNATURES = {
     "dgc_rk_substeps": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
     "dgc_richardson": [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                        ctypes.c_int, _vp, _vp, _vp],
+    "dgc_oifs_rhs": [_vp, _vp, _vp, _vp, ctypes.c_double, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                     ctypes.c_int, _vp],
+    "dgc_conv_apply_hdiv": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp],
+    "dgc_wind_extrapolate": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp],
     "dgc_batch_rk_substeps": [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp],
     "dgc_point_coords": [_vp, ctypes.c_int, _vp, _i64p],
     "dgc_wind_from_potential": [_vp, _vp, _vp, _vp],
@@ -190,6 +194,34 @@ class Mesh:
                                    int(max_iter), PREC[prec], ctypes.c_void_p(iters.data_ptr()),
                                    _ptr(res, max_iter + 1, "res"), _stream(stream)))
         return iters, res
+
+    def oifs_rhs(self, u_hdiv, wind, ds: float, nsteps: int, scheme: int = 3, prec="fp64", wind_prev=None,
+                 dt_prev: float = 0.0, out=None, stream=None):
+        """out = I^T M^V Q I u with a frozen or extrapolated wind (see dgc_oifs_rhs)."""
+        out = self.hdiv_zeros() if out is None else out
+        wp = _ptr(wind_prev, self.n_hdiv, "wind_prev") if wind_prev is not None else None
+        check(lib().dgc_oifs_rhs(self._h, _ptr(u_hdiv, self.n_hdiv, "u_hdiv"), _ptr(wind, self.n_hdiv, "wind"), wp,
+                                 float(dt_prev), _ptr(out, self.n_hdiv, "out"), float(ds), int(nsteps), int(scheme),
+                                 PREC[prec], _stream(stream)))
+        return out
+
+    def conv_apply_hdiv(self, wind, u_hdiv, out=None, prec="fp64", stream=None):
+        """out = I^T C^V(wind) I u (see dgc_conv_apply_hdiv)."""
+        out = self.hdiv_zeros() if out is None else out
+        check(lib().dgc_conv_apply_hdiv(self._h, _ptr(wind, self.n_hdiv, "wind"), _ptr(u_hdiv, self.n_hdiv, "u_hdiv"),
+                                        _ptr(out, self.n_hdiv, "out"), PREC[prec], _stream(stream)))
+        return out
+
+    def wind_extrapolate(self, fields, coefs, out=None, stream=None):
+        """out = sum_t coefs[t] fields[t] over H(div) vectors (see dgc_wind_extrapolate)."""
+        out = self.hdiv_zeros() if out is None else out
+        n = len(fields)
+        if len(coefs) != n:
+            raise ValueError("fields and coefs differ in length")
+        hp = (ctypes.c_void_p * n)(*[_ptr(f, self.n_hdiv, "field").value for f in fields])
+        hc = (ctypes.c_double * n)(*[float(c) for c in coefs])
+        check(lib().dgc_wind_extrapolate(self._h, n, hp, hc, _ptr(out, self.n_hdiv, "out"), _stream(stream)))
+        return out
 
     def richardson_ds(self, wind, tau: float) -> float:
         """Pseudo-time step 1 / (1 + beta^2), beta = tau (2k+1) max|u| / min h_T (stable for every mode)."""
