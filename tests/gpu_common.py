@@ -12,6 +12,18 @@ from paper_1508_04245_gb300 import workloads as W
 TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 1e-5}
 
 
+def tol_hdiv_chain(dim, k, prec):
+    """Tolerance of outputs that pass through I and I^T (reading A26): in FP64
+    max(1e-12, 16 eps ||Cb||_inf), Cb the BDM_k dual-basis coefficients (each
+    transfer rounds at about eps ||Cb||_inf; two transfers, two independent
+    evaluations, slack 4 for the sum lengths); the mixed paths keep TOL."""
+    if prec != "fp64":
+        return TOL[prec]
+    from oracle import basis as B
+    cb = np.abs(np.asarray(B.bdm_element(dim, k), dtype=np.float64)).sum(axis=0).max()
+    return max(1e-12, 16 * np.finfo(np.float64).eps / 2 * cb)
+
+
 def tc_ok(dim, k):
     """The tensor-core (tf32x3) path covers triangles with k <= 4."""
     return dim == 2 and k <= 4

@@ -4,7 +4,7 @@ Sec. 3.2), C^U = I^T C^V I (Sec. 2.4) and the velocity extrapolation."""
 import numpy as np
 import pytest
 
-from gpu_common import TOL, make_case, maxrel, oracle_ds, tc_ok
+from gpu_common import TOL, make_case, maxrel, oracle_ds, tc_ok, tol_hdiv_chain
 from oracle import dg as ODG
 from oracle import hdiv as OH
 from paper_1508_04245_gb300 import build, dgconv
@@ -50,7 +50,7 @@ def test_conv_apply_hdiv(dim, k, n, seed, prec):
     ref = ODG.conv_hdiv(ODG.ConvectionOracle(om, k, wind), u)
     gm = dgconv.Mesh(dim, k, verts, elems)
     got = host(gm.conv_apply_hdiv(cu(wind), cu(u), prec=prec))
-    assert maxrel(got, ref) < TOL[prec]
+    assert maxrel(got, ref) < tol_hdiv_chain(dim, k, prec)
 
 
 @pytest.mark.parametrize("dim,k,n,seed", CASES)
@@ -67,7 +67,7 @@ def test_oifs_rhs(dim, k, n, seed, prec, extrapolated):
     gkw = dict(wind_prev=cu(wind2), dt_prev=3 * ds) if extrapolated else {}
     got = host(gm.oifs_rhs(cu(u), cu(wind), ds, 3, 3, prec=prec, **gkw))
     gm.check()
-    assert maxrel(got, ref) < TOL[prec]
+    assert maxrel(got, ref) < tol_hdiv_chain(dim, k, prec)
 
 
 def test_oifs_rhs_without_substeps_and_rk2():
