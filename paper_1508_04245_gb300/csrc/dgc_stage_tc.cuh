@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   float* blob = sm;
   float* wst = sm + L::oWst;
   float* op = sm + L::oOp;
+  float* stg = sm + L::oStg;                 // [vf | din] tile blocks, TSOA order (may alias op)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::SMEM_FLOATS);
   uint64_t* bar_tab = bars + 0;
   uint64_t* bar_w = bars + 1;
@@ -123,7 +124,8 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   uint64_t* bar_B = bars + 3;
   uint64_t* full = bars + 4;                 // NSLOT
   uint64_t* empty = bars + 4 + L::NSLOT;     // NSLOT
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4 + 2 * L::NSLOT);
+  uint64_t* bar_st = bars + 4 + 2 * L::NSLOT;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5 + 2 * L::NSLOT);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   // threads 0..255: (element row r of the tile, velocity component c); warps
@@ -136,18 +138,27 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   const int c = (t >> 7) & 1;
   const int issuer_t = 256;
   const int ntiles = (a.E + 127) / 128;
-  // the next tile's contiguous TSOA / TR blocks into L2 ahead of use
+  // issuer-side counts of bulk copies into the staging buffers (drained at exit)
+  uint32_t w_issued = 0, st_issued = 0;
+  // the next tile's contiguous TR block into L2 ahead of use
   auto prefetch_tile = [&](int tile) {
-    const uint32_t nst = 128u * 2 * N;        // values per tile in TSOA
     const uint32_t ntr = 128u * 2 * NF * NFM;  // values per tile in TR
-    tc::bulk_prefetch_l2(a.vf + (size_t)tile * nst, nst * 4);
-    if (a.din) tc::bulk_prefetch_l2(a.din + (size_t)tile * nst, nst * 4);
     tc::bulk_prefetch_l2(a.trin + (size_t)tile * ntr, ntr * 4);
   };
   auto load_wind = [&](int tile) {        // a tile's wind coefficients into the staging buffer
     const uint32_t bytes = (uint32_t)min(128, a.E - tile * 128) * 2 * NK * 4;
     tc::mbar_arrive_expect_tx(bar_w, bytes);
     tc::bulk_g2s(wst, a.wcoef + (size_t)tile * 128 * 2 * NK, bytes, bar_w);
+    ++w_issued;
+  };
+  // a tile's blocks of v^n (FP32 copy) and of the stage-input increment (TSOA vectors
+  // are allocated in whole tiles, so the blocks are complete and 16-byte aligned)
+  auto load_state = [&](int tile) {
+    const uint32_t blk = (uint32_t)L::TSOA_TILE * 4;
+    tc::mbar_arrive_expect_tx(bar_st, a.din ? 2 * blk : blk);
+    tc::bulk_g2s(stg, a.vf + (size_t)tile * L::TSOA_TILE, blk, bar_st);
+    if (a.din) tc::bulk_g2s(stg + L::TSOA_TILE, a.din + (size_t)tile * L::TSOA_TILE, blk, bar_st);
+    ++st_issued;
   };
 
   if (t == 0) {
@@ -155,6 +166,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     tc::mbar_init(bar_w, 1);
     tc::mbar_init(bar_A, 1);
     tc::mbar_init(bar_B, 1);
+    tc::mbar_init(bar_st, 1);
     for (int s = 0; s < L::NSLOT; ++s) {
       tc::mbar_init(full + s, 256);
       tc::mbar_init(empty + s, 1);
@@ -167,6 +179,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     tc::mbar_arrive_expect_tx(bar_tab, L::BLOB * 4);
     tc::bulk_g2s(blob, a.blob, L::BLOB * 4, bar_tab);
     load_wind(blockIdx.x);
+    load_state(blockIdx.x);
     prefetch_tile(blockIdx.x);
   }
   if (warp == 0) {
@@ -231,13 +244,14 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     const bool valid = e < a.E;
     const int next = tile + gridDim.x;
 
-    // ---- stage input v^n + din (coalesced TSOA loads) -> state operand of component c
+    // ---- stage input v^n + din (staged by bulk copy) -> state operand of component c
     if (producer) {
+    if (*abort_flag == 0 && !tc::mbar_wait(bar_st, it & 1)) *abort_flag = 1;
     float w[NP4];
 #pragma unroll
     for (int i = 0; i < NP4; ++i) {
-      const size_t ix = tsoa_index(e, c, i < N ? i : 0, N);
-      w[i] = (valid && i < N) ? a.vf[ix] + (a.din ? a.din[ix] : 0.f) : 0.f;
+      const int si = (c * N + (i < N ? i : 0)) * 128 + r;
+      w[i] = (valid && i < N) ? stg[si] + (a.din ? stg[L::TSOA_TILE + si] : 0.f) : 0.f;
     }
 #pragma unroll
     for (int k4 = 0; k4 < NK; k4 += 4) {
@@ -248,6 +262,9 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
       tc::st_shared_v4(op + (c * 2 + 0) * L::szOpA + o, h[0], h[1], h[2], h[3]);
       tc::st_shared_v4(op + (c * 2 + 1) * L::szOpA + o, tl[0], tl[1], tl[2], tl[3]);
     }
+    }   // producer
+    __syncthreads();   // the staged state has been read: its space takes the wind operands
+    if (producer) {
     // ---- wind operand of dimension d = c from the staged coefficients --------------
     if (*abort_flag == 0 && !tc::mbar_wait(bar_w, it & 1)) *abort_flag = 1;
 #pragma unroll
@@ -310,7 +327,11 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     // ---- issuer: next tile's inputs toward L2 (this tile's loads are done), then the
     //      GEMM B chunk MMAs as the producers fill the slots --------------------------
     if (!producer) {
-      if (t == issuer_t && next < ntiles) prefetch_tile(next);
+      if (t == issuer_t && next < ntiles && run2) {
+        tc::fence_proxy_async_smem();
+        load_state(next);   // GEMM A has read the wind operands that share this space
+        prefetch_tile(next);
+      }
       if (t == issuer_t && run2)
         for (int j = 0; j < L::NCH && *abort_flag == 0; ++j) issue_chunk(chunk_ctr + j, j);
     }
@@ -457,6 +478,11 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+  }
+  // bulk copies still in flight (only after a timeout) land before the CTA exits
+  if (t == issuer_t) {
+    if (st_issued) tc::mbar_wait(bar_st, (st_issued - 1) & 1);
+    if (w_issued) tc::mbar_wait(bar_w, (w_issued - 1) & 1);
   }
   tc::fence_before_sync();
   __syncthreads();

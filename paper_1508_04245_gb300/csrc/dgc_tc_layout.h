@@ -39,7 +39,7 @@ struct TcLayout2D {
   static constexpr int KB = KF + KV;
   static constexpr int NCH = KB / 8;                   // GEMM B K-chunks of 8
   static constexpr int NCHF = KF / 8;                  // of which facet chunks
-  static constexpr int NSLOT = 4;                      // GEMM B chunk buffers
+  static constexpr int NSLOT = 2;                      // GEMM B chunk buffers
 
   // TMEM columns (FP32 accumulators)
   static constexpr int cS = 0;                         // state fields, NAS each
@@ -61,8 +61,10 @@ struct TcLayout2D {
   static constexpr int oQt = oEf + szEf;
   static constexpr int BLOB = oQt + szQt;
 
-  // shared memory (floats): blob | wind staging | operand region
+  // shared memory (floats): blob | wind staging | operand region (| state staging)
   static constexpr int WSTAGE = 128 * D * NK;          // wind coefficients of the tile
+  static constexpr int TSOA_TILE = D * N * 128;        // one tile block of a TSOA vector
+  static constexpr int STG = 2 * TSOA_TILE;            // the tile's v^n (FP32) and stage increment
   static constexpr int szOpA = 128 * NK;               // one GEMM A operand part
   static constexpr int szChunk = 128 * 8;              // one GEMM B chunk operand part
   static constexpr int OPREG_A = 2 * D * 2 * szOpA;    // 4 fields x head/tail
@@ -70,7 +72,13 @@ struct TcLayout2D {
   static constexpr int OPREG = OPREG_A > OPREG_B ? OPREG_A : OPREG_B;
   static constexpr int oWst = BLOB;
   static constexpr int oOp = pad(oWst + WSTAGE, 32);   // 128-byte aligned
-  static constexpr int SMEM_FLOATS = oOp + OPREG;
+  // The tile's staged state lives in the wind-operand half of the GEMM A operands
+  // when the GEMM B ring fits in the state half: it is read before the wind
+  // operands are written and refilled for the next tile once GEMM A has completed.
+  static constexpr int HALF_A = 2 * 2 * szOpA;
+  static constexpr bool STG_ALIAS = OPREG_B <= HALF_A && STG <= HALF_A;
+  static constexpr int oStg = STG_ALIAS ? oOp + HALF_A : pad(oOp + OPREG, 32);
+  static constexpr int SMEM_FLOATS = STG_ALIAS ? oOp + OPREG : oStg + STG;
   static constexpr int SMEM_BYTES = SMEM_FLOATS * 4 + 256;   // + barriers
 
   static constexpr unsigned LBO = 128;
