@@ -1,5 +1,6 @@
-// Tensor-core stage kernel: host table blob (operand layout, head/tail TF32
-// split of the FP64 reference tables) and launcher, triangles k = 1..4.
+// Tensor-core stage kernel: host table blob (GEMM A operands with the head/tail
+// TF32 split of the FP64 reference tables, FP32 test tables) and launcher,
+// triangles k = 1..4.
 #include <cstring>
 #include <vector>
 
@@ -45,12 +46,9 @@ std::vector<float> blob_t(const Tables& t) {
     for (int q = 0; q < QF; ++q)
       for (int k = 0; k < N; ++k)
         put_split(b, L::oTAw, L::szTAw, QV + f * QF + q, k, L::SBO_NK, t.wf[q] * t.Bf[(f * QF + q) * N + k]);
-  for (int i = 0; i < N; ++i) {
-    for (int kk = 0; kk < L::NF * NFM; ++kk) put_split(b, L::oTB, L::szTB, i, kk, L::SBO_KB, t.Ef[kk * N + i]);
-    for (int q = 0; q < QV; ++q)
-      for (int dd = 0; dd < 2; ++dd)
-        put_split(b, L::oTB, L::szTB, i, L::KF + 2 * q + dd, L::SBO_KB, t.Gv[(q * N + i) * 2 + dd]);
-  }
+  for (int q = 0; q < QV; ++q)
+    for (int dd = 0; dd < 2; ++dd)
+      for (int i = 0; i < N; ++i) b[L::oG + (q * 2 + dd) * L::NP4 + i] = (float)t.Gv[(q * N + i) * 2 + dd];
   for (int fm = 0; fm < L::NF * NFM; ++fm)
     for (int i = 0; i < N; ++i) b[L::oEf + fm * L::NP4 + i] = (float)t.Ef[fm * N + i];
   for (int q = 0; q < QF; ++q)

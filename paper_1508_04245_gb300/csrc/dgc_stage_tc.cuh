@@ -1,30 +1,31 @@
-// Tensor-core RK stage kernel for triangles: steps a3-a7 with the two dense
-// contractions of the upwind DG operator on tcgen05 (kind::tf32, three-pass
+// Tensor-core RK stage kernel for triangles: steps a3-a7 of the upwind DG
+// operator with its dense contraction on tcgen05 (kind::tf32, three-pass
 // head/tail split, FP32 accumulation in TMEM) and the FP64 stage combination.
 //
 // Per tile of 128 elements (one CTA, 256 threads: thread (r, c) handles
 // velocity component c of element r; element r = GEMM row r = TMEM lane r):
-//   1. bulk copies (TMA) bring the table blob and the tile's wind
-//      coefficients into shared memory; every thread loads its element's FP64
-//      state and writes the head/tail TF32 operands of the state fields;
+//   1. the tile's FP32 state and stage-input increment and its wind
+//      coefficients arrive in shared memory by bulk copies (TMA) issued one
+//      tile ahead; every thread writes the head/tail TF32 operands of its
+//      state component and of one wind component;
 //   2. GEMM A (one issuing thread): state and wind evaluated at the volume
 //      points, the wind also at the facet points (weights and 1/det J folded
 //      into the wind's table and coefficients);
-//   3. CUDA cores, per element: own and neighbour facet traces on the facet
-//      basis (the neighbour's from its FP64 state), upwind selection at the
-//      facet points by the sign of (1/det J) w_q (u^ . -grad lambda_f),
-//      projection back onto the facet basis (Sec. 2.3 upwind flux);
-//   4. GEMM B in K-chunks of 8 through a 4-slot shared-memory ring: the
-//      threads produce -Uw w_c(xi_q) products and the facet projections, one
-//      thread issues the MMAs as chunks fill;
-//   5. epilogue: r from TMEM, vout = alpha vn + beta vin - gamma r in FP64.
+//   3. CUDA cores, per element and component, in FP32: own and neighbour
+//      facet traces on the facet basis (from the trace buffer), upwind
+//      selection at the facet points by the sign of (1/det J) w_q (u^ .
+//      -grad lambda_f), projection back onto the facet basis and restriction
+//      to the element basis (Sec. 2.3 upwind flux); then the volume term,
+//      products -(1/det J) w_q u^_d w_c(xi_q) against the basis gradients;
+//   4. epilogue: the stage increment, in the last stage of a substep the FP64
+//      state accumulation, and the facet traces of the stage output.
 // The kernel is persistent (two CTAs per SM loop over tiles): the tables are
-// loaded once per CTA and the next tile's wind block is bulk-copied as soon as
-// the staging buffer is free.  State vectors use a tile-blocked SoA layout
-// (TSOA) so every warp access is coalesced, and each stage writes the facet
-// traces of its output (TR) for the next stage, which reads its own and its
-// neighbours' traces instead of recomputing them from FP64 coefficients.  Every mbarrier wait is bounded; a timeout sets bit 1
-// of the status word and the CTA stops (TMEM is still released).
+// loaded once per CTA.  State vectors use a tile-blocked SoA layout (TSOA) so
+// every warp access is coalesced, and each stage writes the facet traces of
+// its output (TR) for the next stage, which reads its own and its neighbours'
+// traces instead of recomputing them from the coefficients.  Every mbarrier
+// wait is bounded; a timeout sets bit 1 of the status word and the CTA stops
+// (its bulk copies are drained and TMEM is still released).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -116,16 +117,15 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   float* blob = sm;
   float* wst = sm + L::oWst;
   float* op = sm + L::oOp;
-  float* stg = sm + L::oStg;                 // [vf | din] tile blocks, TSOA order (may alias op)
+  float* stg = sm + L::oStg;                 // next tile's [vf | din] (wind half of op)
+  float* epi = sm + L::oEpi;                 // this tile's [vf | din] (state half of op)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::SMEM_FLOATS);
   uint64_t* bar_tab = bars + 0;
   uint64_t* bar_w = bars + 1;
   uint64_t* bar_A = bars + 2;
-  uint64_t* bar_B = bars + 3;
-  uint64_t* full = bars + 4;                 // NSLOT
-  uint64_t* empty = bars + 4 + L::NSLOT;     // NSLOT
-  uint64_t* bar_st = bars + 4 + 2 * L::NSLOT;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5 + 2 * L::NSLOT);
+  uint64_t* bar_st = bars + 3;
+  uint64_t* bar_ep = bars + 4;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   // threads 0..255: (element row r of the tile, velocity component c); warps
@@ -138,8 +138,11 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   const int c = (t >> 7) & 1;
   const int issuer_t = 256;
   const int ntiles = (a.E + 127) / 128;
+  // the epilogue reads the stage-input increment (modes 0, 1) and v^n (mode 0)
+  const bool epi_din = a.din != nullptr;
+  const bool epi_vf = a.mode == 0;
   // issuer-side counts of bulk copies into the staging buffers (drained at exit)
-  uint32_t w_issued = 0, st_issued = 0;
+  uint32_t w_issued = 0, st_issued = 0, ep_issued = 0;
   // the next tile's contiguous TR block into L2 ahead of use
   auto prefetch_tile = [&](int tile) {
     const uint32_t ntr = 128u * 2 * NF * NFM;  // values per tile in TR
@@ -151,26 +154,21 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     tc::bulk_g2s(wst, a.wcoef + (size_t)tile * 128 * 2 * NK, bytes, bar_w);
     ++w_issued;
   };
-  // a tile's blocks of v^n (FP32 copy) and of the stage-input increment (TSOA vectors
-  // are allocated in whole tiles, so the blocks are complete and 16-byte aligned)
-  auto load_state = [&](int tile) {
-    const uint32_t blk = (uint32_t)L::TSOA_TILE * 4;
-    tc::mbar_arrive_expect_tx(bar_st, a.din ? 2 * blk : blk);
-    tc::bulk_g2s(stg, a.vf + (size_t)tile * L::TSOA_TILE, blk, bar_st);
-    if (a.din) tc::bulk_g2s(stg + L::TSOA_TILE, a.din + (size_t)tile * L::TSOA_TILE, blk, bar_st);
-    ++st_issued;
+  // a tile's blocks of v^n (FP32 copy) and of the stage-input increment into dst
+  // (TSOA vectors are allocated in whole tiles: complete, 16-byte aligned blocks)
+  const uint32_t blk = (uint32_t)L::TSOA_TILE * 4;
+  auto load_state = [&](float* dst, uint64_t* bar, int tile, bool vf, bool din) {
+    tc::mbar_arrive_expect_tx(bar, (vf ? blk : 0u) + (din ? blk : 0u));
+    if (vf) tc::bulk_g2s(dst, a.vf + (size_t)tile * L::TSOA_TILE, blk, bar);
+    if (din) tc::bulk_g2s(dst + L::TSOA_TILE, a.din + (size_t)tile * L::TSOA_TILE, blk, bar);
   };
 
   if (t == 0) {
     tc::mbar_init(bar_tab, 1);
     tc::mbar_init(bar_w, 1);
     tc::mbar_init(bar_A, 1);
-    tc::mbar_init(bar_B, 1);
     tc::mbar_init(bar_st, 1);
-    for (int s = 0; s < L::NSLOT; ++s) {
-      tc::mbar_init(full + s, 256);
-      tc::mbar_init(empty + s, 1);
-    }
+    tc::mbar_init(bar_ep, 1);
     *abort_flag = 0;
     tc::mbar_fence_init();
   }
@@ -179,7 +177,8 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     tc::mbar_arrive_expect_tx(bar_tab, L::BLOB * 4);
     tc::bulk_g2s(blob, a.blob, L::BLOB * 4, bar_tab);
     load_wind(blockIdx.x);
-    load_state(blockIdx.x);
+    load_state(stg, bar_st, blockIdx.x, true, epi_din);
+    ++st_issued;
     prefetch_tile(blockIdx.x);
   }
   if (warp == 0) {
@@ -192,51 +191,11 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   const uint32_t tbase = *tslot;
   const uint32_t lane_base = tbase + ((uint32_t)((warp & 3) * 32) << 16);
   if (!tc::mbar_wait(bar_tab, 0)) *abort_flag = 1;
+  const float* G = blob + L::oG;     // [QV][2][NP4]
   const float* Ef = blob + L::oEf;   // [NF][NFM][NP4]
   const float* Qt = blob + L::oQt;   // [QF][NFM4]
   const uint32_t op_s = tc::smem_u32(op);
   const uint32_t bl_s = tc::smem_u32(blob);
-  const uint32_t tb_s = tc::smem_u32(blob + L::oTB);
-  const uint32_t idescB = tc::idesc_tf32(128, L::NB);
-  uint32_t chunk_ctr = 0;
-
-  // thread 0: wait until chunk g's slot is full, issue its MMAs, release the slot
-  auto issue_chunk = [&](uint32_t g, int j) {
-    const int s = (int)(g % L::NSLOT);
-    if (!tc::mbar_wait(full + s, (g / L::NSLOT) & 1)) {
-      *abort_flag = 1;
-      return;
-    }
-    tc::fence_after_sync();
-    const uint32_t sl = op_s + 4u * (s * 2 * 2 * L::szChunk);
-    for (int cc = 0; cc < 2; ++cc)
-      for (int pass = 0; pass < 3; ++pass) {
-        const uint32_t a_op = sl + 4u * ((cc * 2 + (pass == 2 ? 1 : 0)) * L::szChunk);
-        const uint32_t b_op = tb_s + (pass == 1 ? 4u * L::szTB : 0u) + j * 2 * L::LBO;
-        tc::mma_tf32(tbase + L::cB + cc * L::NB, tc::smem_desc(a_op, L::LBO, L::SBO_CH),
-                     tc::smem_desc(b_op, L::LBO, L::SBO_KB), idescB, (j > 0 || pass > 0) ? 1u : 0u);
-      }
-    tc::mma_commit(empty + s);
-    if (j == L::NCH - 1) tc::mma_commit(bar_B);
-  };
-  // every thread: wait until chunk g's slot is free again
-  auto claim_chunk = [&](uint32_t g) -> float* {
-    const int s = (int)(g % L::NSLOT);
-    const uint32_t use = g / L::NSLOT;
-    if (use > 0 && *abort_flag == 0 && !tc::mbar_wait(empty + s, (use - 1) & 1)) *abort_flag = 1;
-    return op + s * (2 * 2 * L::szChunk) + c * 2 * L::szChunk;
-  };
-  // head / tail of 4 consecutive K values of this thread's row into a chunk operand
-  auto store4 = [&](float* slot, int k4, float v0, float v1, float v2, float v3) {
-    float h[4], tl[4];
-    tcimpl::split(v0, h[0], tl[0]);
-    tcimpl::split(v1, h[1], tl[1]);
-    tcimpl::split(v2, h[2], tl[2]);
-    tcimpl::split(v3, h[3], tl[3]);
-    const uint32_t o = tc::kmajor_off32(r, k4, L::LBO, L::SBO_CH) / 4;
-    tc::st_shared_v4(slot + o, h[0], h[1], h[2], h[3]);
-    tc::st_shared_v4(slot + L::szChunk + o, tl[0], tl[1], tl[2], tl[3]);
-  };
 
   int it = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -251,7 +210,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
 #pragma unroll
     for (int i = 0; i < NP4; ++i) {
       const int si = (c * N + (i < N ? i : 0)) * 128 + r;
-      w[i] = (valid && i < N) ? stg[si] + (a.din ? stg[L::TSOA_TILE + si] : 0.f) : 0.f;
+      w[i] = (valid && i < N) ? stg[si] + (epi_din ? stg[L::TSOA_TILE + si] : 0.f) : 0.f;
     }
 #pragma unroll
     for (int k4 = 0; k4 < NK; k4 += 4) {
@@ -324,26 +283,28 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     tc::fence_after_sync();
     __syncthreads();
     const bool run2 = *abort_flag == 0;
-    // ---- issuer: next tile's inputs toward L2 (this tile's loads are done), then the
-    //      GEMM B chunk MMAs as the producers fill the slots --------------------------
-    if (!producer) {
-      if (t == issuer_t && next < ntiles && run2) {
-        tc::fence_proxy_async_smem();
-        load_state(next);   // GEMM A has read the wind operands that share this space
+    // ---- issuer: GEMM A has read both operand halves: this tile's state for the
+    //      epilogue into the state half, the next tile's into the wind half ---------
+    if (t == issuer_t && run2) {
+      tc::fence_proxy_async_smem();
+      if (epi_vf || epi_din) {
+        load_state(epi, bar_ep, tile, epi_vf, epi_din);
+        ++ep_issued;
+      }
+      if (next < ntiles) {
+        load_state(stg, bar_st, next, true, epi_din);
+        ++st_issued;
         prefetch_tile(next);
       }
-      if (t == issuer_t && run2)
-        for (int j = 0; j < L::NCH && *abort_flag == 0; ++j) issue_chunk(chunk_ctr + j, j);
     }
 
-    // ---- facets: upwind flux at the facet points, projection (chunks 0 .. NCHF-1) ---
+    // ---- test contractions on CUDA cores (FP32): r_i = facet part + volume part ------
+    float rr[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) rr[i] = 0.f;
     if (run2 && producer) {
-      float* fslot[L::NCHF];
-#pragma unroll
-      for (int j = 0; j < L::NCHF; ++j) fslot[j] = claim_chunk(chunk_ctr + j);
-      float phi[L::KF];
-#pragma unroll
-      for (int j = 0; j < L::KF; ++j) phi[j] = 0.f;
+      // facets: upwind flux at the facet points, projected onto the facet basis, then
+      // r_i += sum_{f,m} Ef[f][m][i] phi[f][m]
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         // wind at this facet's points: (1/det J) w_q u^_dd, columns QV + f QF + q
@@ -361,6 +322,9 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
           u1[q] = __uint_as_float(x1);
         }
         tc::tmem_wait_ld();
+        float phi[NFM];
+#pragma unroll
+        for (int m = 0; m < NFM; ++m) phi[m] = 0.f;
 #pragma unroll
         for (int q = 0; q < QF; ++q) {
           // -grad lambda_0 = (1,1), -grad lambda_1 = (-1,0), -grad lambda_2 = (0,-1)
@@ -382,69 +346,63 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
           }
           const float val = valid ? fw * (fw >= 0.f ? o : nb) : 0.f;
 #pragma unroll
-          for (int m = 0; m < NFM; ++m) phi[f * NFM + m] += qq[m] * val;
+          for (int m = 0; m < NFM; ++m) phi[m] += qq[m] * val;
+        }
+#pragma unroll
+        for (int m = 0; m < NFM; ++m) {
+          const float* Er = Ef + (f * NFM + m) * NP4;
+#pragma unroll
+          for (int i4 = 0; i4 < NP4; i4 += 4) {
+            const float4 y = *reinterpret_cast<const float4*>(Er + i4);
+            if (i4 + 0 < N) rr[i4 + 0] = fmaf(y.x, phi[m], rr[i4 + 0]);
+            if (i4 + 1 < N) rr[i4 + 1] = fmaf(y.y, phi[m], rr[i4 + 1]);
+            if (i4 + 2 < N) rr[i4 + 2] = fmaf(y.z, phi[m], rr[i4 + 2]);
+            if (i4 + 3 < N) rr[i4 + 3] = fmaf(y.w, phi[m], rr[i4 + 3]);
+          }
         }
       }
-#pragma unroll
-      for (int j = 0; j < L::NCHF; ++j) {
-        store4(fslot[j], 0, phi[8 * j], phi[8 * j + 1], phi[8 * j + 2], phi[8 * j + 3]);
-        store4(fslot[j], 4, phi[8 * j + 4], phi[8 * j + 5], phi[8 * j + 6], phi[8 * j + 7]);
-        tc::fence_proxy_async_smem();
-        tcimpl::mbar_arrive(full + (chunk_ctr + j) % L::NSLOT);
-      }
 
-      // ---- volume chunks, in pairs sharing one TMEM load of 8 volume points --------
-      constexpr int NCHV = L::NCH - L::NCHF;
+      // volume: r_i -= sum_q sum_d (Uw[q][d] w_c(xi_q)) G[q][d][i], 8 points per TMEM load
 #pragma unroll 1
-      for (int jp = 0; jp < NCHV; jp += 2) {
-        const int q0 = jp * 4;
+      for (int q0 = 0; q0 < QV; q0 += 8) {
         float wq[8], uq0[8], uq1[8];
         tcimpl::tmem_load<8>(lane_base + L::cS + c * L::NAS + q0, wq);
         tcimpl::tmem_load<8>(lane_base + L::cW + q0, uq0);
         tcimpl::tmem_load<8>(lane_base + L::cW + L::NAW + q0, uq1);
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-          const int jv = jp + h2;
-          if (jv >= NCHV) break;
-          const int j = L::NCHF + jv;
-          float* slot = claim_chunk(chunk_ctr + j);
-          float v[8];
+        for (int ql = 0; ql < 8; ++ql) {
+          if (q0 + ql >= QV) break;
+          const float p0 = valid ? -uq0[ql] * wq[ql] : 0.f;
+          const float p1 = valid ? -uq1[ql] * wq[ql] : 0.f;
+          const float* Gq = G + (q0 + ql) * 2 * NP4;
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const int ql = h2 * 4 + kk / 2;
-            const float u = (kk & 1) ? uq1[ql] : uq0[ql];
-            v[kk] = (q0 + ql < QV && valid) ? -u * wq[ql] : 0.f;
+          for (int i4 = 0; i4 < NP4; i4 += 4) {
+            const float4 g0 = *reinterpret_cast<const float4*>(Gq + i4);
+            const float4 g1 = *reinterpret_cast<const float4*>(Gq + NP4 + i4);
+            if (i4 + 0 < N) rr[i4 + 0] = fmaf(p1, g1.x, fmaf(p0, g0.x, rr[i4 + 0]));
+            if (i4 + 1 < N) rr[i4 + 1] = fmaf(p1, g1.y, fmaf(p0, g0.y, rr[i4 + 1]));
+            if (i4 + 2 < N) rr[i4 + 2] = fmaf(p1, g1.z, fmaf(p0, g0.z, rr[i4 + 2]));
+            if (i4 + 3 < N) rr[i4 + 3] = fmaf(p1, g1.w, fmaf(p0, g0.w, rr[i4 + 3]));
           }
-          store4(slot, 0, v[0], v[1], v[2], v[3]);
-          store4(slot, 4, v[4], v[5], v[6], v[7]);
-          tc::fence_proxy_async_smem();
-          tcimpl::mbar_arrive(full + (chunk_ctr + j) % L::NSLOT);
         }
       }
     }
-    chunk_ctr += L::NCH;
 
     // ---- epilogue: increment, FP64 accumulation (mode 1), output traces --------------
-    // operands of the epilogue are loaded before waiting on GEMM B
-    float ed[N], ev[N];
     double ex[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const size_t ix = tsoa_index(e, c, i, N);
-      ed[i] = (producer && valid && a.din) ? a.din[ix] : 0.f;
-      ev[i] = (producer && valid && a.mode == 0) ? a.vf[ix] : 0.f;
-      ex[i] = (producer && valid && a.mode == 1) ? a.v[ix] : 0.0;
-    }
-    if (producer && run2 && *abort_flag == 0 && !tc::mbar_wait(bar_B, it & 1)) *abort_flag = 1;
-    tc::fence_after_sync();
+    for (int i = 0; i < N; ++i)
+      ex[i] = (producer && valid && a.mode == 1) ? a.v[tsoa_index(e, c, i, N)] : 0.0;
+    if (producer && run2 && (epi_vf || epi_din) && *abort_flag == 0 && !tc::mbar_wait(bar_ep, it & 1))
+      *abort_flag = 1;
+    tc::fence_before_sync();
     __syncthreads();
+    tc::fence_after_sync();
     const bool fin = run2 && *abort_flag == 0;   // uniform after the barrier
     if (!fin) {
       if (t == 0) atomicOr(a.status, 2);   // a bounded wait gave up: this CTA stops
       break;
     }
-    float rr[L::NB];
-    if (producer) tcimpl::tmem_load<L::NB>(lane_base + L::cB + c * L::NB, rr);
     if (producer && valid) {
       // inc = p din + q L, L = -r (r carries FP32 accuracy)
       float xo[NP4];
@@ -453,10 +411,12 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const size_t ix = tsoa_index(e, c, i, N);
-        const float inc = fmaf(a.p, ed[i], -a.q * rr[i]);
+        const int si = (c * N + i) * 128 + r;
+        const float ed = epi_din ? epi[L::TSOA_TILE + si] : 0.f;
+        const float inc = fmaf(a.p, ed, -a.q * rr[i]);
         if (a.mode == 0) {
           a.dout[ix] = inc;
-          xo[i] = ev[i] + inc;
+          xo[i] = epi[si] + inc;
         } else if (a.mode == 1) {
           const double x = ex[i] + tc::f32_to_f64(inc);   // FP64 state accumulation
           a.v[ix] = x;
@@ -482,6 +442,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   // bulk copies still in flight (only after a timeout) land before the CTA exits
   if (t == issuer_t) {
     if (st_issued) tc::mbar_wait(bar_st, (st_issued - 1) & 1);
+    if (ep_issued) tc::mbar_wait(bar_ep, (ep_issued - 1) & 1);
     if (w_issued) tc::mbar_wait(bar_w, (w_issued - 1) & 1);
   }
   tc::fence_before_sync();
