@@ -299,9 +299,11 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     }
 
     // ---- test contractions on CUDA cores (FP32): r_i = facet part + volume part ------
-    float rr[N];
+    // r is held as packed pairs (i = 2j, 2j + 1); the tables' padding rows are zero
+    constexpr int NP2 = NP4 / 2;
+    unsigned long long r2[NP2];
 #pragma unroll
-    for (int i = 0; i < N; ++i) rr[i] = 0.f;
+    for (int j = 0; j < NP2; ++j) r2[j] = 0ull;
     if (run2 && producer) {
       // facets: upwind flux at the facet points, projected onto the facet basis, then
       // r_i += sum_{f,m} Ef[f][m][i] phi[f][m]
@@ -350,14 +352,13 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
         }
 #pragma unroll
         for (int m = 0; m < NFM; ++m) {
-          const float* Er = Ef + (f * NFM + m) * NP4;
+          const ulonglong2* Er = reinterpret_cast<const ulonglong2*>(Ef + (f * NFM + m) * NP4);
+          const unsigned long long pp = tc::f2_pack(phi[m], phi[m]);
 #pragma unroll
-          for (int i4 = 0; i4 < NP4; i4 += 4) {
-            const float4 y = *reinterpret_cast<const float4*>(Er + i4);
-            if (i4 + 0 < N) rr[i4 + 0] = fmaf(y.x, phi[m], rr[i4 + 0]);
-            if (i4 + 1 < N) rr[i4 + 1] = fmaf(y.y, phi[m], rr[i4 + 1]);
-            if (i4 + 2 < N) rr[i4 + 2] = fmaf(y.z, phi[m], rr[i4 + 2]);
-            if (i4 + 3 < N) rr[i4 + 3] = fmaf(y.w, phi[m], rr[i4 + 3]);
+          for (int j4 = 0; j4 < NP4 / 4; ++j4) {
+            const ulonglong2 y = Er[j4];
+            r2[2 * j4] = tc::f2_fma(y.x, pp, r2[2 * j4]);
+            r2[2 * j4 + 1] = tc::f2_fma(y.y, pp, r2[2 * j4 + 1]);
           }
         }
       }
@@ -374,20 +375,22 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
           if (q0 + ql >= QV) break;
           const float p0 = valid ? -uq0[ql] * wq[ql] : 0.f;
           const float p1 = valid ? -uq1[ql] * wq[ql] : 0.f;
-          const float* Gq = G + (q0 + ql) * 2 * NP4;
+          const unsigned long long pp0 = tc::f2_pack(p0, p0), pp1 = tc::f2_pack(p1, p1);
+          const ulonglong2* Gq = reinterpret_cast<const ulonglong2*>(G + (q0 + ql) * 2 * NP4);
 #pragma unroll
-          for (int i4 = 0; i4 < NP4; i4 += 4) {
-            const float4 g0 = *reinterpret_cast<const float4*>(Gq + i4);
-            const float4 g1 = *reinterpret_cast<const float4*>(Gq + NP4 + i4);
-            if (i4 + 0 < N) rr[i4 + 0] = fmaf(p1, g1.x, fmaf(p0, g0.x, rr[i4 + 0]));
-            if (i4 + 1 < N) rr[i4 + 1] = fmaf(p1, g1.y, fmaf(p0, g0.y, rr[i4 + 1]));
-            if (i4 + 2 < N) rr[i4 + 2] = fmaf(p1, g1.z, fmaf(p0, g0.z, rr[i4 + 2]));
-            if (i4 + 3 < N) rr[i4 + 3] = fmaf(p1, g1.w, fmaf(p0, g0.w, rr[i4 + 3]));
+          for (int j4 = 0; j4 < NP4 / 4; ++j4) {
+            const ulonglong2 g0 = Gq[j4];
+            const ulonglong2 g1 = Gq[NP4 / 4 + j4];
+            r2[2 * j4] = tc::f2_fma(pp1, g1.x, tc::f2_fma(pp0, g0.x, r2[2 * j4]));
+            r2[2 * j4 + 1] = tc::f2_fma(pp1, g1.y, tc::f2_fma(pp0, g0.y, r2[2 * j4 + 1]));
           }
         }
       }
     }
 
+    float rr[NP4];
+#pragma unroll
+    for (int j = 0; j < NP2; ++j) tc::f2_unpack(r2[j], rr[2 * j], rr[2 * j + 1]);
     // ---- epilogue: increment, FP64 accumulation (mode 1), output traces --------------
     double ex[N];
 #pragma unroll
