@@ -266,7 +266,7 @@ dgc_status check_prec(const dgc_mesh* m, dgc_prec prec) {
 dgc_status ensure_tc_scratch(dgc_mesh* m) {
   cudaError_t perr = dgc::launch_stage_tc(m->s.D, m->s.K, nullptr, nullptr);
   if (perr != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage setup failed: %s", cudaGetErrorString(perr));
-  DGC_CUDA(m->wcoef.alloc((size_t)m->E * m->s.D * dgc::tc_nk(m->s.D, m->s.K)));
+  DGC_CUDA(m->wcoef.alloc(((size_t)m->E + 127) / 128 * 128 * m->s.D * dgc::tc_nk(m->s.D, m->s.K)));
   const size_t nt = dgc::tc_tsoa_len(m->s.D, m->s.K, m->E), nr = dgc::tc_tr_len(m->s.D, m->s.K, m->E);
   DGC_CUDA(m->ts0.alloc(nt));
   DGC_CUDA(m->tsf.alloc(nt));

@@ -108,8 +108,10 @@ __global__ void wind_coeffs_kernel(DevMesh m, const double* __restrict__ u, floa
   gather_local(m, e, u, ut);
   bdm_to_dubiner(m, ut, uc);
   const double inv = 1.0 / m.detJ[e];
+  // tile-blocked [tile][a][i][128] (tile = 128 consecutive elements)
+  float* wt = wc + (long)(e >> 7) * s.D * nk * 128 + (e & 127);
   for (int a = 0; a < s.D; ++a)
-    for (int i = 0; i < nk; ++i) wc[((long)e * s.D + a) * nk + i] = i < s.N ? (float)(inv * uc[a * s.N + i]) : 0.f;
+    for (int i = 0; i < nk; ++i) wt[(long)(a * nk + i) * 128] = i < s.N ? (float)(inv * uc[a * s.N + i]) : 0.f;
 }
 
 // w_{c,i} = (1/det J) sum_a J[c][a] uc[a][i]   (= (1/|det J|) int_T u_c psi_i)

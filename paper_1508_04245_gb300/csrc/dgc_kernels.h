@@ -55,7 +55,8 @@ size_t tc_tr_len(int D, int K, int E);
 cudaError_t launch_tsoa_in(int D, int K, const double* v, double* vt, float* vft, float* tr, const float* blob,
                            int E, cudaStream_t s);
 cudaError_t launch_tsoa_out(int D, int K, const double* vt, double* v, int E, cudaStream_t s);
-// wind on the Dubiner basis scaled by 1/det J, float [E][D][nk] (zero padded)
+// wind on the Dubiner basis scaled by 1/det J, float, tile-blocked [tile][D][nk][128]
+// (zero padded in i; entries of elements past E in the last tile are not written)
 cudaError_t launch_wind_coeffs(const DevMesh& m, const double* u_hdiv, float* wc, int nk, cudaStream_t s);
 
 cudaError_t launch_geometry(const DevMesh& m, cudaStream_t s);

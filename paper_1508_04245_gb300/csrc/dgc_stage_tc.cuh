@@ -59,7 +59,7 @@ struct StageTcArgs {
   double* v;            // modes 1, 2: TSOA FP64 state
   float* vf_out;        // mode 1: FP32 copy of the new state (may equal vf)
   float* trout;         // modes 0, 1: facet traces of the stage output
-  const float* wcoef;   // [E][2][NK] wind on the Dubiner basis, scaled by 1/det J
+  const float* wcoef;   // [tile][2][NK][128] wind on the Dubiner basis, scaled by 1/det J
   const int* nbr;       // [E][3]
   const float* blob;    // TcLayout2D<K> table blob
   int* status;          // device status word
@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     tc::bulk_prefetch_l2(a.trin + (size_t)tile * ntr, ntr * 4);
   };
   auto load_wind = [&](int tile) {        // a tile's wind coefficients into the staging buffer
-    const uint32_t bytes = (uint32_t)min(128, a.E - tile * 128) * 2 * NK * 4;
+    const uint32_t bytes = (uint32_t)L::WSTAGE * 4;   // whole tile block ([c][k][128])
     tc::mbar_arrive_expect_tx(bar_w, bytes);
-    tc::bulk_g2s(wst, a.wcoef + (size_t)tile * 128 * 2 * NK, bytes, bar_w);
+    tc::bulk_g2s(wst, a.wcoef + (size_t)tile * L::WSTAGE, bytes, bar_w);
     ++w_issued;
   };
   // a tile's blocks of v^n (FP32 copy) and of the stage-input increment into dst
@@ -228,13 +228,10 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     if (*abort_flag == 0 && !tc::mbar_wait(bar_w, it & 1)) *abort_flag = 1;
 #pragma unroll
     for (int k4 = 0; k4 < NK; k4 += 4) {
-      const float4 x = valid ? *reinterpret_cast<const float4*>(wst + (r * 2 + c) * NK + k4)
-                             : make_float4(0.f, 0.f, 0.f, 0.f);
       float h[4], tl[4];
-      tcimpl::split(x.x, h[0], tl[0]);
-      tcimpl::split(x.y, h[1], tl[1]);
-      tcimpl::split(x.z, h[2], tl[2]);
-      tcimpl::split(x.w, h[3], tl[3]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)   // consecutive threads read consecutive words
+        tcimpl::split(valid ? wst[(c * NK + k4 + u) * 128 + r] : 0.f, h[u], tl[u]);
       const uint32_t o = tc::kmajor_off32(r, k4, L::LBO, L::SBO_NK) / 4;
       tc::st_shared_v4(op + ((2 + c) * 2 + 0) * L::szOpA + o, h[0], h[1], h[2], h[3]);
       tc::st_shared_v4(op + ((2 + c) * 2 + 1) * L::szOpA + o, tl[0], tl[1], tl[2], tl[3]);
@@ -287,6 +284,8 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     //      epilogue into the state half, the next tile's into the wind half ---------
     if (t == issuer_t && run2) {
       tc::fence_proxy_async_smem();
+      // the FP64 state the epilogue accumulates into (mode 1), toward L2
+      if (a.mode == 1) tc::bulk_prefetch_l2(a.v + (size_t)tile * L::TSOA_TILE, (uint32_t)L::TSOA_TILE * 8);
       if (epi_vf || epi_din) {
         load_state(epi, bar_ep, tile, epi_vf, epi_din);
         ++ep_issued;
