@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--substeps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -207,6 +208,84 @@ def peaks():
             m = json.load(f)
         return m.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# batched workload: 64 independent 2D instances of uneven size and order
+# ---------------------------------------------------------------------------
+def measure_batched(torch, dgconv, rank: int, world: int, flush, stream, reps: int = 3):
+    """The batched instances in one graph launch (mixed precision: TF32x3 where the
+    tensor-core path covers the order, FP32 otherwise) against one FP64
+    rk_substeps launch per instance; same inputs, errors against the FP64 run."""
+    insts = W.batched_instances(seed=5 + 1000 * rank)
+    meshes, winds, v0s, ds, nsteps = [], [], [], [], []
+    units = 0
+    byts = 0
+    for wl in insts:
+        verts, elems = wl.mesh()
+        m = dgconv.Mesh(2, wl.k, verts, elems)
+        pot = dgconv.potential_values(m, wl.potential())
+        w = m.wind_from_potential(torch.tensor(pot, dtype=torch.float64, device="cuda"))
+        meshes.append(m)
+        winds.append(w)
+        v0s.append(torch.tensor(W.uniform_coeffs(wl.seed, m.n_elem, 2, wl.k), dtype=torch.float64, device="cuda"))
+        ds.append(m.cfl_ds(w, wl.cfl))
+        nsteps.append(wl.substeps)
+        b, _, n = stage_bytes_flops(wl)
+        units += m.n_elem * n * 2 * 3 * wl.substeps
+        byts += b * m.n_elem * 3 * wl.substeps
+    # autotuned block shapes of the CUDA-core kernel for the orders that use it
+    # (k = 5, 6 in mixed precision; every order in the FP64 comparison), each tuned
+    # on the largest instance of its order
+    tuned = {}
+    for k in sorted({wl.k for wl in insts}):
+        j = max((i for i, wl in enumerate(insts) if wl.k == k), key=lambda i: meshes[i].n_elem)
+        for prec in (("fp32", "fp64") if k > 4 else ("fp64",)):
+            tuned[f"k{k}/{prec}"] = meshes[j].autotune(winds[j], prec)
+    states = [v.clone() for v in v0s]
+
+    def reset():
+        for s_, v in zip(states, v0s):
+            s_.copy_(v)
+
+    def timed(fn):
+        ts = []
+        for rep in range(reps + 1):
+            reset()
+            flush.zero_()
+            a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            fn()
+            b0.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:                                    # the first call builds the graphs
+                ts.append(a0.elapsed_time(b0))
+        return max_over_ranks(min(ts), world, "cuda")
+
+    def mixed():
+        dgconv.batch_rk_substeps(meshes, winds, states, ds, nsteps, 3, "tf32x3")
+
+    def fp64():
+        for m, w, s_, d, n in zip(meshes, winds, states, ds, nsteps):
+            m.rk_substeps(w, s_, d, n, 3, "fp64")
+
+    ms_mixed = timed(mixed)
+    out_mixed = [s_.clone() for s_ in states]
+    ms_fp64 = timed(fp64)
+    err = max(float((a - b).abs().max() / b.abs().max()) for a, b in zip(out_mixed, states))
+    for m in meshes:
+        m.check()
+    hbm, _ = peaks()
+    return {"instances": len(insts), "elements": sum(m.n_elem for m in meshes),
+            "orders": sorted({wl.k for wl in insts}), "substeps": 50, "scheme": "SSP-RK3",
+            "mixed": {"value": job_throughput(units, world, ms_mixed), "ms": ms_mixed,
+                      "prec": "tf32x3 (k <= 4), fp32 (k = 5, 6)", "launch": "one cached multi-branch CUDA graph",
+                      "roofline_frac": byts / (ms_mixed * 1e-3) / 1e9 / hbm},
+            "fp64_per_instance": {"value": job_throughput(units, world, ms_fp64), "ms": ms_fp64,
+                                  "launch": "one cached graph per instance, in sequence"},
+            "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed, "max_rel_err_vs_fp64": err,
+            "autotuned_block": tuned,
+            "unit": "DOF-stage updates/s"}
 
 
 # ---------------------------------------------------------------------------
@@ -465,6 +544,8 @@ def main():
                           "tau": tau, "ds": ds_r, "by_prec": rich,
                           "note": "operator evaluations = iterations + 1; roofline against the same "
                                   "algorithmic bytes per element as one stage"}
+    if not args.no_batched:
+        line["batched"] = measure_batched(torch, dgconv, rank, world, flush, stream)
     # clocks sampled from before the first timed step to the end of the GPU measurements
     line["clocks"] = clocks.stop()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -203,6 +203,18 @@ dgc_status dgc_conv_apply_hdiv(dgc_mesh* mesh, const double* wind_hdiv, const do
 dgc_status dgc_wind_extrapolate(dgc_mesh* mesh, int n_terms, const double* const* fields, const double* coefs,
                                 double* out_hdiv, void* stream);
 
+/* Autotuner of the CUDA-core stage kernel (every order of both element types,
+ * DGC_FP64 and DGC_FP32): times one stage on this mesh with its wind for each
+ * candidate block shape (64, 128, 192, 256 threads; reps timed launches each)
+ * and keeps the fastest for this (dim, k, prec) in a process-wide table that
+ * every later launch on any mesh of that kind uses.  Results do not depend on
+ * the choice (each element is computed independently).  Drops the cached
+ * graphs of this mesh (they hold the old shape).  *block_out (host, may be
+ * NULL) receives the choice, 0 for DGC_TF32X3 (one fixed tile shape, nothing
+ * to tune).  1 <= reps <= 1000.  Synchronizes `stream`. */
+dgc_status dgc_autotune(dgc_mesh* mesh, const double* wind_hdiv, dgc_prec prec, int reps, int* block_out,
+                        void* stream);
+
 /* Points at which callers evaluate input fields, host [count][dim]:
  * kind 0: the element-wise equispaced P^{k+1} Lagrange nodes used by
  *         dgc_wind_from_potential ([E][n_lagrange][dim]);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <array>
 #include <cmath>
@@ -419,6 +420,20 @@ dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, in
   return DGC_OK;
 }
 
+// forget the cached batch graphs that contain this mesh
+void drop_batch_graphs(const dgc_mesh* mesh) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  for (size_t j = 0; j < g_batch_cache.size();) {
+    BatchGraph& b = g_batch_cache[j];
+    if (std::find(b.meshes.begin(), b.meshes.end(), mesh) != b.meshes.end()) {
+      if (b.exec) cudaGraphExecDestroy(b.exec);
+      g_batch_cache.erase(g_batch_cache.begin() + j);
+    } else {
+      ++j;
+    }
+  }
+}
+
 // out = (M^V)^-1 C^V w = -L(w) with the wind prepared for prec
 dgc_status apply_operator(dgc_mesh* m, dgc_prec prec, const double* w, double* out, cudaStream_t st) {
   if (prec == DGC_TF32X3) {
@@ -510,6 +525,12 @@ dgc_status rich_build(dgc_mesh* m, const double* wind, const double* g, double* 
 }  // namespace
 
 namespace dgc {
+// autotuned threads per block of the CUDA-core stage kernel, [dim - 2][k][fp32]; 0 = default
+std::atomic<int> g_stage_block[2][7][2];
+int stage_block_get(int D, int K, bool fp32) {
+  if (D < 2 || D > 3 || K < 1 || K > 6) return 0;
+  return g_stage_block[D - 2][K][fp32 ? 1 : 0].load(std::memory_order_relaxed);
+}
 // helpers for entry points defined in other translation units
 bool mesh_view(const dgc_mesh* mesh, DevMesh* out) {
   if (!mesh) return false;
@@ -616,18 +637,7 @@ dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int 
 
 dgc_status dgc_mesh_free(dgc_mesh* mesh) {
   if (!mesh) return DGC_OK;
-  {
-    std::lock_guard<std::mutex> lock(g_batch_mu);
-    for (size_t j = 0; j < g_batch_cache.size();) {
-      BatchGraph& b = g_batch_cache[j];
-      if (std::find(b.meshes.begin(), b.meshes.end(), mesh) != b.meshes.end()) {
-        if (b.exec) cudaGraphExecDestroy(b.exec);
-        g_batch_cache.erase(g_batch_cache.begin() + j);
-      } else {
-        ++j;
-      }
-    }
-  }
+  drop_batch_graphs(mesh);
   mesh->release_all();
   delete mesh;
   return DGC_OK;
@@ -765,6 +775,69 @@ dgc_status dgc_richardson(dgc_mesh* mesh, const double* wind_hdiv, const double*
     mesh->rich_key = key;
   }
   DGC_CUDA(cudaGraphLaunch(mesh->rich_graph, as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_autotune(dgc_mesh* mesh, const double* wind_hdiv, dgc_prec prec, int reps, int* block_out,
+                        void* stream) {
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (dgc_status rc = check_prec(mesh, prec)) return rc;
+  if (!wind_hdiv) return fail(DGC_ERR_ARG, "wind_hdiv is NULL");
+  if (reps < 1 || reps > 1000) return fail(DGC_ERR_ARG, "reps must lie in 1..1000 (got %d)", reps);
+  if (block_out) *block_out = 0;
+  if (prec == DGC_TF32X3) return DGC_OK;   // the tensor-core kernel has one tile shape (128 x 288)
+  const bool fp32 = prec == DGC_FP32;
+  const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
+  if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
+  DGC_CUDA(mesh->stage1.alloc(n));
+  DGC_CUDA(mesh->stage2.alloc(n));
+  cudaStream_t st = as_stream(stream);
+  DGC_CUDA(cudaMemsetAsync(mesh->stage1.ptr, 0, n * sizeof(double), st));
+  if (dgc_status rc = prepare_wind(mesh, prec, wind_hdiv, st)) return rc;
+  cudaEvent_t e0, e1;
+  DGC_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(DGC_ERR_CUDA, "event creation failed");
+  }
+  std::atomic<int>& slot = dgc::g_stage_block[mesh->s.D - 2][mesh->s.K][fp32 ? 1 : 0];
+  const int before = slot.load();
+  int best = 0;
+  float best_ms = 0.f;
+  dgc_status rc = DGC_OK;
+  for (int b : dgc::kStageBlocks) {
+    slot.store(b);
+    // one untimed launch, then reps timed launches of one stage (stage1 -> stage2)
+    for (int r = 0; r <= reps && rc == DGC_OK; ++r) {
+      if (r == 1 && cudaEventRecord(e0, st) != cudaSuccess) rc = fail(DGC_ERR_CUDA, "event record failed");
+      if (rc == DGC_OK) rc = stage(mesh, prec, mesh->stage1.ptr, nullptr, mesh->stage2.ptr, 0.0, 1.0, 1e-3, st);
+    }
+    float ms = 0.f;
+    if (rc == DGC_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = fail(DGC_ERR_CUDA, "timing the stage kernel failed");
+    if (rc != DGC_OK) break;
+    if (best == 0 || ms < best_ms) {
+      best = b;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != DGC_OK) {
+    slot.store(before);
+    return rc;
+  }
+  slot.store(best);
+  // graphs captured before the choice keep their old launch shape: drop them
+  if (mesh->graph) cudaGraphExecDestroy(mesh->graph);
+  mesh->graph = nullptr;
+  if (mesh->rich_graph) cudaGraphExecDestroy(mesh->rich_graph);
+  mesh->rich_graph = nullptr;
+  if (mesh->oifs_graph) cudaGraphExecDestroy(mesh->oifs_graph);
+  mesh->oifs_graph = nullptr;
+  drop_batch_graphs(mesh);
+  if (block_out) *block_out = best;
   return DGC_OK;
 }
 

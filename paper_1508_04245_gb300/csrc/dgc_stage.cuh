@@ -64,13 +64,19 @@ constexpr int stage_cpt() {
   return (D == 2 && sizeof(T) == 4) ? 2 : 1;
 }
 
+// Threads per block: a per-(dim, order, precision) choice made by the autotuner
+// (dgc_autotune) among kStageBlocks, the default until it runs.  Every element
+// is computed by one thread independently of the block shape, so the choice
+// changes the speed only, never a result.
+constexpr int kStageBlocks[4] = {64, 128, 192, 256};
 template <typename T, int D, int K>
-constexpr int stage_block() {
+constexpr int stage_block_default() {
   return D == 2 ? 128 : 256;
 }
+int stage_block_get(int D, int K, bool fp32);   // tuned value or 0
 
 template <int D, int K, typename T, int CPT, bool SMEM>
-__global__ void __launch_bounds__(D == 2 ? 128 : 256) stage_kernel(StageArgs a) {
+__global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
   using Dm = Dims<D, K>;
   using TB = StageTab<D, K>;
   constexpr int N = Dm::N, QV = Dm::QV, QF = Dm::QF, NFM = Dm::NFM, NF = Dm::NF;
@@ -215,7 +221,8 @@ template <int D, int K, typename T>
 cudaError_t launch_stage_t(const StageArgs* ap, cudaStream_t stream) {
   constexpr int CPT = stage_cpt<T, D, K>();
   constexpr bool SMEM = stage_tab_in_smem<T, D, K>();
-  constexpr int BLOCK = stage_block<T, D, K>();
+  const int tuned = stage_block_get(D, K, sizeof(T) == 4);
+  const int BLOCK = tuned > 0 ? tuned : stage_block_default<T, D, K>();
   const size_t smem = SMEM ? StageTab<D, K>::size * sizeof(T) : 0;
   auto kern = stage_kernel<D, K, T, CPT, SMEM>;
   if (!ap) {

@@ -40,6 +40,7 @@ SIGNATURES = {
                      ctypes.c_int, _vp],
     "dgc_conv_apply_hdiv": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp],
     "dgc_wind_extrapolate": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp],
+    "dgc_autotune": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp],
     "dgc_batch_rk_substeps": [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp],
     "dgc_point_coords": [_vp, ctypes.c_int, _vp, _i64p],
     "dgc_wind_from_potential": [_vp, _vp, _vp, _vp],
@@ -222,6 +223,13 @@ class Mesh:
         hc = (ctypes.c_double * n)(*[float(c) for c in coefs])
         check(lib().dgc_wind_extrapolate(self._h, n, hp, hc, _ptr(out, self.n_hdiv, "out"), _stream(stream)))
         return out
+
+    def autotune(self, wind, prec="fp64", reps: int = 5, stream=None) -> int:
+        """Pick the CUDA-core stage kernel's block shape for this (dim, k, prec) (see dgc_autotune)."""
+        b = ctypes.c_int()
+        check(lib().dgc_autotune(self._h, _ptr(wind, self.n_hdiv, "wind"), PREC[prec], int(reps), ctypes.byref(b),
+                                 _stream(stream)))
+        return b.value
 
     def richardson_ds(self, wind, tau: float) -> float:
         """Pseudo-time step 1 / (1 + beta^2), beta = tau (2k+1) max|u| / min h_T (stable for every mode)."""
