@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 from paper_1508_04245_gb300 import workloads as W  # noqa: E402
 
 METRIC = "DG convection DOF-stage updates/s, plain FP64 vs mixed/batched at ≤1e-6 err"
+TC_PRECS = ("tf32x3", "bf16x3")
 WORKLOAD = "square256_k4"
 L2_BYTES = 129 * 2 ** 20
 
@@ -46,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dgconv", choices=["dgconv", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=["fp32", "fp64", "tf32x3"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp32", "fp64", "tf32x3", "bf16x3"])
     ap.add_argument("--no-other-precisions", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--substeps", type=int, default=None)
@@ -184,7 +185,7 @@ def ncu_traffic(wl, prec):
     The capture records the sha1 of the kernel source it measured; after any
     change of that source the figure is stale and None is returned.
     """
-    if prec != "tf32x3" or wl.name != "square256_k4":
+    if prec not in TC_PRECS or wl.name != "square256_k4":
         return None
     import hashlib
     prof = os.path.join(ROOT, "profiles", "stage_tc_kernel_square256_k4.md")
@@ -195,8 +196,10 @@ def ncu_traffic(wl, prec):
     except OSError:
         return None
     fields = dict(ln.split(":", 1) for ln in text.splitlines()
-                  if ln.startswith(("kernel_source_sha1:", "traffic_bytes_per_launch:")))
+                  if ln.startswith(("kernel_source_sha1:", "traffic_bytes_per_launch:", "prec:")))
     if fields.get("kernel_source_sha1", "").split()[0:1] != [sha]:
+        return None
+    if fields.get("prec", "tf32x3").strip() != prec:
         return None
     return float(fields["traffic_bytes_per_launch"].strip())
 
@@ -213,9 +216,9 @@ def peaks():
 # ---------------------------------------------------------------------------
 # batched workload: 64 independent 2D instances of uneven size and order
 # ---------------------------------------------------------------------------
-def measure_batched(torch, dgconv, rank: int, world: int, flush, stream, reps: int = 3):
-    """The batched instances in one graph launch (mixed precision: TF32x3 where the
-    tensor-core path covers the order, FP32 otherwise) against one FP64
+def measure_batched(torch, dgconv, rank: int, world: int, flush, stream, mixed_prec: str, reps: int = 3):
+    """The batched instances in one graph launch (mixed precision: the tensor-core
+    split precision where it covers the order, FP32 otherwise) against one FP64
     rk_substeps launch per instance; same inputs, errors against the FP64 run."""
     insts = W.batched_instances(seed=5 + 1000 * rank)
     meshes, winds, v0s, ds, nsteps = [], [], [], [], []
@@ -263,7 +266,7 @@ def measure_batched(torch, dgconv, rank: int, world: int, flush, stream, reps: i
         return max_over_ranks(min(ts), world, "cuda")
 
     def mixed():
-        dgconv.batch_rk_substeps(meshes, winds, states, ds, nsteps, 3, "tf32x3")
+        dgconv.batch_rk_substeps(meshes, winds, states, ds, nsteps, 3, mixed_prec)
 
     def fp64():
         for m, w, s_, d, n in zip(meshes, winds, states, ds, nsteps):
@@ -271,20 +274,33 @@ def measure_batched(torch, dgconv, rank: int, world: int, flush, stream, reps: i
 
     ms_mixed = timed(mixed)
     out_mixed = [s_.clone() for s_ in states]
+    # the same graph restricted to the tensor-core orders and to the others
+    sub_ms = {}
+    for name, keep in (("k<=4 (tensor cores)", lambda k: k <= 4), ("k>=5 (CUDA cores, fp32)", lambda k: k > 4)):
+        idx = [i for i, wl in enumerate(insts) if keep(wl.k)]
+        if idx:
+            sub_ms[name] = timed(lambda idx=idx: dgconv.batch_rk_substeps(
+                [meshes[i] for i in idx], [winds[i] for i in idx], [states[i] for i in idx],
+                [ds[i] for i in idx], [nsteps[i] for i in idx], 3, mixed_prec))
     ms_fp64 = timed(fp64)
-    err = max(float((a - b).abs().max() / b.abs().max()) for a, b in zip(out_mixed, states))
+    errs = [float((a - b).abs().max() / b.abs().max()) for a, b in zip(out_mixed, states)]
+    err = max(errs)
+    err_by_k = {f"k{k}": max(e for e, wl in zip(errs, insts) if wl.k == k) for k in sorted({wl.k for wl in insts})}
+    units_by_k = {f"k{k}": sum(m.n_elem * math.comb(k + 2, 2) * 2 * 3 * 50 for m, wl in zip(meshes, insts)
+                               if wl.k == k) for k in sorted({wl.k for wl in insts})}
     for m in meshes:
         m.check()
     hbm, _ = peaks()
     return {"instances": len(insts), "elements": sum(m.n_elem for m in meshes),
             "orders": sorted({wl.k for wl in insts}), "substeps": 50, "scheme": "SSP-RK3",
             "mixed": {"value": job_throughput(units, world, ms_mixed), "ms": ms_mixed,
-                      "prec": "tf32x3 (k <= 4), fp32 (k = 5, 6)", "launch": "one cached multi-branch CUDA graph",
+                      "prec": f"{mixed_prec} (k <= 4), fp32 (k = 5, 6)", "launch": "one cached multi-branch CUDA graph",
                       "roofline_frac": byts / (ms_mixed * 1e-3) / 1e9 / hbm},
             "fp64_per_instance": {"value": job_throughput(units, world, ms_fp64), "ms": ms_fp64,
                                   "launch": "one cached graph per instance, in sequence"},
             "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed, "max_rel_err_vs_fp64": err,
-            "autotuned_block": tuned,
+            "autotuned_block": tuned, "max_rel_err_by_order": err_by_k, "units_by_order": units_by_k,
+            "sub_batch_ms": sub_ms,
             "unit": "DOF-stage updates/s"}
 
 
@@ -378,7 +394,7 @@ def main():
         mesh.mass(v, out=mv)                              # a6 (M^V)
         mesh.transfer_T(mv, out=g)                        # a8
     # geometry, transfer, [wind prep (+ layout in/out on the tensor-core path), stages], mass, transfer_T (2)
-    launches_per_step = 1 + 1 + (1 + 3 * substeps + (2 if args.prec == "tf32x3" else 0)) + 1 + 2
+    launches_per_step = 1 + 1 + (1 + 3 * substeps + (2 if args.prec in TC_PRECS else 0)) + 1 + 2
 
     for _ in range(args.warmup):
         step()
@@ -461,13 +477,14 @@ def main():
     achieved = byts * wl.n_elem / (stage_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": ncu_traffic(wl, args.prec), "peak_source": hbm_src,
-            "kernel": "stage_tc_kernel" if args.prec == "tf32x3" else "stage_kernel",
+            "kernel": "stage_tc_kernel" if args.prec in TC_PRECS else "stage_kernel",
             "stage_ms": stage_ms, "alg_bytes_per_elem_stage": byts, "alg_flops_per_elem_stage": flops,
             "achieved_tflops": flops * wl.n_elem / (stage_ms * 1e-3) / 1e12}
     line = {
         "metric": METRIC, "value": value, "unit": "DOF-stage updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3"}[args.prec], "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3", "bf16x3": "bf16x3"}[args.prec],
+        "data": "synthetic",
         "config": {"workload": wl.name, "elements": wl.n_elem, "dim": wl.dim, "k": wl.k, "substeps": substeps,
                    "scheme": "SSP-RK3", "prec": args.prec, "l2": "flushed between timed steps",
                    "step": "a1 geometry, a2 I, 100x RK3 (a3-a7), M^V, a8 I^T"},
@@ -480,8 +497,8 @@ def main():
     if not args.no_other_precisions:
         # the same step at the other contraction precisions (1 warm-up, 2 timed steps each)
         others = {}
-        for prec in ("fp64", "fp32", "tf32x3"):
-            if prec == args.prec:
+        for prec in ("fp64", "fp32", "tf32x3", "bf16x3"):
+            if prec == args.prec or (prec in TC_PRECS and not (wl.dim == 2 and wl.k <= 4)):
                 continue
 
             def step_p(p=prec):
@@ -521,8 +538,8 @@ def main():
     it_r = torch.zeros(1, dtype=torch.int32, device="cuda")
     res_r = torch.zeros(rich_iters + 1, dtype=torch.float64, device="cuda")
     rich = {}
-    for prec in ("fp64", "fp32", "tf32x3"):
-        if prec == "tf32x3" and not (wl.dim == 2 and wl.k <= 4):
+    for prec in ("fp64", "fp32", "tf32x3", "bf16x3"):
+        if prec in TC_PRECS and not (wl.dim == 2 and wl.k <= 4):
             continue
         ts = []
         for rep in range(4):
@@ -545,7 +562,8 @@ def main():
                           "note": "operator evaluations = iterations + 1; roofline against the same "
                                   "algorithmic bytes per element as one stage"}
     if not args.no_batched:
-        line["batched"] = measure_batched(torch, dgconv, rank, world, flush, stream)
+        line["batched"] = measure_batched(torch, dgconv, rank, world, flush, stream,
+                                          args.prec if args.prec in TC_PRECS else "bf16x3")
     # clocks sampled from before the first timed step to the end of the GPU measurements
     line["clocks"] = clocks.stop()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

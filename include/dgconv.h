@@ -64,14 +64,19 @@ typedef int dgc_status;
 #define DGC_ERR_NONFINITE (-5)    /* a NaN or Inf was produced */
 #define DGC_ERR_ALLOC (-6)        /* device or host allocation failed */
 
-/* Contraction precision of the convection stages; the state and the RK stage
- * combinations are FP64 in every mode.
+/* Contraction precision of the convection stages; the state is FP64 in every
+ * mode.
  *   DGC_FP64    FP64 on CUDA cores
  *   DGC_FP32    FP32 on CUDA cores
- *   DGC_BF16X3  reserved (not available)
- *   DGC_TF32X3  tcgen05 tensor cores, kind::tf32, each operand split into a
- *               TF32 head and tail, three products, FP32 accumulation
- *               (triangles, k <= 4) */
+ *   DGC_BF16X3  triangles, k <= 4: the evaluation at the quadrature points on
+ *               tcgen05 tensor cores, kind::f16, each operand split exactly into
+ *               three BF16 pieces, six products, FP32 accumulation; the test
+ *               contractions in FP32 on CUDA cores; FP32 stage increments,
+ *               FP64 accumulation once per substep
+ *   DGC_TF32X3  the same with kind::tf32 and a two-piece TF32 split (about 22
+ *               significand bits per operand), three products
+ * Other orders and tetrahedra return DGC_ERR_UNSUPPORTED for the tensor-core
+ * precisions. */
 typedef enum { DGC_FP64 = 0, DGC_FP32 = 1, DGC_BF16X3 = 2, DGC_TF32X3 = 3 } dgc_prec;
 typedef enum { DGC_SSPRK2 = 2, DGC_SSPRK3 = 3 } dgc_scheme;
 
@@ -144,7 +149,7 @@ dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg
  * run concurrently; the graph is cached (keyed by every argument) and
  * replayed by later identical calls, and dropped when one of its meshes is
  * freed.  meshes, winds, states, ds, nsteps: host arrays of n_inst entries.
- * With DGC_TF32X3, instances whose order the tensor-core path does not cover
+ * With DGC_TF32X3 or DGC_BF16X3, instances whose order the tensor-core path does not cover
  * (see dgc_prec) run their contractions in FP32 on CUDA cores. */
 dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const double* const* winds,
                                  double* const* states, const double* ds, const int* nsteps, dgc_scheme scheme,
@@ -210,7 +215,7 @@ dgc_status dgc_wind_extrapolate(dgc_mesh* mesh, int n_terms, const double* const
  * every later launch on any mesh of that kind uses.  Results do not depend on
  * the choice (each element is computed independently).  Drops the cached
  * graphs of this mesh (they hold the old shape).  *block_out (host, may be
- * NULL) receives the choice, 0 for DGC_TF32X3 (one fixed tile shape, nothing
+ * NULL) receives the choice, 0 for the tensor-core precisions (one fixed tile shape, nothing
  * to tune).  1 <= reps <= 1000.  Synchronizes `stream`. */
 dgc_status dgc_autotune(dgc_mesh* mesh, const double* wind_hdiv, dgc_prec prec, int reps, int* block_out,
                         void* stream);

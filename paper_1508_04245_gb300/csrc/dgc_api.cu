@@ -107,7 +107,7 @@ struct dgc_mesh {
   DevBuf<double> Bv, wv, wf, Bf, Cb, Lg_int, Lg_fac, Tint, wd, wfd, Qfd, Bd;
   // stage-table blobs
   DevBuf<double> tab64;
-  DevBuf<float> tab32, tcblob, wcoef, trA, trB;
+  DevBuf<float> tab32, tcblob, tcblob16, wcoef, trA, trB;   // tensor-core blobs: TF32x3, BF16x3
   DevBuf<double> ts0;              // tile-blocked FP64 state of the tensor-core path
   DevBuf<float> tsf, d1, d2;       // its FP32 copy and the FP32 stage increments
   DevBuf<int> status;
@@ -177,6 +177,7 @@ struct dgc_mesh {
     orient.release();
     tab32.release();
     tcblob.release();
+    tcblob16.release();
     wcoef.release();
     trA.release();
     trB.release();
@@ -253,20 +254,25 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
   return DGC_OK;
 }
 
+// the tensor-core precisions (split operands on tcgen05)
+bool is_tc(dgc_prec prec) { return prec == DGC_TF32X3 || prec == DGC_BF16X3; }
+
 dgc_status check_prec(const dgc_mesh* m, dgc_prec prec) {
   if (prec == DGC_FP64 || prec == DGC_FP32) return DGC_OK;
-  if (prec == DGC_TF32X3) {
+  if (is_tc(prec)) {
     if (dgc::tc_supported(m->s.D, m->s.K)) return DGC_OK;
-    return fail(DGC_ERR_UNSUPPORTED, "DGC_TF32X3 is available for triangles with k <= 4 (dim %d, k %d)", m->s.D,
-                m->s.K);
+    return fail(DGC_ERR_UNSUPPORTED, "%s is available for triangles with k <= 4 (dim %d, k %d)",
+                prec == DGC_TF32X3 ? "DGC_TF32X3" : "DGC_BF16X3", m->s.D, m->s.K);
   }
-  if (prec == DGC_BF16X3) return fail(DGC_ERR_UNSUPPORTED, "precision DGC_BF16X3 is not available in this build");
   return fail(DGC_ERR_ARG, "unknown precision %d", (int)prec);
 }
 
 dgc_status ensure_tc_scratch(dgc_mesh* m) {
-  cudaError_t perr = dgc::launch_stage_tc(m->s.D, m->s.K, nullptr, nullptr);
-  if (perr != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage setup failed: %s", cudaGetErrorString(perr));
+  for (int P = 0; P < 2; ++P) {
+    cudaError_t perr = dgc::launch_stage_tc(m->s.D, m->s.K, P, nullptr, nullptr);
+    if (perr != cudaSuccess)
+      return fail(DGC_ERR_CUDA, "tensor-core stage setup failed: %s", cudaGetErrorString(perr));
+  }
   DGC_CUDA(m->wcoef.alloc(((size_t)m->E + 127) / 128 * 128 * m->s.D * dgc::tc_nk(m->s.D, m->s.K)));
   const size_t nt = dgc::tc_tsoa_len(m->s.D, m->s.K, m->E), nr = dgc::tc_tr_len(m->s.D, m->s.K, m->E);
   DGC_CUDA(m->ts0.alloc(nt));
@@ -279,8 +285,9 @@ dgc_status ensure_tc_scratch(dgc_mesh* m) {
 }
 
 // one tensor-core stage in increment form (see dgc::StageTcArgs)
-dgc_status launch_stage_tc(dgc_mesh* m, int mode, const float* din, const float* trin, float* dout, float* trout,
-                           double p, double q, double* v, cudaStream_t st) {
+dgc_status launch_stage_tc(dgc_mesh* m, dgc_prec prec, int mode, const float* din, const float* trin, float* dout,
+                           float* trout, double p, double q, double* v, cudaStream_t st) {
+  const int P = prec == DGC_BF16X3 ? 1 : 0;
   dgc::StageTcArgs a;
   a.vf = m->tsf.ptr;
   a.din = din;
@@ -291,13 +298,13 @@ dgc_status launch_stage_tc(dgc_mesh* m, int mode, const float* din, const float*
   a.trout = trout;
   a.wcoef = m->wcoef.ptr;
   a.nbr = m->nbr.ptr;
-  a.blob = m->tcblob.ptr;
+  a.blob = P ? m->tcblob16.ptr : m->tcblob.ptr;
   a.status = m->status.ptr;
   a.E = m->E;
   a.mode = mode;
   a.p = (float)p;
   a.q = (float)q;
-  cudaError_t err = dgc::launch_stage_tc(m->s.D, m->s.K, &a, st);
+  cudaError_t err = dgc::launch_stage_tc(m->s.D, m->s.K, P, &a, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed: %s", cudaGetErrorString(err));
   return DGC_OK;
 }
@@ -344,20 +351,21 @@ dgc_status substep_wind(dgc_mesh* m, dgc_prec prec, const WindPlan& w, double ds
 //   RK2: d1 = ds L(v),  v += d1/2 + ds/2 L(v + d1)
 // (identical to the Shu-Osher / Heun forms); the state v is accumulated in FP64
 // once per substep, the increments are FP32.  ABI -> TSOA once, back at the end.
-dgc_status rk_sequence_tc(dgc_mesh* m, double* v, double ds, int nsteps, int scheme, const WindPlan& wp,
-                          cudaStream_t st) {
+dgc_status rk_sequence_tc(dgc_mesh* m, dgc_prec prec, double* v, double ds, int nsteps, int scheme,
+                          const WindPlan& wp, cudaStream_t st) {
   float *cur = m->trA.ptr, *oth = m->trB.ptr;
   if (dgc_status rc = tc_transpose_in(m, v, cur, st)) return rc;
   for (int n = 0; n < nsteps; ++n) {
     dgc_status rc;
-    if ((rc = substep_wind(m, DGC_TF32X3, wp, ds, n, st))) return rc;
+    if ((rc = substep_wind(m, prec, wp, ds, n, st))) return rc;
     if (scheme == DGC_SSPRK2) {
-      if ((rc = launch_stage_tc(m, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr, st))) return rc;
-      if ((rc = launch_stage_tc(m, 1, m->d1.ptr, oth, nullptr, cur, 0.5, 0.5 * ds, m->ts0.ptr, st))) return rc;
+      if ((rc = launch_stage_tc(m, prec, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr, st))) return rc;
+      if ((rc = launch_stage_tc(m, prec, 1, m->d1.ptr, oth, nullptr, cur, 0.5, 0.5 * ds, m->ts0.ptr, st))) return rc;
     } else {
-      if ((rc = launch_stage_tc(m, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr, st))) return rc;
-      if ((rc = launch_stage_tc(m, 0, m->d1.ptr, oth, m->d2.ptr, cur, 0.25, 0.25 * ds, nullptr, st))) return rc;
-      if ((rc = launch_stage_tc(m, 1, m->d2.ptr, cur, nullptr, oth, 2.0 / 3.0, 2.0 / 3.0 * ds, m->ts0.ptr, st)))
+      if ((rc = launch_stage_tc(m, prec, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr, st))) return rc;
+      if ((rc = launch_stage_tc(m, prec, 0, m->d1.ptr, oth, m->d2.ptr, cur, 0.25, 0.25 * ds, nullptr, st))) return rc;
+      if ((rc = launch_stage_tc(m, prec, 1, m->d2.ptr, cur, nullptr, oth, 2.0 / 3.0, 2.0 / 3.0 * ds, m->ts0.ptr,
+                                st)))
         return rc;
       std::swap(cur, oth);
     }
@@ -374,7 +382,7 @@ dgc_status stage(dgc_mesh* m, dgc_prec prec, const double* vin, const double* vn
 // frozen-wind data for the chosen precision
 dgc_status prepare_wind(dgc_mesh* m, dgc_prec prec, const double* wind, cudaStream_t st) {
   cudaError_t err;
-  if (prec == DGC_TF32X3) {
+  if (is_tc(prec)) {
     err = dgc::launch_wind_coeffs(m->view(), wind, m->wcoef.ptr, dgc::tc_nk(m->s.D, m->s.K), st);
   } else {
     const bool fp32 = prec == DGC_FP32;
@@ -386,7 +394,7 @@ dgc_status prepare_wind(dgc_mesh* m, dgc_prec prec, const double* wind, cudaStre
 }
 
 dgc_status ensure_prec_scratch(dgc_mesh* m, dgc_prec prec) {
-  if (prec == DGC_TF32X3) return ensure_tc_scratch(m);
+  if (is_tc(prec)) return ensure_tc_scratch(m);
   return ensure_wind_scratch(m, prec == DGC_FP32);
 }
 
@@ -400,7 +408,7 @@ dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, in
   wp.dt_prev = dt_prev;
   if (!wind_prev)
     if (dgc_status rc = prepare_wind(m, prec, wind, st)) return rc;
-  if (prec == DGC_TF32X3) return rk_sequence_tc(m, v, ds, nsteps, scheme, wp, st);
+  if (is_tc(prec)) return rk_sequence_tc(m, prec, v, ds, nsteps, scheme, wp, st);
   double* v1 = m->stage1.ptr;
   double* v2 = m->stage2.ptr;
   for (int n = 0; n < nsteps; ++n) {
@@ -436,10 +444,11 @@ void drop_batch_graphs(const dgc_mesh* mesh) {
 
 // out = (M^V)^-1 C^V w = -L(w) with the wind prepared for prec
 dgc_status apply_operator(dgc_mesh* m, dgc_prec prec, const double* w, double* out, cudaStream_t st) {
-  if (prec == DGC_TF32X3) {
+  if (is_tc(prec)) {
     if (dgc_status rc = tc_transpose_in(m, w, m->trA.ptr, st)) return rc;
     // mode 2 with q = -1: v <- -L(w)
-    if (dgc_status rc = launch_stage_tc(m, 2, nullptr, m->trA.ptr, nullptr, nullptr, 0.0, -1.0, m->ts0.ptr, st))
+    if (dgc_status rc =
+            launch_stage_tc(m, prec, 2, nullptr, m->trA.ptr, nullptr, nullptr, 0.0, -1.0, m->ts0.ptr, st))
       return rc;
     return tc_transpose_out(m, m->ts0.ptr, out, st);
   }
@@ -617,7 +626,8 @@ dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int 
             up(m->Bd.upload(t.Bd)) && up(m->tab64.upload(stage_blob<double>(t))) &&
             up(m->tab32.upload(stage_blob<float>(t))) && up(m->status.alloc(1)) &&
             up(cudaMemset(m->status.ptr, 0, sizeof(int))) &&
-            (!dgc::tc_supported(dim, k) || up(m->tcblob.upload(dgc::tc_blob(dim, k, t))));
+            (!dgc::tc_supported(dim, k) ||
+             (up(m->tcblob.upload(dgc::tc_blob(dim, k, 0, t))) && up(m->tcblob16.upload(dgc::tc_blob(dim, k, 1, t)))));
   if (!ok) {
     cudaError_t err = cudaGetLastError();
     m->release_all();
@@ -785,7 +795,7 @@ dgc_status dgc_autotune(dgc_mesh* mesh, const double* wind_hdiv, dgc_prec prec, 
   if (!wind_hdiv) return fail(DGC_ERR_ARG, "wind_hdiv is NULL");
   if (reps < 1 || reps > 1000) return fail(DGC_ERR_ARG, "reps must lie in 1..1000 (got %d)", reps);
   if (block_out) *block_out = 0;
-  if (prec == DGC_TF32X3) return DGC_OK;   // the tensor-core kernel has one tile shape (128 x 288)
+  if (is_tc(prec)) return DGC_OK;   // the tensor-core kernel has one tile shape (128 x 288)
   const bool fp32 = prec == DGC_FP32;
   const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
   if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
@@ -950,8 +960,8 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
   if (n_inst == 0) return DGC_OK;
   if (!meshes || !winds || !states || !ds || !nsteps) return fail(DGC_ERR_ARG, "NULL argument array");
   if (scheme != DGC_SSPRK2 && scheme != DGC_SSPRK3) return fail(DGC_ERR_ARG, "unknown scheme %d", (int)scheme);
-  if (prec != DGC_FP64 && prec != DGC_FP32 && prec != DGC_TF32X3)
-    return fail(prec == DGC_BF16X3 ? DGC_ERR_UNSUPPORTED : DGC_ERR_ARG, "precision %d not available", (int)prec);
+  if (prec != DGC_FP64 && prec != DGC_FP32 && !is_tc(prec))
+    return fail(DGC_ERR_ARG, "precision %d not available", (int)prec);
   std::vector<dgc_prec> pr(n_inst);
   std::vector<uint64_t> key = {(uint64_t)n_inst, (uint64_t)scheme, (uint64_t)prec};
   for (int i = 0; i < n_inst; ++i) {
@@ -962,7 +972,7 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
     for (int j = 0; j < i; ++j)
       if (meshes[j] == m) return fail(DGC_ERR_ARG, "instances %d and %d share a mesh handle (scratch)", j, i);
     // the tensor-core path covers triangles k <= 4; other orders run their stages in FP32
-    pr[i] = (prec == DGC_TF32X3 && !dgc::tc_supported(m->s.D, m->s.K)) ? DGC_FP32 : prec;
+    pr[i] = (is_tc(prec) && !dgc::tc_supported(m->s.D, m->s.K)) ? DGC_FP32 : prec;
     if (dgc_status rc = ensure_prec_scratch(m, pr[i])) return rc;
     const size_t n = (size_t)m->E * m->s.D * m->s.N;
     DGC_CUDA(m->stage1.alloc(n));

@@ -46,8 +46,9 @@ cudaError_t launch_stage_3d(int K, bool fp32, const StageArgs* a, cudaStream_t s
 // tensor-core stage kernel (triangles, k <= 4); a == nullptr prepares the kernel
 bool tc_supported(int D, int K);
 int tc_nk(int D, int K);
-std::vector<float> tc_blob(int D, int K, const Tables& t);
-cudaError_t launch_stage_tc(int D, int K, const StageTcArgs* a, cudaStream_t s);
+// P: 0 = TF32 head/tail (3 products), 1 = BF16 three pieces (6 products)
+std::vector<float> tc_blob(int D, int K, int P, const Tables& t);
+cudaError_t launch_stage_tc(int D, int K, int P, const StageTcArgs* a, cudaStream_t s);
 // tile-blocked layouts of the tensor-core path: lengths, and the ABI <-> TSOA transposes
 // (the inward one also writes the facet traces of the state)
 size_t tc_tsoa_len(int D, int K, int E);

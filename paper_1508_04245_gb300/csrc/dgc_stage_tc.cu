@@ -20,32 +20,64 @@ float tf32_rna(float x) {
   return x;
 }
 
-size_t koff(int row, int k, unsigned sbo) {   // float offset in a K-major operand (LBO 128 B)
-  return ((row & 7) * 16 + (row >> 3) * sbo + (k & 3) * 4 + (k >> 2) * 128) / 4;
+// BF16 bits of a value, round to nearest even (from its FP32 rounding)
+uint16_t bf16_rn(double x) {
+  const float f = (float)x;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+double bf16_value(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
 }
 
-// write value x of element (row, k) as head at base[], tail at base[size + ...]
+// byte offset of element (row, k) in a K-major operand of esz-byte elements (LBO 128 B)
+size_t kbyte(int row, int k, unsigned sbo, int esz) {
+  const int ck = 16 / esz;
+  return (size_t)((row & 7) * 16 + (row >> 3) * sbo + (k % ck) * esz + (k / ck) * 128);
+}
+
+// value x of operand element (row, k) split into the pieces of the scheme; pieces
+// start at word `base` of the blob and lie `size` words apart
+template <int P>
 void put_split(std::vector<float>& b, size_t base, size_t size, int row, int k, unsigned sbo, double x) {
-  const float h = tf32_rna((float)x);
-  const float t = tf32_rna((float)(x - (double)h));
-  b[base + koff(row, k, sbo)] = h;
-  b[base + size + koff(row, k, sbo)] = t;
+  unsigned char* bytes = reinterpret_cast<unsigned char*>(b.data());
+  if (P == kTf32x3) {
+    const float h = tf32_rna((float)x);
+    const float t = tf32_rna((float)(x - (double)h));
+    const size_t o = kbyte(row, k, sbo, 4);
+    std::memcpy(bytes + 4 * base + o, &h, 4);
+    std::memcpy(bytes + 4 * (base + size) + o, &t, 4);
+  } else {
+    const uint16_t h = bf16_rn(x);
+    const double r = x - bf16_value(h);
+    const uint16_t m = bf16_rn(r);
+    const uint16_t l = bf16_rn(r - bf16_value(m));
+    const size_t o = kbyte(row, k, sbo, 2);
+    std::memcpy(bytes + 4 * base + o, &h, 2);
+    std::memcpy(bytes + 4 * (base + size) + o, &m, 2);
+    std::memcpy(bytes + 4 * (base + 2 * size) + o, &l, 2);
+  }
 }
 
-template <int K>
+template <int K, int P>
 std::vector<float> blob_t(const Tables& t) {
-  using L = TcLayout2D<K>;
+  using L = TcLayout2D<K, P>;
   const int N = L::N, QV = L::QV, QF = L::QF, NFM = L::NFM;
   std::vector<float> b(L::BLOB, 0.f);
   for (int n = 0; n < QV; ++n)
     for (int k = 0; k < N; ++k) {
-      put_split(b, L::oTAs, L::szTAs, n, k, L::SBO_NK, t.Bv[n * N + k]);
-      put_split(b, L::oTAw, L::szTAw, n, k, L::SBO_NK, t.wv[n] * t.Bv[n * N + k]);
+      put_split<P>(b, L::oTAs, L::szTAs, n, k, L::SBO_NK, t.Bv[n * N + k]);
+      put_split<P>(b, L::oTAw, L::szTAw, n, k, L::SBO_NK, t.wv[n] * t.Bv[n * N + k]);
     }
   for (int f = 0; f < L::NF; ++f)
     for (int q = 0; q < QF; ++q)
       for (int k = 0; k < N; ++k)
-        put_split(b, L::oTAw, L::szTAw, QV + f * QF + q, k, L::SBO_NK, t.wf[q] * t.Bf[(f * QF + q) * N + k]);
+        put_split<P>(b, L::oTAw, L::szTAw, QV + f * QF + q, k, L::SBO_NK, t.wf[q] * t.Bf[(f * QF + q) * N + k]);
   for (int q = 0; q < QV; ++q)
     for (int dd = 0; dd < 2; ++dd)
       for (int i = 0; i < N; ++i) b[L::oG + (q * 2 + dd) * L::NP4 + i] = (float)t.Gv[(q * N + i) * 2 + dd];
@@ -56,10 +88,10 @@ std::vector<float> blob_t(const Tables& t) {
   return b;
 }
 
-template <int K>
+template <int K, int P>
 cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
-  using L = TcLayout2D<K>;
-  auto kern = stage_tc_kernel<K>;
+  using L = TcLayout2D<K, P>;
+  auto kern = stage_tc_kernel<K, P>;
   if (!a) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_BYTES);
   const int tiles = (a->E + 127) / 128;
   if (tiles == 0) return cudaSuccess;
@@ -140,24 +172,32 @@ int tc_nk(int D, int K) {
   }
 }
 
-std::vector<float> tc_blob(int D, int K, const Tables& t) {
+std::vector<float> tc_blob(int D, int K, int P, const Tables& t) {
   if (D != 2) return {};
-  switch (K) {
-    case 1: return blob_t<1>(t);
-    case 2: return blob_t<2>(t);
-    case 3: return blob_t<3>(t);
-    case 4: return blob_t<4>(t);
+  switch (K * 2 + (P == kBf16x3 ? 1 : 0)) {
+    case 2: return blob_t<1, kTf32x3>(t);
+    case 3: return blob_t<1, kBf16x3>(t);
+    case 4: return blob_t<2, kTf32x3>(t);
+    case 5: return blob_t<2, kBf16x3>(t);
+    case 6: return blob_t<3, kTf32x3>(t);
+    case 7: return blob_t<3, kBf16x3>(t);
+    case 8: return blob_t<4, kTf32x3>(t);
+    case 9: return blob_t<4, kBf16x3>(t);
     default: return {};
   }
 }
 
-cudaError_t launch_stage_tc(int D, int K, const StageTcArgs* a, cudaStream_t s) {
+cudaError_t launch_stage_tc(int D, int K, int P, const StageTcArgs* a, cudaStream_t s) {
   if (D != 2) return cudaErrorInvalidValue;
-  switch (K) {
-    case 1: return launch_t<1>(a, s);
-    case 2: return launch_t<2>(a, s);
-    case 3: return launch_t<3>(a, s);
-    case 4: return launch_t<4>(a, s);
+  switch (K * 2 + (P == kBf16x3 ? 1 : 0)) {
+    case 2: return launch_t<1, kTf32x3>(a, s);
+    case 3: return launch_t<1, kBf16x3>(a, s);
+    case 4: return launch_t<2, kTf32x3>(a, s);
+    case 5: return launch_t<2, kBf16x3>(a, s);
+    case 6: return launch_t<3, kTf32x3>(a, s);
+    case 7: return launch_t<3, kBf16x3>(a, s);
+    case 8: return launch_t<4, kTf32x3>(a, s);
+    case 9: return launch_t<4, kBf16x3>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

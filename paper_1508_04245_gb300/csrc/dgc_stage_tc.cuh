@@ -80,6 +80,51 @@ __device__ __forceinline__ void split(float x, float& h, float& t) {
   t = tc::to_tf32(x - h);
 }
 
+// two FP32 values to a packed BF16 pair (round to nearest even), lo in the low half
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// exact three-piece BF16 split of two FP32 values: a = h + m + l (each residual
+// is exact in FP32 and the last has at most 8 significant bits)
+__device__ __forceinline__ void split3_bf16x2(float a, float b, uint32_t& h, uint32_t& m, uint32_t& l) {
+  h = bf16x2_rn(a, b);
+  const float ra = a - __uint_as_float(h << 16), rb = b - __uint_as_float(h & 0xFFFF0000u);
+  m = bf16x2_rn(ra, rb);
+  l = bf16x2_rn(ra - __uint_as_float(m << 16), rb - __uint_as_float(m & 0xFFFF0000u));
+}
+
+// The pieces of NK values x of this thread's operand row r into the pieces of one
+// field (base = first piece, pieces szOpA words apart), K-major core-matrix layout.
+template <int K, int P>
+__device__ __forceinline__ void put_operand(float* base, int r, const float* x) {
+  using L = TcLayout2D<K, P>;
+  const uint32_t row = (uint32_t)((r & 7) * 16 + (r >> 3) * L::SBO_NK);
+  if constexpr (P == kTf32x3) {
+#pragma unroll
+    for (int k4 = 0; k4 < L::NK; k4 += 4) {
+      float h[4], tl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) split(x[k4 + u], h[u], tl[u]);
+      const uint32_t o = (row + (k4 / 4) * L::LBO) / 4;
+      tc::st_shared_v4(base + o, h[0], h[1], h[2], h[3]);
+      tc::st_shared_v4(base + L::szOpA + o, tl[0], tl[1], tl[2], tl[3]);
+    }
+  } else {
+#pragma unroll
+    for (int k8 = 0; k8 < L::NK; k8 += 8) {
+      uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) split3_bf16x2(x[k8 + 2 * j], x[k8 + 2 * j + 1], hw[j], mw[j], lw[j]);
+      const uint32_t o = (row + (k8 / 8) * L::LBO) / 4;
+      tc::st_shared_v4u(base + o, hw[0], hw[1], hw[2], hw[3]);
+      tc::st_shared_v4u(base + L::szOpA + o, mw[0], mw[1], mw[2], mw[3]);
+      tc::st_shared_v4u(base + 2 * L::szOpA + o, lw[0], lw[1], lw[2], lw[3]);
+    }
+  }
+}
+
 template <int NCOL>
 __device__ __forceinline__ void tmem_load(uint32_t taddr, float* v) {
   static_assert(NCOL % 8 == 0, "TMEM loads in groups of 8 columns");
@@ -108,9 +153,9 @@ __device__ __forceinline__ void facet_traces(const float* Ef, const float* x, fl
     }
 }
 
-template <int K>
+template <int K, int P>
 __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
-  using L = TcLayout2D<K>;
+  using L = TcLayout2D<K, P>;
   constexpr int N = L::N, QV = L::QV, QF = L::QF, NFM = L::NFM, NF = L::NF, NK = L::NK;
   constexpr int NP4 = L::NP4, NFM4 = L::NFM4;
   extern __shared__ __align__(1024) float sm[];
@@ -206,36 +251,22 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     // ---- stage input v^n + din (staged by bulk copy) -> state operand of component c
     if (producer) {
     if (*abort_flag == 0 && !tc::mbar_wait(bar_st, it & 1)) *abort_flag = 1;
-    float w[NP4];
+    float w[NK];
 #pragma unroll
-    for (int i = 0; i < NP4; ++i) {
+    for (int i = 0; i < NK; ++i) {
       const int si = (c * N + (i < N ? i : 0)) * 128 + r;
       w[i] = (valid && i < N) ? stg[si] + (epi_din ? stg[L::TSOA_TILE + si] : 0.f) : 0.f;
     }
-#pragma unroll
-    for (int k4 = 0; k4 < NK; k4 += 4) {
-      float h[4], tl[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) tcimpl::split(k4 + u < NP4 ? w[k4 + u < NP4 ? k4 + u : 0] : 0.f, h[u], tl[u]);
-      const uint32_t o = tc::kmajor_off32(r, k4, L::LBO, L::SBO_NK) / 4;
-      tc::st_shared_v4(op + (c * 2 + 0) * L::szOpA + o, h[0], h[1], h[2], h[3]);
-      tc::st_shared_v4(op + (c * 2 + 1) * L::szOpA + o, tl[0], tl[1], tl[2], tl[3]);
-    }
+    tcimpl::put_operand<K, P>(op + c * L::PIECES * L::szOpA, r, w);
     }   // producer
     __syncthreads();   // the staged state has been read: its space takes the wind operands
     if (producer) {
     // ---- wind operand of dimension d = c from the staged coefficients --------------
     if (*abort_flag == 0 && !tc::mbar_wait(bar_w, it & 1)) *abort_flag = 1;
+    float x[NK];
 #pragma unroll
-    for (int k4 = 0; k4 < NK; k4 += 4) {
-      float h[4], tl[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)   // consecutive threads read consecutive words
-        tcimpl::split(valid ? wst[(c * NK + k4 + u) * 128 + r] : 0.f, h[u], tl[u]);
-      const uint32_t o = tc::kmajor_off32(r, k4, L::LBO, L::SBO_NK) / 4;
-      tc::st_shared_v4(op + ((2 + c) * 2 + 0) * L::szOpA + o, h[0], h[1], h[2], h[3]);
-      tc::st_shared_v4(op + ((2 + c) * 2 + 1) * L::szOpA + o, tl[0], tl[1], tl[2], tl[3]);
-    }
+    for (int k = 0; k < NK; ++k) x[k] = valid ? wst[(c * NK + k) * 128 + r] : 0.f;   // conflict-free
+    tcimpl::put_operand<K, P>(op + (2 + c) * L::PIECES * L::szOpA, r, x);
     }   // producer
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -245,19 +276,25 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     if (t == issuer_t && run) {
       if (next < ntiles) load_wind(next);   // the staging buffer is free again
       // ---- GEMM A ------------------------------------------------------------------
+      // products of pieces (A piece, B piece): TF32 hh, ht, th; BF16 hh, hm, mh, hl, lh, mm
+      constexpr int PA[6] = {0, 0, 1, 0, 2, 1};
+      constexpr int PB[6] = {0, 1, 0, 2, 0, 1};
       for (int f = 0; f < 4; ++f) {
         const bool wind = f >= 2;
-        const uint32_t idesc = tc::idesc_tf32(128, wind ? L::NAW : L::NAS);
+        const int NA = wind ? L::NAW : L::NAS;
+        const uint32_t idesc = P == kBf16x3 ? tc::idesc_bf16(128, NA) : tc::idesc_tf32(128, NA);
         const uint32_t dcol = wind ? L::cW + (f - 2) * L::NAW : L::cS + f * L::NAS;
         const uint32_t tab = bl_s + 4u * (wind ? L::oTAw : L::oTAs);
         const uint32_t tsz = 4u * (wind ? L::szTAw : L::szTAs);
         uint32_t acc = 0;
-        for (int pass = 0; pass < 3; ++pass) {
-          const uint32_t a_op = op_s + 4u * ((f * 2 + (pass == 2 ? 1 : 0)) * L::szOpA);
-          const uint32_t b_op = tab + (pass == 1 ? tsz : 0u);
-          for (int ks = 0; ks < NK / 8; ++ks) {
-            tc::mma_tf32(tbase + dcol, tc::smem_desc(a_op + ks * 2 * L::LBO, L::LBO, L::SBO_NK),
-                         tc::smem_desc(b_op + ks * 2 * L::LBO, L::LBO, L::SBO_NK), idesc, acc);
+        for (int pr = 0; pr < L::NPROD; ++pr) {
+          const uint32_t a_op = op_s + 4u * ((f * L::PIECES + PA[pr]) * L::szOpA);
+          const uint32_t b_op = tab + PB[pr] * tsz;
+          for (int ks = 0; ks < NK / L::KSTEP; ++ks) {
+            const uint64_t ad = tc::smem_desc(a_op + ks * 2 * L::LBO, L::LBO, L::SBO_NK);
+            const uint64_t bd = tc::smem_desc(b_op + ks * 2 * L::LBO, L::LBO, L::SBO_NK);
+            if constexpr (P == kBf16x3) tc::mma_bf16(tbase + dcol, ad, bd, idesc, acc);
+            else tc::mma_tf32(tbase + dcol, ad, bd, idesc, acc);
             acc = 1;
           }
         }

@@ -323,6 +323,6 @@ def potential_values(mesh: Mesh, potential) -> np.ndarray:
     """Evaluate a workload potential at the mesh's Lagrange nodes: [E, n_lag] or [E, n_lag, 3]."""
     X = mesh.point_coords(0)
     if mesh.dim == 2:
-        return potential(X[..., 0], X[..., 1])
+        return np.ascontiguousarray(potential(X[..., 0], X[..., 1]))
     A = potential(X[..., 0], X[..., 1], X[..., 2])        # [3, E, n_lag]
-    return np.moveaxis(A, 0, -1)
+    return np.ascontiguousarray(np.moveaxis(A, 0, -1))

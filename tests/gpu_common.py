@@ -9,7 +9,8 @@ from oracle import hdiv as OH
 from oracle import mesh as OM
 from paper_1508_04245_gb300 import workloads as W
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-6}
+TC_PRECS = ("tf32x3", "bf16x3")
 
 
 def tol_hdiv_chain(dim, k, prec):
@@ -25,7 +26,7 @@ def tol_hdiv_chain(dim, k, prec):
 
 
 def tc_ok(dim, k):
-    """The tensor-core (tf32x3) path covers triangles with k <= 4."""
+    """The tensor-core paths (tf32x3, bf16x3) cover triangles with k <= 4."""
     return dim == 2 and k <= 4
 
 

@@ -4,7 +4,7 @@ Sec. 3.2), C^U = I^T C^V I (Sec. 2.4) and the velocity extrapolation."""
 import numpy as np
 import pytest
 
-from gpu_common import TOL, make_case, maxrel, oracle_ds, tc_ok, tol_hdiv_chain
+from gpu_common import TC_PRECS, TOL, make_case, maxrel, oracle_ds, tc_ok, tol_hdiv_chain
 from oracle import dg as ODG
 from oracle import hdiv as OH
 from paper_1508_04245_gb300 import build, dgconv
@@ -42,9 +42,9 @@ CASES = [(2, 1, 5, 1), (2, 3, 4, 2), (2, 4, 4, 3), (2, 6, 2, 4), (3, 2, 2, 5)]
 
 
 @pytest.mark.parametrize("dim,k,n,seed", CASES)
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_conv_apply_hdiv(dim, k, n, seed, prec):
-    if prec == "tf32x3" and not tc_ok(dim, k):
+    if prec in TC_PRECS and not tc_ok(dim, k):
         pytest.skip("tensor-core path covers triangles k <= 4")
     verts, elems, om, wind, _, u = case(dim, k, n, seed)
     ref = ODG.conv_hdiv(ODG.ConvectionOracle(om, k, wind), u)
@@ -54,10 +54,10 @@ def test_conv_apply_hdiv(dim, k, n, seed, prec):
 
 
 @pytest.mark.parametrize("dim,k,n,seed", CASES)
-@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("extrapolated", [False, True])
 def test_oifs_rhs(dim, k, n, seed, prec, extrapolated):
-    if prec == "tf32x3" and not tc_ok(dim, k):
+    if prec in TC_PRECS and not tc_ok(dim, k):
         pytest.skip("tensor-core path covers triangles k <= 4")
     verts, elems, om, wind, wind2, u = case(dim, k, n, seed)
     ds = oracle_ds(om, k, wind)
@@ -86,7 +86,7 @@ def test_oifs_rhs_is_the_composition_of_the_single_calls():
     gm = dgconv.Mesh(2, 4, verts, elems)
     w, uu = cu(wind), cu(u)
     ds = oracle_ds(om, 4, wind)
-    for prec in ("fp64", "tf32x3"):
+    for prec in ("fp64", "tf32x3", "bf16x3"):
         fused = host(gm.oifs_rhs(uu, w, ds, 5, 3, prec=prec))
         v = gm.transfer(uu)
         gm.rk_substeps(w, v, ds, 5, 3, prec)

@@ -8,7 +8,7 @@ Tolerances are max-norm relative errors (reading A17): 1e-12 for FP64,
 import numpy as np
 import pytest
 
-from gpu_common import TOL, make_case, maxrel, oracle_ds, oracle_state, tc_ok
+from gpu_common import TC_PRECS, TOL, make_case, maxrel, oracle_ds, oracle_state, tc_ok
 from oracle import dg as ODG
 from oracle import hdiv as OH
 from paper_1508_04245_gb300 import build, dgconv
@@ -73,10 +73,10 @@ def test_transfer_T(cases, dim, k):
     assert maxrel(host(gm.transfer_T(cu(f))), ODG.transfer_T(om, k, f)) < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("dim,k", ORDERS)
 def test_conv_apply(cases, dim, k, prec):
-    if prec == "tf32x3" and not tc_ok(dim, k):
+    if prec in TC_PRECS and not tc_ok(dim, k):
         pytest.skip("tensor-core path covers triangles with k <= 4")
     verts, elems, pot, om, wind, gm = cases(dim, k)
     w = oracle_state(om, k)
@@ -86,11 +86,11 @@ def test_conv_apply(cases, dim, k, prec):
     gm.check()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("dim,k,scheme", [(2, 1, 3), (2, 2, 2), (2, 3, 3), (2, 4, 3), (2, 6, 3), (3, 1, 2), (3, 3, 3),
                                           (3, 4, 3)])
 def test_rk_substeps(cases, dim, k, scheme, prec):
-    if prec == "tf32x3" and not tc_ok(dim, k):
+    if prec in TC_PRECS and not tc_ok(dim, k):
         pytest.skip("tensor-core path covers triangles with k <= 4")
     verts, elems, pot, om, wind, gm = cases(dim, k)
     v0 = oracle_state(om, k, seed=5)

@@ -10,7 +10,7 @@ returned state element by element.
 import numpy as np
 import pytest
 
-from gpu_common import TOL, make_case, maxrel, oracle_state, tc_ok
+from gpu_common import TC_PRECS, TOL, make_case, maxrel, oracle_state, tc_ok
 from oracle import dg as ODG
 from oracle import hdiv as OH
 from oracle import mesh as OM
@@ -60,9 +60,9 @@ CASES = [(2, 1, 5, 1), (2, 2, 6, 2), (2, 4, 4, 3), (2, 6, 3, 4), (3, 2, 2, 5)]
 
 
 @pytest.mark.parametrize("dim,k,n,seed", CASES)
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_richardson_matches_oracle(dim, k, n, seed, prec):
-    if prec == "tf32x3" and not tc_ok(dim, k):
+    if prec in TC_PRECS and not tc_ok(dim, k):
         pytest.skip("tensor-core path covers triangles k <= 4")
     verts, elems, om, op, wind, g, v0, tau, ds = problem(dim, k, n, seed)
     red, it_o, hist_o, margin = reduction_for(op, g, v0, tau, ds, 12)
@@ -147,7 +147,7 @@ def test_richardson_full_size_residual_property():
     g = cu(W.uniform_coeffs(wl.seed + 11, gm.n_elem, 2, wl.k))
     tau = 2.0 * ODG.cfl_ds(om, wl.k, wind_o, 1.0)
     ds = ODG.richardson_ds(om, wl.k, wind_o, tau)
-    for prec, tol in (("fp64", 1e-12), ("tf32x3", 1e-5)):
+    for prec, tol in (("fp64", 1e-12), ("tf32x3", 1e-5), ("bf16x3", 1e-6)):
         v = gm.dg_zeros()
         iters, res = gm.richardson(wind, g, v, tau, ds, 0.0, 20, prec=prec)
         gm.check()
