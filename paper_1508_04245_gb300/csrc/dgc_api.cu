@@ -302,8 +302,10 @@ dgc_status launch_stage_tc(dgc_mesh* m, dgc_prec prec, int mode, const float* di
   a.status = m->status.ptr;
   a.E = m->E;
   a.mode = mode;
-  a.p = (float)p;
-  a.q = (float)q;
+  a.p_hi = (float)p;
+  a.p_lo = (float)(p - (double)a.p_hi);
+  a.q_hi = (float)q;
+  a.q_lo = (float)(q - (double)a.q_hi);
   cudaError_t err = dgc::launch_stage_tc(m->s.D, m->s.K, P, &a, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed: %s", cudaGetErrorString(err));
   return DGC_OK;

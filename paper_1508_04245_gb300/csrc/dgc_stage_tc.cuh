@@ -65,7 +65,10 @@ struct StageTcArgs {
   int* status;          // device status word
   int E;
   int mode;
-  float p, q;
+  // the coefficients p, q of the increment as FP32 pairs (hi + lo = the FP64 value
+  // to 2^-48): a single FP32 rounding of q = c ds would scale every substep's
+  // time step by the same (1 + eps), an error that grows linearly in time
+  float p_hi, p_lo, q_hi, q_lo;
 };
 
 namespace tcimpl {
@@ -276,9 +279,14 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     if (t == issuer_t && run) {
       if (next < ntiles) load_wind(next);   // the staging buffer is free again
       // ---- GEMM A ------------------------------------------------------------------
-      // products of pieces (A piece, B piece): TF32 hh, ht, th; BF16 hh, hm, mh, hl, lh, mm
-      constexpr int PA[6] = {0, 0, 1, 0, 2, 1};
-      constexpr int PB[6] = {0, 1, 0, 2, 0, 1};
+      // products of pieces (A piece, B piece), smallest first: the tensor-core FP32
+      // accumulation rounds partly toward zero, so the small correction products
+      // are summed while the accumulator is still small and the dominant head x
+      // head product comes last.  TF32: th, ht, hh; BF16: mm, lh, hl, mh, hm, hh
+      constexpr int PA3[3] = {1, 0, 0}, PB3[3] = {0, 1, 0};
+      constexpr int PA6[6] = {1, 2, 0, 1, 0, 0}, PB6[6] = {1, 0, 2, 0, 1, 0};
+      const int* PA = P == kBf16x3 ? PA6 : PA3;
+      const int* PB = P == kBf16x3 ? PB6 : PB3;
       for (int f = 0; f < 4; ++f) {
         const bool wind = f >= 2;
         const int NA = wind ? L::NAW : L::NAS;
@@ -452,7 +460,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
         const size_t ix = tsoa_index(e, c, i, N);
         const int si = (c * N + i) * 128 + r;
         const float ed = epi_din ? epi[L::TSOA_TILE + si] : 0.f;
-        const float inc = fmaf(a.p, ed, -a.q * rr[i]);
+        const float inc = fmaf(a.p_hi, ed, fmaf(a.p_lo, ed, -fmaf(a.q_hi, rr[i], a.q_lo * rr[i])));
         if (a.mode == 0) {
           a.dout[ix] = inc;
           xo[i] = epi[si] + inc;
