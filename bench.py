@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dgconv", choices=["dgconv", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=["fp32", "fp64", "tf32x3", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "fp64", "tf32x3", "bf16x3"])
     ap.add_argument("--no-other-precisions", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--substeps", type=int, default=None)
