@@ -20,6 +20,12 @@
  *
  * Conventions shared by every call
  * --------------------------------
+ * - Diagnostics: every compute entry point opens an NVTX range named after it
+ *   (visible under a profiler, free otherwise).  For tests of error handling,
+ *   the environment variable DGC_FAULT=alloc|capture|launch makes device
+ *   allocations, graph captures or kernel launches fail on the host before the
+ *   CUDA call is made; the call returns its DGC_ERR_* code and the handle stays
+ *   usable.
  * - Status: 0 (DGC_OK) on success, a negative DGC_ERR_* code otherwise; the
  *   message is available from dgc_last_error().  Argument errors are detected
  *   on the host before anything is launched.
@@ -252,6 +258,21 @@ dgc_status dgc_project(dgc_mesh* mesh, const double* vals, double* w_dg, void* s
 /* max |u(x_q)| over the volume quadrature points (degree 3k-1 rule) of all
  * elements.  Synchronizes `stream`; result in *out (host). */
 dgc_status dgc_max_wind_speed(dgc_mesh* mesh, const double* wind_hdiv, double* out, void* stream);
+
+/* Checkpoint of a DG state (not part of the paper: restart support).  The blob
+ * is host memory: a header (magic "DGCS", version 1, dim, k, n_elem, n_dg, the
+ * caller's time t and step count, FNV-1a 64 checksum of the payload) followed
+ * by the FP64 state in the DG layout.  dgc_state_save: with blob == NULL
+ * writes the needed size to *size; otherwise *size is the blob's capacity on
+ * input and the bytes written on output.  dgc_state_load: checks magic,
+ * version, the mesh's dim / k / n_elem and the checksum (DGC_ERR_ARG on any
+ * mismatch, nothing written), then copies the state to v_dg (device [n_dg])
+ * and returns t and step (each pointer may be NULL).  Both synchronize
+ * `stream`.  A run resumed from a saved state continues bit for bit. */
+dgc_status dgc_state_save(const dgc_mesh* mesh, const double* v_dg, double t, int64_t step, void* blob,
+                          int64_t* size, void* stream);
+dgc_status dgc_state_load(const dgc_mesh* mesh, const void* blob, int64_t size, double* v_dg, double* t,
+                          int64_t* step, void* stream);
 
 /* Device-side status of the handle: synchronizes `stream`, returns
  * DGC_ERR_TIMEOUT if a bounded wait inside a kernel gave up since the last

@@ -10,9 +10,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/dgconv.h"
 #include "dgc_kernels.h"
@@ -25,6 +28,22 @@ using dgc::Sizes;
 namespace {
 
 thread_local std::string g_last_error;
+
+// Host-side fault injection for tests of error propagation (no GPU is ever made
+// to fault): DGC_FAULT=alloc makes device allocations fail, =capture makes graph
+// captures fail to start, =launch makes kernel launches fail, each before the
+// CUDA call is made.
+bool injected(const char* what) {
+  const char* f = std::getenv("DGC_FAULT");
+  return f && std::strcmp(f, what) == 0;
+}
+
+// NVTX range over one entry point (a no-op unless a profiler is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+#define DGC_RANGE() NvtxRange dgc_range_(__func__)
 
 dgc_status fail(dgc_status code, const char* fmt, ...) {
   char buf[512];
@@ -50,6 +69,7 @@ struct DevBuf {
   size_t n = 0;
   cudaError_t alloc(size_t count) {
     if (count <= n && ptr) return cudaSuccess;
+    if (injected("alloc")) return cudaErrorMemoryAllocation;
     release();
     n = count;
     return cudaMalloc(&ptr, std::max<size_t>(count, 1) * sizeof(T));
@@ -237,6 +257,7 @@ dgc_status ensure_wind_scratch(dgc_mesh* m, bool fp32) {
 
 dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double* vn, double* vout,
                         double alpha, double beta, double gamma, cudaStream_t st) {
+  if (injected("launch")) return fail(DGC_ERR_CUDA, "stage kernel launch failed (injected)");
   dgc::StageArgs a;
   a.vin = vin;
   a.vn = vn;
@@ -288,6 +309,7 @@ dgc_status ensure_tc_scratch(dgc_mesh* m) {
 dgc_status launch_stage_tc(dgc_mesh* m, dgc_prec prec, int mode, const float* din, const float* trin, float* dout,
                            float* trout, double p, double q, double* v, cudaStream_t st) {
   const int P = prec == DGC_BF16X3 ? 1 : 0;
+  if (injected("launch")) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed (injected)");
   dgc::StageTcArgs a;
   a.vf = m->tsf.ptr;
   a.din = din;
@@ -430,6 +452,12 @@ dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, in
   return DGC_OK;
 }
 
+// begin a stream capture (fails before any CUDA call under DGC_FAULT=capture)
+cudaError_t begin_capture(cudaStream_t st) {
+  if (injected("capture")) return cudaErrorStreamCaptureUnsupported;
+  return cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+}
+
 // forget the cached batch graphs that contain this mesh
 void drop_batch_graphs(const dgc_mesh* mesh) {
   std::lock_guard<std::mutex> lock(g_batch_mu);
@@ -480,7 +508,7 @@ dgc_status rich_build(dgc_mesh* m, const double* wind, const double* g, double* 
   if (!m->body_stream) DGC_CUDA(cudaStreamCreateWithFlags(&m->body_stream, cudaStreamNonBlocking));
   cudaStream_t cs = m->capture_stream, bs = m->body_stream;
   const long n = (long)m->E * m->s.D * m->s.N;
-  DGC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  DGC_CUDA(begin_capture(cs));
   cudaGraph_t graph = nullptr;
   dgc_status rc = DGC_OK;
   cudaError_t err = cudaSuccess;
@@ -561,6 +589,7 @@ dgc_status dgc_last_error(char* buf, int len) {
 
 dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int n_elem, const int32_t* elems,
                            void* stream, dgc_mesh** out) {
+  DGC_RANGE();
   if (!out) return fail(DGC_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(DGC_ERR_UNSUPPORTED, "dim must be 2 or 3 (got %d)", dim);
@@ -672,12 +701,14 @@ dgc_status dgc_mesh_info(const dgc_mesh* mesh, int64_t* info) {
 }
 
 dgc_status dgc_geometry(dgc_mesh* mesh, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   DGC_CUDA(dgc::launch_geometry(mesh->view(), as_stream(stream)));
   return DGC_OK;
 }
 
 dgc_status dgc_transfer(dgc_mesh* mesh, const double* u_hdiv, double* w_dg, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (!u_hdiv || !w_dg) return fail(DGC_ERR_ARG, "NULL vector");
   DGC_CUDA(dgc::launch_transfer(mesh->view(), u_hdiv, w_dg, as_stream(stream)));
@@ -685,6 +716,7 @@ dgc_status dgc_transfer(dgc_mesh* mesh, const double* u_hdiv, double* w_dg, void
 }
 
 dgc_status dgc_transfer_T(dgc_mesh* mesh, const double* f_dg, double* g_hdiv, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (!f_dg || !g_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
   DGC_CUDA(mesh->zbuf.alloc((size_t)mesh->E * mesh->s.NF * mesh->s.NFM));
@@ -693,6 +725,7 @@ dgc_status dgc_transfer_T(dgc_mesh* mesh, const double* f_dg, double* g_hdiv, vo
 }
 
 dgc_status dgc_mass_apply(dgc_mesh* mesh, const double* v_dg, double* out_dg, int inverse, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (!v_dg || !out_dg) return fail(DGC_ERR_ARG, "NULL vector");
   DGC_CUDA(dgc::launch_mass(mesh->view(), v_dg, out_dg, inverse != 0, as_stream(stream)));
@@ -701,6 +734,7 @@ dgc_status dgc_mass_apply(dgc_mesh* mesh, const double* v_dg, double* out_dg, in
 
 dgc_status dgc_conv_apply(dgc_mesh* mesh, const double* wind_hdiv, const double* w_dg, double* out_dg,
                           dgc_prec prec, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (dgc_status rc = check_prec(mesh, prec)) return rc;
   if (!wind_hdiv || !w_dg || !out_dg) return fail(DGC_ERR_ARG, "NULL vector");
@@ -714,6 +748,7 @@ dgc_status dgc_conv_apply(dgc_mesh* mesh, const double* wind_hdiv, const double*
 
 dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg, double ds, int nsteps,
                            dgc_scheme scheme, dgc_prec prec, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (dgc_status rc = check_prec(mesh, prec)) return rc;
   if (!wind_hdiv || !v_dg) return fail(DGC_ERR_ARG, "NULL vector");
@@ -731,7 +766,7 @@ dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg
     if (mesh->graph) cudaGraphExecDestroy(mesh->graph);
     mesh->graph = nullptr;
     if (!mesh->capture_stream) DGC_CUDA(cudaStreamCreateWithFlags(&mesh->capture_stream, cudaStreamNonBlocking));
-    DGC_CUDA(cudaStreamBeginCapture(mesh->capture_stream, cudaStreamCaptureModeThreadLocal));
+    DGC_CUDA(begin_capture(mesh->capture_stream));
     dgc_status rc = rk_sequence(mesh, wind_hdiv, v_dg, ds, nsteps, (int)scheme, prec, mesh->capture_stream);
     cudaGraph_t g = nullptr;
     cudaError_t err = cudaStreamEndCapture(mesh->capture_stream, &g);
@@ -755,6 +790,7 @@ dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg
 dgc_status dgc_richardson(dgc_mesh* mesh, const double* wind_hdiv, const double* g_dg, double* v_dg, double tau,
                           double ds, double reduction, int max_iter, dgc_prec prec, int32_t* iters_dev,
                           double* res_dev, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (dgc_status rc = check_prec(mesh, prec)) return rc;
   if (!wind_hdiv || !g_dg || !v_dg || !iters_dev) return fail(DGC_ERR_ARG, "NULL argument");
@@ -792,6 +828,7 @@ dgc_status dgc_richardson(dgc_mesh* mesh, const double* wind_hdiv, const double*
 
 dgc_status dgc_autotune(dgc_mesh* mesh, const double* wind_hdiv, dgc_prec prec, int reps, int* block_out,
                         void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (dgc_status rc = check_prec(mesh, prec)) return rc;
   if (!wind_hdiv) return fail(DGC_ERR_ARG, "wind_hdiv is NULL");
@@ -855,6 +892,7 @@ dgc_status dgc_autotune(dgc_mesh* mesh, const double* wind_hdiv, dgc_prec prec, 
 
 dgc_status dgc_wind_extrapolate(dgc_mesh* mesh, int n_terms, const double* const* fields, const double* coefs,
                                 double* out_hdiv, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (n_terms < 1 || n_terms > dgc::kMaxTerms)
     return fail(DGC_ERR_ARG, "n_terms must lie in 1..%d (got %d)", dgc::kMaxTerms, n_terms);
@@ -874,6 +912,7 @@ dgc_status dgc_wind_extrapolate(dgc_mesh* mesh, int n_terms, const double* const
 
 dgc_status dgc_conv_apply_hdiv(dgc_mesh* mesh, const double* wind_hdiv, const double* u_hdiv, double* out_hdiv,
                                dgc_prec prec, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (dgc_status rc = check_prec(mesh, prec)) return rc;
   if (!wind_hdiv || !u_hdiv || !out_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
@@ -898,6 +937,7 @@ dgc_status dgc_conv_apply_hdiv(dgc_mesh* mesh, const double* wind_hdiv, const do
 dgc_status dgc_oifs_rhs(dgc_mesh* mesh, const double* u_hdiv, const double* wind_hdiv, const double* wind_prev_hdiv,
                         double dt_prev, double* out_hdiv, double ds, int nsteps, dgc_scheme scheme, dgc_prec prec,
                         void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (dgc_status rc = check_prec(mesh, prec)) return rc;
   if (!u_hdiv || !wind_hdiv || !out_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
@@ -927,7 +967,7 @@ dgc_status dgc_oifs_rhs(dgc_mesh* mesh, const double* u_hdiv, const double* wind
     mesh->oifs_graph = nullptr;
     if (!mesh->capture_stream) DGC_CUDA(cudaStreamCreateWithFlags(&mesh->capture_stream, cudaStreamNonBlocking));
     cudaStream_t cs = mesh->capture_stream;
-    DGC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    DGC_CUDA(begin_capture(cs));
     // a2: v = I u;  Q: nsteps substeps;  out = I^T M^V v
     dgc_status rc = DGC_OK;
     cudaError_t err = dgc::launch_transfer(mesh->view(), u_hdiv, mesh->ov.ptr, cs);
@@ -958,6 +998,7 @@ dgc_status dgc_oifs_rhs(dgc_mesh* mesh, const double* u_hdiv, const double* wind
 dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const double* const* winds,
                                  double* const* states, const double* ds, const int* nsteps, dgc_scheme scheme,
                                  dgc_prec prec, void* stream) {
+  DGC_RANGE();
   if (n_inst < 0) return fail(DGC_ERR_ARG, "n_inst must be >= 0");
   if (n_inst == 0) return DGC_OK;
   if (!meshes || !winds || !states || !ds || !nsteps) return fail(DGC_ERR_ARG, "NULL argument array");
@@ -1001,7 +1042,7 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
     auto cleanup = [&]() {
       for (cudaEvent_t e : evs) cudaEventDestroy(e);
     };
-    DGC_CUDA(cudaStreamBeginCapture(main_st, cudaStreamCaptureModeThreadLocal));
+    DGC_CUDA(begin_capture(main_st));
     cudaEvent_t fork;
     cudaError_t err = new_event(&fork);
     if (err == cudaSuccess) err = cudaEventRecord(fork, main_st);
@@ -1070,6 +1111,7 @@ dgc_status dgc_point_coords(const dgc_mesh* mesh, int kind, double* xyz, int64_t
 }
 
 dgc_status dgc_wind_from_potential(dgc_mesh* mesh, const double* pot, double* u_hdiv, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (!pot || !u_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
   DGC_CUDA(dgc::launch_wind_from_potential(mesh->view(), pot, u_hdiv, as_stream(stream)));
@@ -1077,6 +1119,7 @@ dgc_status dgc_wind_from_potential(dgc_mesh* mesh, const double* pot, double* u_
 }
 
 dgc_status dgc_hdiv_interpolate(dgc_mesh* mesh, const double* vals, double* u_hdiv, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (!vals || !u_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
   DGC_CUDA(dgc::launch_hdiv_interpolate(mesh->view(), vals, u_hdiv, as_stream(stream)));
@@ -1084,6 +1127,7 @@ dgc_status dgc_hdiv_interpolate(dgc_mesh* mesh, const double* vals, double* u_hd
 }
 
 dgc_status dgc_project(dgc_mesh* mesh, const double* vals, double* w_dg, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (!vals || !w_dg) return fail(DGC_ERR_ARG, "NULL vector");
   DGC_CUDA(dgc::launch_project(mesh->view(), vals, w_dg, as_stream(stream)));
@@ -1091,6 +1135,7 @@ dgc_status dgc_project(dgc_mesh* mesh, const double* vals, double* w_dg, void* s
 }
 
 dgc_status dgc_max_wind_speed(dgc_mesh* mesh, const double* wind_hdiv, double* out, void* stream) {
+  DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (!wind_hdiv || !out) return fail(DGC_ERR_ARG, "NULL argument");
   cudaStream_t st = as_stream(stream);
@@ -1148,6 +1193,82 @@ dgc_status dgc_connectivity(int dim, int n_vert, int n_elem, const int32_t* elem
     if (orient) orient[j] = con.orient[j];
   }
   if (n_facets) *n_facets = con.n_facets;
+  return DGC_OK;
+}
+
+// ---- checkpoint / resume ----------------------------------------------------------
+namespace {
+struct StateHeader {
+  char magic[4];          // "DGCS"
+  uint32_t version;       // 1
+  int32_t dim, k;
+  int64_t n_elem, n_dg;
+  double t;
+  int64_t step;
+  uint64_t checksum;      // FNV-1a 64 of the payload bytes
+};
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t j = 0; j < n; ++j) {
+    h ^= p[j];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+}  // namespace
+
+dgc_status dgc_state_save(const dgc_mesh* mesh, const double* v_dg, double t, int64_t step, void* blob,
+                          int64_t* size, void* stream) {
+  DGC_RANGE();
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!v_dg || !size) return fail(DGC_ERR_ARG, "NULL argument");
+  const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
+  const size_t bytes = sizeof(StateHeader) + n * sizeof(double);
+  if (!blob) {
+    *size = (int64_t)bytes;
+    return DGC_OK;
+  }
+  if (*size < (int64_t)bytes) return fail(DGC_ERR_ARG, "blob holds %lld bytes, %zu needed", (long long)*size, bytes);
+  unsigned char* out = static_cast<unsigned char*>(blob);
+  cudaStream_t st = as_stream(stream);
+  DGC_CUDA(cudaMemcpyAsync(out + sizeof(StateHeader), v_dg, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DGC_CUDA(cudaStreamSynchronize(st));
+  StateHeader h;
+  std::memcpy(h.magic, "DGCS", 4);
+  h.version = 1;
+  h.dim = mesh->s.D;
+  h.k = mesh->s.K;
+  h.n_elem = mesh->E;
+  h.n_dg = (int64_t)n;
+  h.t = t;
+  h.step = step;
+  h.checksum = fnv1a64(out + sizeof(StateHeader), n * sizeof(double));
+  std::memcpy(out, &h, sizeof(h));
+  *size = (int64_t)bytes;
+  return DGC_OK;
+}
+
+dgc_status dgc_state_load(const dgc_mesh* mesh, const void* blob, int64_t size, double* v_dg, double* t,
+                          int64_t* step, void* stream) {
+  DGC_RANGE();
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!blob || !v_dg) return fail(DGC_ERR_ARG, "NULL argument");
+  if (size < (int64_t)sizeof(StateHeader)) return fail(DGC_ERR_ARG, "blob too short for a header");
+  StateHeader h;
+  std::memcpy(&h, blob, sizeof(h));
+  const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
+  if (std::memcmp(h.magic, "DGCS", 4) != 0 || h.version != 1) return fail(DGC_ERR_ARG, "not a dgconv state blob");
+  if (h.dim != mesh->s.D || h.k != mesh->s.K || h.n_elem != mesh->E || h.n_dg != (int64_t)n)
+    return fail(DGC_ERR_ARG, "blob is for dim %d, k %d, %lld elements; mesh has dim %d, k %d, %d elements", h.dim, h.k,
+                (long long)h.n_elem, mesh->s.D, mesh->s.K, mesh->E);
+  if (size < (int64_t)(sizeof(StateHeader) + n * sizeof(double))) return fail(DGC_ERR_ARG, "blob truncated");
+  const unsigned char* payload = static_cast<const unsigned char*>(blob) + sizeof(StateHeader);
+  if (fnv1a64(payload, n * sizeof(double)) != h.checksum) return fail(DGC_ERR_ARG, "blob checksum mismatch");
+  cudaStream_t st = as_stream(stream);
+  DGC_CUDA(cudaMemcpyAsync(v_dg, payload, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  DGC_CUDA(cudaStreamSynchronize(st));
+  if (t) *t = h.t;
+  if (step) *step = h.step;
   return DGC_OK;
 }
 

@@ -41,6 +41,8 @@ SIGNATURES = {
     "dgc_conv_apply_hdiv": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp],
     "dgc_wind_extrapolate": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp],
     "dgc_autotune": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp],
+    "dgc_state_save": [_vp, _vp, ctypes.c_double, ctypes.c_int64, _vp, _i64p, _vp],
+    "dgc_state_load": [_vp, _vp, ctypes.c_int64, _vp, _dp, _i64p, _vp],
     "dgc_batch_rk_substeps": [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp],
     "dgc_point_coords": [_vp, ctypes.c_int, _vp, _i64p],
     "dgc_wind_from_potential": [_vp, _vp, _vp, _vp],
@@ -230,6 +232,25 @@ class Mesh:
         check(lib().dgc_autotune(self._h, _ptr(wind, self.n_hdiv, "wind"), PREC[prec], int(reps), ctypes.byref(b),
                                  _stream(stream)))
         return b.value
+
+    def state_save(self, v_dg, t: float = 0.0, step: int = 0, stream=None) -> bytes:
+        """Checkpoint blob of a DG state (see dgc_state_save)."""
+        size = ctypes.c_int64()
+        check(lib().dgc_state_save(self._h, _ptr(v_dg, self.n_dg, "v_dg"), float(t), int(step), None,
+                                   ctypes.byref(size), _stream(stream)))
+        buf = ctypes.create_string_buffer(size.value)
+        check(lib().dgc_state_save(self._h, _ptr(v_dg, self.n_dg, "v_dg"), float(t), int(step), buf,
+                                   ctypes.byref(size), _stream(stream)))
+        return buf.raw[:size.value]
+
+    def state_load(self, blob: bytes, out=None, stream=None):
+        """Restore a DG state from a checkpoint blob; returns (v_dg, t, step)."""
+        out = self.dg_zeros() if out is None else out
+        t, step = ctypes.c_double(), ctypes.c_int64()
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        check(lib().dgc_state_load(self._h, buf, len(blob), _ptr(out, self.n_dg, "out"), ctypes.byref(t),
+                                   ctypes.byref(step), _stream(stream)))
+        return out, t.value, step.value
 
     def richardson_ds(self, wind, tau: float) -> float:
         """Pseudo-time step 1 / (1 + beta^2), beta = tau (2k+1) max|u| / min h_T (stable for every mode)."""
