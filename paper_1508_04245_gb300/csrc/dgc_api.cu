@@ -214,22 +214,23 @@ struct dgc_mesh {
 
 namespace {
 
-// stage-table blob in the layout of dgc::StageTab
+// stage-table blob in the layout of dgc::StageTab (rows padded to 4 values)
 template <typename T>
 std::vector<T> stage_blob(const dgc::Tables& t) {
   const Sizes& s = t.s;
-  auto pad = [](size_t n) { return (n + 3) / 4 * 4; };
-  std::vector<T> out;
-  auto put = [&](const std::vector<double>& v) {
-    size_t o = out.size();
-    out.resize(o + pad(v.size()), (T)0);
-    for (size_t j = 0; j < v.size(); ++j) out[o + j] = (T)v[j];
-  };
-  put(t.Bv);
-  put(t.Gv);
-  put(t.Ef);
-  put(t.Qt);
-  (void)s;
+  const int D = s.D, N = s.N, NFM = s.NFM, NF = s.NF;
+  const int NP4 = (N + 3) / 4 * 4, NFM4 = (NFM + 3) / 4 * 4;
+  const size_t oG = (size_t)s.QV * NP4, oE = oG + (size_t)s.QV * D * NP4, oQ = oE + (size_t)NF * NFM * NP4;
+  std::vector<T> out(oQ + (size_t)s.QF * NFM4, (T)0);
+  for (int q = 0; q < s.QV; ++q)
+    for (int i = 0; i < N; ++i) {
+      out[(size_t)q * NP4 + i] = (T)t.Bv[(size_t)q * N + i];
+      for (int d = 0; d < D; ++d) out[oG + ((size_t)q * D + d) * NP4 + i] = (T)t.Gv[((size_t)q * N + i) * D + d];
+    }
+  for (int fm = 0; fm < NF * NFM; ++fm)
+    for (int i = 0; i < N; ++i) out[oE + (size_t)fm * NP4 + i] = (T)t.Ef[(size_t)fm * N + i];
+  for (int q = 0; q < s.QF; ++q)
+    for (int m = 0; m < NFM; ++m) out[oQ + (size_t)q * NFM4 + m] = (T)t.Qt[(size_t)q * NFM + m];
   return out;
 }
 

@@ -42,16 +42,35 @@ struct StageArgs {
   double alpha, beta, gamma;
 };
 
+// Rows padded to multiples of 4 values (zero filled) so the kernel reads them in
+// 16-byte-aligned groups of four.
 template <int D, int K>
 struct StageTab {
   using Dm = Dims<D, K>;
   static constexpr int pad(int n) { return (n + 3) / 4 * 4; }
-  static constexpr int oB = 0;                                        // [QV][N]
-  static constexpr int oG = pad(Dm::QV * Dm::N);                      // [QV][N][D]
-  static constexpr int oE = oG + pad(Dm::QV * Dm::N * D);             // [NF][NFM][N]
-  static constexpr int oQ = oE + pad(Dm::NF * Dm::NFM * Dm::N);       // [QF][NFM]
-  static constexpr int size = oQ + pad(Dm::QF * Dm::NFM);
+  static constexpr int NP4 = pad(Dm::N), NFM4 = pad(Dm::NFM);
+  static constexpr int oB = 0;                                        // [QV][NP4]
+  static constexpr int oG = oB + Dm::QV * NP4;                        // [QV][D][NP4]
+  static constexpr int oE = oG + Dm::QV * D * NP4;                    // [NF][NFM][NP4]
+  static constexpr int oQ = oE + Dm::NF * Dm::NFM * NP4;              // [QF][NFM4]
+  static constexpr int size = oQ + Dm::QF * NFM4;
 };
+
+// four consecutive table values from a 16-byte-aligned address
+__device__ __forceinline__ void load4(const float* p, float* o) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* o) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = b.x;
+  o[3] = b.y;
+}
 
 template <typename T, int D, int K>
 constexpr bool stage_tab_in_smem() {
@@ -76,7 +95,7 @@ constexpr int stage_block_default() {
 int stage_block_get(int D, int K, bool fp32);   // tuned value or 0
 
 template <int D, int K, typename T, int CPT, bool SMEM>
-__global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
+__global__ void __launch_bounds__(256, 1) stage_kernel(StageArgs a) {
   using Dm = Dims<D, K>;
   using TB = StageTab<D, K>;
   constexpr int N = Dm::N, QV = Dm::QV, QF = Dm::QF, NFM = Dm::NFM, NF = Dm::NF;
@@ -114,33 +133,68 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
     }
 
   // ---- volume term: r -= sum_q sum_a Uw[q][a] w(xi_q) d_a psi_i(xi_q) ------
+  // Table rows are read four values at a time, except for FP32 tetrahedra with
+  // k >= 4, where the wider unrolled form no longer fits the register file and
+  // the one-value form is kept.
+  constexpr int NP4 = TB::NP4, NFM4 = TB::NFM4;
+  constexpr bool VEC = !(D == 3 && K >= 4 && sizeof(T) == 4);
 #pragma unroll 1
   for (int q = 0; q < QV; ++q) {
-    const T* Bq = Bv + q * N;
+    const T* Bq = Bv + q * NP4;
     T wq[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) wq[c] = (T)0;
+    if constexpr (!VEC) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const T b = Bq[i];
+      for (int i = 0; i < N; ++i) {
+        const T b = Bq[i];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) wq[c] += b * w[c][i];
+        for (int c = 0; c < CPT; ++c) wq[c] += b * w[c][i];
+      }
+    } else
+#pragma unroll
+    for (int i4 = 0; i4 < NP4; i4 += 4) {
+      T b[4];
+      load4(Bq + i4, b);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i4 + u < N ? i4 + u : N - 1;
+        if (i4 + u < N)
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) wq[c] += b[u] * w[c][i];
+      }
     }
     T p[CPT][D];
 #pragma unroll
     for (int aa = 0; aa < D; ++aa) {
-      const T u = Uw[(long)(q * D + aa) * E + e];
+      const T uu = Uw[(long)(q * D + aa) * E + e];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) p[c][aa] = u * wq[c];
+      for (int c = 0; c < CPT; ++c) p[c][aa] = uu * wq[c];
     }
-    const T* Gq = Gv + q * N * D;
+    const T* Gq = Gv + q * D * NP4;
+    if constexpr (!VEC) {
 #pragma unroll
-    for (int i = 0; i < N; ++i)
+      for (int i = 0; i < N; ++i)
 #pragma unroll
-      for (int aa = 0; aa < D; ++aa) {
-        const T g = Gq[i * D + aa];
+        for (int aa = 0; aa < D; ++aa) {
+          const T g = Gq[aa * NP4 + i];
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) r[c][i] -= p[c][aa] * g;
+          for (int c = 0; c < CPT; ++c) r[c][i] -= p[c][aa] * g;
+        }
+    } else
+#pragma unroll
+    for (int aa = 0; aa < D; ++aa)
+#pragma unroll
+      for (int i4 = 0; i4 < NP4; i4 += 4) {
+        T g[4];
+        load4(Gq + aa * NP4 + i4, g);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i4 + u < N ? i4 + u : N - 1;
+          if (i4 + u < N)
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) r[c][i] -= p[c][aa] * g[u];
+        }
       }
   }
 
@@ -148,58 +202,114 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
 #pragma unroll 1
   for (int f = 0; f < NF; ++f) {
     const int code = a.nbr[(long)e * NF + f];
-    const T* Eo = Ef + f * NFM * N;
+    const T* Eo = Ef + f * NFM * NP4;
     T to[CPT][NFM], tn[CPT][NFM], phi[CPT][NFM];
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
 #pragma unroll
       for (int m = 0; m < NFM; ++m) {
         T acc = (T)0;
+        if constexpr (!VEC) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) acc += Eo[m * N + i] * w[c][i];
+          for (int i = 0; i < N; ++i) acc += Eo[m * NP4 + i] * w[c][i];
+        } else
+#pragma unroll
+        for (int i4 = 0; i4 < NP4; i4 += 4) {
+          T ev[4];
+          load4(Eo + m * NP4 + i4, ev);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (i4 + u < N) acc += ev[u] * w[c][i4 + u < N ? i4 + u : N - 1];
+        }
         to[c][m] = acc;
         tn[c][m] = (T)0;
         phi[c][m] = (T)0;
       }
     if (code >= 0) {
       const int ne = code >> 2, fn = code & 3;
-      const T* En = Ef + fn * NFM * N;
+      const T* En = Ef + fn * NFM * NP4;
       const double* __restrict__ wn = a.vin + ((long)ne * D + c0) * N;
+      if constexpr (!VEC) {
 #pragma unroll
-      for (int i = 0; i < N; ++i)
+        for (int i = 0; i < N; ++i)
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          const T x = (T)wn[c * N + i];
+          for (int c = 0; c < CPT; ++c) {
+            const T x = (T)wn[c * N + i];
 #pragma unroll
-          for (int m = 0; m < NFM; ++m) tn[c][m] += En[m * N + i] * x;
+            for (int m = 0; m < NFM; ++m) tn[c][m] += En[m * NP4 + i] * x;
+          }
+      } else
+#pragma unroll
+      for (int i4 = 0; i4 < NP4; i4 += 4) {
+        T x[CPT][4];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) x[c][u] = i4 + u < N ? (T)wn[c * N + (i4 + u < N ? i4 + u : 0)] : (T)0;
+#pragma unroll
+        for (int m = 0; m < NFM; ++m) {
+          T ev[4];
+          load4(En + m * NP4 + i4, ev);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (i4 + u < N)
+#pragma unroll
+              for (int c = 0; c < CPT; ++c) tn[c][m] += ev[u] * x[c][u];
         }
+      }
     }
 #pragma unroll 1
     for (int q = 0; q < QF; ++q) {
       const T fw = Fw[(long)(f * QF + q) * E + e];
-      const T* Qq = Qt + q * NFM;
+      T qq[NFM4];
+#pragma unroll
+      for (int m4 = 0; m4 < NFM4; m4 += 4) load4(Qt + q * NFM4 + m4, qq + m4);
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         T o = (T)0, n = (T)0;
 #pragma unroll
         for (int m = 0; m < NFM; ++m) {
-          o += Qq[m] * to[c][m];
-          n += Qq[m] * tn[c][m];
+          o += qq[m] * to[c][m];
+          n += qq[m] * tn[c][m];
         }
         const T val = fw * (fw >= (T)0 ? o : n);
 #pragma unroll
-        for (int m = 0; m < NFM; ++m) phi[c][m] += Qq[m] * val;
+        for (int m = 0; m < NFM; ++m) phi[c][m] += qq[m] * val;
       }
     }
+    if constexpr (!VEC) {
 #pragma unroll
-    for (int i = 0; i < N; ++i)
+      for (int i = 0; i < N; ++i)
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        T acc = (T)0;
+        for (int c = 0; c < CPT; ++c) {
+          T acc = (T)0;
 #pragma unroll
-        for (int m = 0; m < NFM; ++m) acc += Eo[m * N + i] * phi[c][m];
-        r[c][i] += acc;
+          for (int m = 0; m < NFM; ++m) acc += Eo[m * NP4 + i] * phi[c][m];
+          r[c][i] += acc;
+        }
+    } else
+#pragma unroll
+    for (int i4 = 0; i4 < NP4; i4 += 4) {
+      T acc[CPT][4];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[c][u] = (T)0;
+#pragma unroll
+      for (int m = 0; m < NFM; ++m) {
+        T ev[4];
+        load4(Eo + m * NP4 + i4, ev);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[c][u] += ev[u] * phi[c][m];
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i4 + u < N)
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) r[c][i4 + u < N ? i4 + u : N - 1] += acc[c][u];
+    }
   }
 
   // ---- epilogue: RK stage combination in FP64 --------------------------------
