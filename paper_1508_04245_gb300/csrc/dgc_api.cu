@@ -130,6 +130,8 @@ struct dgc_mesh {
   DevBuf<float> tab32, tcblob, tcblob16, wcoef, trA, trB;   // tensor-core blobs: TF32x3, BF16x3
   DevBuf<double> ts0;              // tile-blocked FP64 state of the tensor-core path
   DevBuf<float> tsf, d1, d2;       // its FP32 copy and the FP32 stage increments
+  DevBuf<double> ts1, tsg;         // pseudo-time solve on that path: second state, right-hand side
+  DevBuf<float> tsf1;              // and the second state's FP32 copy
   DevBuf<int> status;
   // scratch
   DevBuf<double> Uw64, Fw64, stage1, stage2, zbuf;
@@ -203,6 +205,9 @@ struct dgc_mesh {
     trB.release();
     ts0.release();
     tsf.release();
+    ts1.release();
+    tsg.release();
+    tsf1.release();
     d1.release();
     d2.release();
     status.release();
@@ -311,7 +316,7 @@ dgc_status launch_stage_tc(dgc_mesh* m, dgc_prec prec, int mode, const float* di
                            float* trout, double p, double q, double* v, cudaStream_t st) {
   const int P = prec == DGC_BF16X3 ? 1 : 0;
   if (injected("launch")) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed (injected)");
-  dgc::StageTcArgs a;
+  dgc::StageTcArgs a{};   // every pointer a mode does not use is null
   a.vf = m->tsf.ptr;
   a.din = din;
   a.trin = trin;
@@ -329,6 +334,35 @@ dgc_status launch_stage_tc(dgc_mesh* m, dgc_prec prec, int mode, const float* di
   a.p_lo = (float)(p - (double)a.p_hi);
   a.q_hi = (float)q;
   a.q_lo = (float)(q - (double)a.q_hi);
+  cudaError_t err = dgc::launch_stage_tc(m->s.D, m->s.K, P, &a, st);
+  if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed: %s", cudaGetErrorString(err));
+  return DGC_OK;
+}
+
+// one fused pseudo-time iteration on the tensor-core path (mode 3 of dgc::StageTcArgs)
+dgc_status launch_rich_tc(dgc_mesh* m, dgc_prec prec, double tau, double ds, cudaStream_t st) {
+  const int P = prec == DGC_BF16X3 ? 1 : 0;
+  if (injected("launch")) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed (injected)");
+  dgc::StageTcArgs a{};
+  a.din = nullptr;
+  a.wcoef = m->wcoef.ptr;
+  a.nbr = m->nbr.ptr;
+  a.blob = P ? m->tcblob16.ptr : m->tcblob.ptr;
+  a.status = m->status.ptr;
+  a.E = m->E;
+  a.mode = 3;
+  a.ctrl = m->rstate.ptr;
+  a.vf2[0] = m->tsf.ptr;
+  a.vf2[1] = m->tsf1.ptr;
+  a.tr2[0] = m->trA.ptr;
+  a.tr2[1] = m->trB.ptr;
+  a.v2[0] = m->ts0.ptr;
+  a.v2[1] = m->ts1.ptr;
+  a.g = m->tsg.ptr;
+  a.detJ = m->detJ.ptr;
+  a.tau = tau;
+  a.ds = ds;
+  a.partials = m->partials.ptr;
   cudaError_t err = dgc::launch_stage_tc(m->s.D, m->s.K, P, &a, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed: %s", cudaGetErrorString(err));
   return DGC_OK;
@@ -509,6 +543,9 @@ dgc_status rich_build(dgc_mesh* m, const double* wind, const double* g, double* 
   if (!m->body_stream) DGC_CUDA(cudaStreamCreateWithFlags(&m->body_stream, cudaStreamNonBlocking));
   cudaStream_t cs = m->capture_stream, bs = m->body_stream;
   const long n = (long)m->E * m->s.D * m->s.N;
+  // tensor-core precisions: the iteration stays in the tile-blocked layout, fused into the stage kernel
+  const bool tc = is_tc(prec);
+  const int ntiles = (m->E + 127) / 128;
   DGC_CUDA(begin_capture(cs));
   cudaGraph_t graph = nullptr;
   dgc_status rc = DGC_OK;
@@ -523,7 +560,18 @@ dgc_status rich_build(dgc_mesh* m, const double* wind, const double* g, double* 
     if ((err = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, nullptr, nullptr, nullptr)) != cudaSuccess) break;
     if ((err = cudaGraphConditionalHandleCreate(&h, graph, 0, 0)) != cudaSuccess) break;
     if ((rc = prepare_wind(m, prec, wind, cs))) break;
-    if ((rc = rich_step(m, prec, g, v, tau, reduction, max_iter, true, h, iters, res, cs))) break;
+    if (tc) {
+      // tile-blocked state (set 0) and right-hand side; iteration count 0 selects set 0
+      if ((err = cudaMemsetAsync(m->rstate.ptr, 0, 2 * sizeof(double), cs)) != cudaSuccess) break;
+      if ((rc = tc_transpose_in(m, v, m->trA.ptr, cs))) break;
+      if ((err = dgc::launch_tsoa_in64(m->s.D, m->s.K, g, m->tsg.ptr, m->E, cs)) != cudaSuccess) break;
+      if ((rc = launch_rich_tc(m, prec, tau, ds, cs))) break;
+      if ((err = dgc::launch_rich_control(m->partials.ptr, ntiles, m->rstate.ptr, iters, res, reduction, max_iter,
+                                          true, h, m->status.ptr, cs)) != cudaSuccess)
+        break;
+    } else if ((rc = rich_step(m, prec, g, v, tau, reduction, max_iter, true, h, iters, res, cs))) {
+      break;
+    }
     if ((err = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps)) != cudaSuccess) break;
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
@@ -537,13 +585,27 @@ dgc_status rich_build(dgc_mesh* m, const double* wind, const double* g, double* 
     if ((err = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
         cudaSuccess)
       break;
-    cudaError_t e1 = dgc::launch_rich_update(v, m->rho.ptr, ds, n, bs);
-    dgc_status rc1 = e1 == cudaSuccess ? rich_step(m, prec, g, v, tau, reduction, max_iter, false, h, iters, res, bs)
-                                       : DGC_OK;
+    cudaError_t e1 = cudaSuccess;
+    dgc_status rc1 = DGC_OK;
+    if (tc) {
+      // one fused iteration: operator, residual, next iterate (other buffer set), partials
+      rc1 = launch_rich_tc(m, prec, tau, ds, bs);
+      if (rc1 == DGC_OK)
+        e1 = dgc::launch_rich_control(m->partials.ptr, ntiles, m->rstate.ptr, iters, res, reduction, max_iter,
+                                      false, h, m->status.ptr, bs);
+    } else {
+      e1 = dgc::launch_rich_update(v, m->rho.ptr, ds, n, bs);
+      if (e1 == cudaSuccess) rc1 = rich_step(m, prec, g, v, tau, reduction, max_iter, false, h, iters, res, bs);
+    }
     cudaError_t e2 = cudaStreamEndCapture(bs, &body);
     if (rc1) rc = rc1;
     else if (e1 != cudaSuccess) err = e1;
     else if (e2 != cudaSuccess) err = e2;
+    if (rc != DGC_OK || err != cudaSuccess) break;
+    // after the loop: the accepted iterate back to the caller's layout
+    if (tc && (err = dgc::launch_tsoa_out_sel(m->s.D, m->s.K, m->ts0.ptr, m->ts1.ptr, m->rstate.ptr, v, m->E, cs)) !=
+                  cudaSuccess)
+      break;
   } while (false);
   cudaGraph_t done = nullptr;
   cudaError_t e3 = cudaStreamEndCapture(cs, &done);
@@ -805,8 +867,14 @@ dgc_status dgc_richardson(dgc_mesh* mesh, const double* wind_hdiv, const double*
   if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
   DGC_CUDA(mesh->rho.alloc(n));
   DGC_CUDA(mesh->rop.alloc(n));
-  DGC_CUDA(mesh->partials.alloc((size_t)dgc::rich_blocks((long)n)));
+  DGC_CUDA(mesh->partials.alloc(std::max<size_t>((size_t)dgc::rich_blocks((long)n), ((size_t)mesh->E + 127) / 128)));
   DGC_CUDA(mesh->rstate.alloc(2));
+  if (is_tc(prec)) {
+    const size_t nt = dgc::tc_tsoa_len(mesh->s.D, mesh->s.K, mesh->E);
+    DGC_CUDA(mesh->ts1.alloc(nt));
+    DGC_CUDA(mesh->tsg.alloc(nt));
+    DGC_CUDA(mesh->tsf1.alloc(nt));
+  }
   std::vector<uint64_t> key = {(uint64_t)(uintptr_t)wind_hdiv, (uint64_t)(uintptr_t)g_dg, (uint64_t)(uintptr_t)v_dg,
                                (uint64_t)(uintptr_t)iters_dev, (uint64_t)(uintptr_t)res_dev, (uint64_t)max_iter,
                                (uint64_t)prec};

@@ -56,6 +56,10 @@ size_t tc_tr_len(int D, int K, int E);
 cudaError_t launch_tsoa_in(int D, int K, const double* v, double* vt, float* vft, float* tr, const float* blob,
                            int E, cudaStream_t s);
 cudaError_t launch_tsoa_out(int D, int K, const double* vt, double* v, int E, cudaStream_t s);
+// FP64-only ABI -> TSOA, and TSOA -> ABI from the buffer of a pair picked by the parity of ctrl[1]
+cudaError_t launch_tsoa_in64(int D, int K, const double* v, double* vt, int E, cudaStream_t s);
+cudaError_t launch_tsoa_out_sel(int D, int K, const double* vt0, const double* vt1, const double* ctrl, double* v,
+                                int E, cudaStream_t s);
 // wind on the Dubiner basis scaled by 1/det J, float, tile-blocked [tile][D][nk][128]
 // (zero padded in i; entries of elements past E in the last tile are not written)
 cudaError_t launch_wind_coeffs(const DevMesh& m, const double* u_hdiv, float* wc, int nk, cudaStream_t s);

@@ -125,7 +125,47 @@ cudaError_t tsoa_out_t(const double* vt, double* v, int E, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int K>
+cudaError_t tsoa_in64_t(const double* v, double* vt, int E, cudaStream_t s) {
+  const long n = 2L * E * TcLayout2D<K>::N;
+  if (n == 0) return cudaSuccess;
+  tsoa_in64_kernel<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, vt, E);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t tsoa_out_sel_t(const double* vt0, const double* vt1, const double* ctrl, double* v, int E,
+                           cudaStream_t s) {
+  const long n = 2L * E * TcLayout2D<K>::N;
+  if (n == 0) return cudaSuccess;
+  tsoa_out_sel_kernel<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(vt0, vt1, ctrl, v, E);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_tsoa_in64(int D, int K, const double* v, double* vt, int E, cudaStream_t s) {
+  if (D != 2) return cudaErrorInvalidValue;
+  switch (K) {
+    case 1: return tsoa_in64_t<1>(v, vt, E, s);
+    case 2: return tsoa_in64_t<2>(v, vt, E, s);
+    case 3: return tsoa_in64_t<3>(v, vt, E, s);
+    case 4: return tsoa_in64_t<4>(v, vt, E, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_tsoa_out_sel(int D, int K, const double* vt0, const double* vt1, const double* ctrl, double* v,
+                                int E, cudaStream_t s) {
+  if (D != 2) return cudaErrorInvalidValue;
+  switch (K) {
+    case 1: return tsoa_out_sel_t<1>(vt0, vt1, ctrl, v, E, s);
+    case 2: return tsoa_out_sel_t<2>(vt0, vt1, ctrl, v, E, s);
+    case 3: return tsoa_out_sel_t<3>(vt0, vt1, ctrl, v, E, s);
+    case 4: return tsoa_out_sel_t<4>(vt0, vt1, ctrl, v, E, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 size_t tc_tsoa_len(int D, int K, int E) {
   const size_t tiles = ((size_t)E + 127) / 128;

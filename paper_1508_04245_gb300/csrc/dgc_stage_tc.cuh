@@ -50,7 +50,14 @@ __host__ __device__ __forceinline__ size_t tr_index(int e, int c, int f, int m, 
 //   mode 0: writes inc (FP32) and the facet traces of v^n + inc;
 //   mode 1: v <- v + inc in FP64 (the substep's state accumulation), writes
 //           the FP32 copy of the new v and its facet traces;
-//   mode 2: v <- inc in FP64 (the operator itself, for conv_apply).
+//   mode 2: v <- inc in FP64 (the operator itself, for conv_apply);
+//   mode 3: one pseudo-time (Richardson) iteration of Sec. 3.3.2 with the
+//           buffer sets selected by the parity of the iteration count i =
+//           ctrl[1]: from v_i (FP64 v2[i&1], its FP32 copy vf2[i&1] and
+//           traces tr2[i&1]) it forms r = (M^V)^{-1} C^V v_i, the residual
+//           rho = g - v_i - tau r and v_i + ds rho in FP64, writes the latter
+//           (FP64, FP32 copy, traces) into the other set, and per tile the
+//           sum over its elements of |det J| rho^2 into partials[tile].
 struct StageTcArgs {
   const float* vf;      // TSOA FP32 copy of v^n
   const float* din;     // TSOA FP32 increment of the stage input, null = none
@@ -69,6 +76,15 @@ struct StageTcArgs {
   // to 2^-48): a single FP32 rounding of q = c ds would scale every substep's
   // time step by the same (1 + eps), an error that grows linearly in time
   float p_hi, p_lo, q_hi, q_lo;
+  // mode 3
+  const double* ctrl;   // [1] = iteration count (as a double)
+  const float* vf2[2];
+  float* tr2[2];
+  double* v2[2];
+  const double* g;      // TSOA FP64 right-hand side
+  const double* detJ;   // [E]
+  double tau, ds;
+  double* partials;     // [tiles]
 };
 
 namespace tcimpl {
@@ -175,6 +191,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   uint64_t* bar_ep = bars + 4;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  double* red = reinterpret_cast<double*>(bars + 6);   // per-warp sums of mode 3 (8)
 
   // threads 0..255: (element row r of the tile, velocity component c); warps
   // 0-3 and 4-7 read the same TMEM lanes (a warp sees lanes 32 (warp % 4) ..
@@ -186,6 +203,22 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   const int c = (t >> 7) & 1;
   const int issuer_t = 256;
   const int ntiles = (a.E + 127) / 128;
+  // input and output buffers (mode 3 picks its pair by the parity of the iteration count)
+  const float* vf_in = a.vf;
+  const float* tr_in = a.trin;
+  double* v_state = a.v;
+  double* v_out = a.v;
+  float* vf_out = a.vf_out;
+  float* tr_out = a.trout;
+  if (a.mode == 3) {
+    const int par = ((int)a.ctrl[1]) & 1;
+    vf_in = a.vf2[par];
+    tr_in = a.tr2[par];
+    v_state = a.v2[par];
+    v_out = a.v2[par ^ 1];
+    vf_out = const_cast<float*>(a.vf2[par ^ 1]);
+    tr_out = a.tr2[par ^ 1];
+  }
   // the epilogue reads the stage-input increment (modes 0, 1) and v^n (mode 0)
   const bool epi_din = a.din != nullptr;
   const bool epi_vf = a.mode == 0;
@@ -194,7 +227,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   // the next tile's contiguous TR block into L2 ahead of use
   auto prefetch_tile = [&](int tile) {
     const uint32_t ntr = 128u * 2 * NF * NFM;  // values per tile in TR
-    tc::bulk_prefetch_l2(a.trin + (size_t)tile * ntr, ntr * 4);
+    tc::bulk_prefetch_l2(tr_in + (size_t)tile * ntr, ntr * 4);
   };
   auto load_wind = [&](int tile) {        // a tile's wind coefficients into the staging buffer
     const uint32_t bytes = (uint32_t)L::WSTAGE * 4;   // whole tile block ([c][k][128])
@@ -207,7 +240,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   const uint32_t blk = (uint32_t)L::TSOA_TILE * 4;
   auto load_state = [&](float* dst, uint64_t* bar, int tile, bool vf, bool din) {
     tc::mbar_arrive_expect_tx(bar, (vf ? blk : 0u) + (din ? blk : 0u));
-    if (vf) tc::bulk_g2s(dst, a.vf + (size_t)tile * L::TSOA_TILE, blk, bar);
+    if (vf) tc::bulk_g2s(dst, vf_in + (size_t)tile * L::TSOA_TILE, blk, bar);
     if (din) tc::bulk_g2s(dst + L::TSOA_TILE, a.din + (size_t)tile * L::TSOA_TILE, blk, bar);
   };
 
@@ -317,8 +350,8 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
       const int ne = code >> 2, fn = code & 3;
 #pragma unroll
       for (int m = 0; m < NFM; ++m) {
-        to[f][m] = (producer && valid) ? a.trin[tr_index(e, c, f, m, NFM)] : 0.f;
-        tn[f][m] = code >= 0 ? a.trin[tr_index(ne, c, fn, m, NFM)] : 0.f;
+        to[f][m] = (producer && valid) ? tr_in[tr_index(e, c, f, m, NFM)] : 0.f;
+        tn[f][m] = code >= 0 ? tr_in[tr_index(ne, c, fn, m, NFM)] : 0.f;
       }
     }
     if (producer && run && *abort_flag == 0 && !tc::mbar_wait(bar_A, it & 1)) *abort_flag = 1;
@@ -330,7 +363,9 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     if (t == issuer_t && run2) {
       tc::fence_proxy_async_smem();
       // the FP64 state the epilogue accumulates into (mode 1), toward L2
-      if (a.mode == 1) tc::bulk_prefetch_l2(a.v + (size_t)tile * L::TSOA_TILE, (uint32_t)L::TSOA_TILE * 8);
+      if (a.mode == 1 || a.mode == 3)
+        tc::bulk_prefetch_l2(v_state + (size_t)tile * L::TSOA_TILE, (uint32_t)L::TSOA_TILE * 8);
+      if (a.mode == 3) tc::bulk_prefetch_l2(a.g + (size_t)tile * L::TSOA_TILE, (uint32_t)L::TSOA_TILE * 8);
       if (epi_vf || epi_din) {
         load_state(epi, bar_ep, tile, epi_vf, epi_din);
         ++ep_issued;
@@ -439,7 +474,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     double ex[N];
 #pragma unroll
     for (int i = 0; i < N; ++i)
-      ex[i] = (producer && valid && a.mode == 1) ? a.v[tsoa_index(e, c, i, N)] : 0.0;
+      ex[i] = (producer && valid && a.mode == 1) ? v_state[tsoa_index(e, c, i, N)] : 0.0;
     if (producer && run2 && (epi_vf || epi_din) && *abort_flag == 0 && !tc::mbar_wait(bar_ep, it & 1))
       *abort_flag = 1;
     tc::fence_before_sync();
@@ -450,6 +485,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
       if (t == 0) atomicOr(a.status, 2);   // a bounded wait gave up: this CTA stops
       break;
     }
+    double racc = 0.0;   // mode 3: sum of rho^2 over this thread's coefficients
     if (producer && valid) {
       // inc = p din + q L, L = -r (r carries FP32 accuracy)
       float xo[NP4];
@@ -466,11 +502,20 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
           xo[i] = epi[si] + inc;
         } else if (a.mode == 1) {
           const double x = ex[i] + tc::f32_to_f64(inc);   // FP64 state accumulation
-          a.v[ix] = x;
+          v_out[ix] = x;
           xo[i] = tc::f64_to_f32_rn(x);
-          a.vf_out[ix] = xo[i];
+          vf_out[ix] = xo[i];
+        } else if (a.mode == 3) {
+          // rho = g - v - tau r and the next iterate, in FP64
+          const double vx = v_state[ix];
+          const double rho = (a.g[ix] - vx) - a.tau * tc::f32_to_f64(rr[i]);
+          const double vn = vx + a.ds * rho;
+          v_out[ix] = vn;
+          xo[i] = tc::f64_to_f32_rn(vn);
+          vf_out[ix] = xo[i];
+          racc += rho * rho;
         } else {
-          a.v[ix] = tc::f32_to_f64(inc);
+          v_out[ix] = tc::f32_to_f64(inc);
         }
       }
       if (a.mode != 2) {
@@ -479,12 +524,24 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
 #pragma unroll
         for (int f = 0; f < NF; ++f)
 #pragma unroll
-          for (int m = 0; m < NFM; ++m) a.trout[tr_index(e, c, f, m, NFM)] = tr[f][m];
+          for (int m = 0; m < NFM; ++m) tr_out[tr_index(e, c, f, m, NFM)] = tr[f][m];
       }
+      if (a.mode == 3) racc *= fabs(a.detJ[e]);
+    }
+    if (a.mode == 3 && producer) {   // per-warp sum in a fixed order
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) racc += __shfl_xor_sync(0xffffffffu, racc, o);
+      if ((t & 31) == 0) red[warp] = racc;
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    if (a.mode == 3 && t == 0) {
+      double sum = 0.0;
+#pragma unroll
+      for (int w8 = 0; w8 < 8; ++w8) sum += red[w8];
+      a.partials[tile] = sum;
+    }
   }
   // bulk copies still in flight (only after a timeout) land before the CTA exits
   if (t == issuer_t) {
@@ -523,6 +580,35 @@ __global__ void __launch_bounds__(256) tsoa_in_kernel(const double* __restrict__
   for (int f = 0; f < NF; ++f)
 #pragma unroll
     for (int m = 0; m < NFM; ++m) tr[tr_index(e, c, f, m, NFM)] = t[f][m];
+}
+
+// ABI layout [E][2][N] -> TSOA, FP64 only
+template <int K>
+__global__ void __launch_bounds__(256) tsoa_in64_kernel(const double* __restrict__ v, double* __restrict__ vt,
+                                                        int E) {
+  constexpr int N = TcLayout2D<K>::N;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long)E * 2 * N) return;
+  const int i = (int)(gid % N);
+  const int c = (int)((gid / N) % 2);
+  const int e = (int)(gid / (2 * N));
+  vt[tsoa_index(e, c, i, N)] = v[gid];
+}
+
+// TSOA -> ABI layout from the buffer of a pair selected by the parity of ctrl[1]
+template <int K>
+__global__ void __launch_bounds__(256) tsoa_out_sel_kernel(const double* __restrict__ vt0,
+                                                           const double* __restrict__ vt1,
+                                                           const double* __restrict__ ctrl, double* __restrict__ v,
+                                                           int E) {
+  constexpr int N = TcLayout2D<K>::N;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long)E * 2 * N) return;
+  const int i = (int)(gid % N);
+  const int c = (int)((gid / N) % 2);
+  const int e = (int)(gid / (2 * N));
+  const double* vt = (((int)ctrl[1]) & 1) ? vt1 : vt0;
+  v[gid] = vt[tsoa_index(e, c, i, N)];
 }
 
 // TSOA -> ABI layout
