@@ -91,8 +91,14 @@ std::vector<float> blob_t(const Tables& t) {
 template <int K, int P>
 cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
   using L = TcLayout2D<K, P>;
-  auto kern = stage_tc_kernel<K, P>;
-  if (!a) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_BYTES);
+  if (!a) {
+    cudaError_t e0 = cudaFuncSetAttribute(stage_tc_kernel<K, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          L::SMEM_BYTES);
+    if (e0 != cudaSuccess) return e0;
+    return cudaFuncSetAttribute(stage_tc_kernel<K, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                L::SMEM_BYTES);
+  }
+  auto kern = a->mode == 3 ? stage_tc_kernel<K, P, true> : stage_tc_kernel<K, P, false>;
   const int tiles = (a->E + 127) / 128;
   if (tiles == 0) return cudaSuccess;
   // persistent: two resident CTAs per SM (shared memory and TMEM allow two)

@@ -172,7 +172,8 @@ __device__ __forceinline__ void facet_traces(const float* Ef, const float* x, fl
     }
 }
 
-template <int K, int P>
+// RICH: the variant for mode 3 (pseudo-time iteration); modes 0-2 compile without it
+template <int K, int P, bool RICH>
 __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   using L = TcLayout2D<K, P>;
   constexpr int N = L::N, QV = L::QV, QF = L::QF, NFM = L::NFM, NF = L::NF, NK = L::NK;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   double* v_out = a.v;
   float* vf_out = a.vf_out;
   float* tr_out = a.trout;
-  if (a.mode == 3) {
+  if constexpr (RICH) {
     const int par = ((int)a.ctrl[1]) & 1;
     vf_in = a.vf2[par];
     tr_in = a.tr2[par];
@@ -363,9 +364,9 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     if (t == issuer_t && run2) {
       tc::fence_proxy_async_smem();
       // the FP64 state the epilogue accumulates into (mode 1), toward L2
-      if (a.mode == 1 || a.mode == 3)
+      if (RICH || a.mode == 1)
         tc::bulk_prefetch_l2(v_state + (size_t)tile * L::TSOA_TILE, (uint32_t)L::TSOA_TILE * 8);
-      if (a.mode == 3) tc::bulk_prefetch_l2(a.g + (size_t)tile * L::TSOA_TILE, (uint32_t)L::TSOA_TILE * 8);
+      if constexpr (RICH) tc::bulk_prefetch_l2(a.g + (size_t)tile * L::TSOA_TILE, (uint32_t)L::TSOA_TILE * 8);
       if (epi_vf || epi_din) {
         load_state(epi, bar_ep, tile, epi_vf, epi_din);
         ++ep_issued;
@@ -497,15 +498,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
         const int si = (c * N + i) * 128 + r;
         const float ed = epi_din ? epi[L::TSOA_TILE + si] : 0.f;
         const float inc = fmaf(a.p_hi, ed, fmaf(a.p_lo, ed, -fmaf(a.q_hi, rr[i], a.q_lo * rr[i])));
-        if (a.mode == 0) {
-          a.dout[ix] = inc;
-          xo[i] = epi[si] + inc;
-        } else if (a.mode == 1) {
-          const double x = ex[i] + tc::f32_to_f64(inc);   // FP64 state accumulation
-          v_out[ix] = x;
-          xo[i] = tc::f64_to_f32_rn(x);
-          vf_out[ix] = xo[i];
-        } else if (a.mode == 3) {
+        if (RICH) {
           // rho = g - v - tau r and the next iterate, in FP64
           const double vx = v_state[ix];
           const double rho = (a.g[ix] - vx) - a.tau * tc::f32_to_f64(rr[i]);
@@ -514,6 +507,14 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
           xo[i] = tc::f64_to_f32_rn(vn);
           vf_out[ix] = xo[i];
           racc += rho * rho;
+        } else if (a.mode == 0) {
+          a.dout[ix] = inc;
+          xo[i] = epi[si] + inc;
+        } else if (a.mode == 1) {
+          const double x = ex[i] + tc::f32_to_f64(inc);   // FP64 state accumulation
+          v_out[ix] = x;
+          xo[i] = tc::f64_to_f32_rn(x);
+          vf_out[ix] = xo[i];
         } else {
           v_out[ix] = tc::f32_to_f64(inc);
         }
@@ -526,9 +527,9 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
 #pragma unroll
           for (int m = 0; m < NFM; ++m) tr_out[tr_index(e, c, f, m, NFM)] = tr[f][m];
       }
-      if (a.mode == 3) racc *= fabs(a.detJ[e]);
+      if constexpr (RICH) racc *= fabs(a.detJ[e]);
     }
-    if (a.mode == 3 && producer) {   // per-warp sum in a fixed order
+    if (RICH && producer) {   // per-warp sum in a fixed order
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) racc += __shfl_xor_sync(0xffffffffu, racc, o);
       if ((t & 31) == 0) red[warp] = racc;
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (a.mode == 3 && t == 0) {
+    if (RICH && t == 0) {
       double sum = 0.0;
 #pragma unroll
       for (int w8 = 0; w8 < 8; ++w8) sum += red[w8];
