@@ -195,6 +195,52 @@ def fourier_field(seed: int, dim: int, n_modes: int = 8) -> FourierField:
     return FourierField(b, kappa, phi)
 
 
+def parallelogram_mesh(n: int, seed: int | None = None, stretch: float = 0.4, skew: float = 0.4,
+                       reorient: bool = True):
+    """``n x n`` parallelograms (uncurved quadrilaterals).
+
+    A tensor grid with random column widths and row heights (each
+    ``1 + U[-stretch, stretch]``, normalised to a unit total), every row of
+    vertices shifted sideways by a random walk of steps ``U[-skew, skew]``
+    times the row height: cell (i, j) is a parallelogram whose size, aspect
+    ratio and shear change from cell to cell.  With ``reorient`` the vertex
+    numbering is a random permutation and every cell starts its cyclic vertex
+    order at a random corner, in reversed (clockwise) order for about half of
+    them, so every local facet orientation and both signs of det J occur.
+
+    Returns ``(verts [ (n+1)^2, 2 ] float64, elems [ n^2, 4 ] int32)``, the
+    vertices of each element in cyclic order; cells are row-major.
+    """
+    rng = np.random.default_rng(seed)
+    wx = 1.0 + rng.uniform(-stretch, stretch, n)
+    wy = 1.0 + rng.uniform(-stretch, stretch, n)
+    x = np.concatenate([[0.0], np.cumsum(wx / wx.sum())])
+    y = np.concatenate([[0.0], np.cumsum(wy / wy.sum())])
+    shift = np.concatenate([[0.0], np.cumsum(rng.uniform(-skew, skew, n) * np.diff(y))])
+    verts = np.array([(x[i] + shift[j], y[j]) for j in range(n + 1) for i in range(n + 1)], dtype=np.float64)
+    vid = lambda i, j: i + (n + 1) * j                     # noqa: E731
+    elems = np.array([(vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1))
+                      for j in range(n) for i in range(n)], dtype=np.int64)
+    if reorient:
+        perm = rng.permutation(verts.shape[0])            # new id of old vertex v: perm[v]
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        verts = verts[inv]
+        elems = perm[elems]
+        start = rng.integers(0, 4, size=elems.shape[0])
+        rev = rng.random(elems.shape[0]) < 0.5
+        for e in range(elems.shape[0]):
+            cyc = np.roll(elems[e], -start[e])
+            elems[e] = cyc[[0, 3, 2, 1]] if rev[e] else cyc
+    return verts, elems.astype(np.int32)
+
+
+def tensor_coeffs(seed: int, n_elem: int, k: int) -> np.ndarray:
+    """DG coefficients on parallelograms i.i.d. U[-1, 1], layout [E][2][(k+1)^2]."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=(n_elem, 2, (k + 1) ** 2))
+
+
 # --------------------------------------------------------------------------
 # coefficient vectors
 # --------------------------------------------------------------------------
