@@ -49,6 +49,25 @@
  *   convection (Sec. 2.4) and are not represented.
  * - Orders supported: dim 2, k = 1..6; dim 3, k = 1..5 (DGC_ERR_UNSUPPORTED
  *   otherwise).
+ * - Parallelograms (handles from dgc_mesh_upload_quad, the uncurved
+ *   quadrilaterals of Sec. 2 "Preliminaries"): V_h = [Q^k]^2 on the basis
+ *   psi_{ab} = l_a(xi) l_b(eta), i = a (k+1) + b, l_a the orthonormal shifted
+ *   Legendre polynomial on [0,1] (N = (k+1)^2, M^V_T = |det J_T| Id); W_h the
+ *   H(div)-conforming subspace of the Piola images of [Q^k]^2, so W_h lies in
+ *   V_h and I is an embedding (Sec. 2.4).  H(div) layout: [n_facets][k+1]
+ *   facet moments int_F u.n_F l_m(s) dS, s running from the facet's lower to
+ *   its higher global vertex id, then [E][2(k+1)(k-1)] interior moments of the
+ *   reference field against (l_a l_b, 0), a <= k-2, b <= k, then
+ *   (0, l_a l_b), a <= k, b <= k-2.  dgc_geometry, dgc_transfer,
+ *   dgc_transfer_T(_noalloc), dgc_mass_apply, dgc_conv_apply, dgc_rk_substeps,
+ *   dgc_batch_rk_substeps, dgc_richardson, dgc_oifs_rhs, dgc_conv_apply_hdiv,
+ *   dgc_wind_extrapolate, dgc_wind_from_potential, dgc_hdiv_interpolate,
+ *   dgc_project, dgc_point_coords, dgc_max_wind_speed, dgc_min_edge,
+ *   dgc_state_save / _load and dgc_check accept them with DGC_FP64 and
+ *   DGC_FP32 (the stage kernel contracts one direction at a time); the
+ *   tensor-core precisions return DGC_ERR_UNSUPPORTED.  dgc_wind_from_potential
+ *   takes the stream function at the (k+1)^2 nodes (a/k, b/k), index
+ *   a (k+1) + b, of every element (dgc_point_coords kind 0).
  */
 #ifndef DGCONV_H
 #define DGCONV_H
@@ -95,6 +114,21 @@ typedef enum { DGC_SSPRK2 = 2, DGC_SSPRK3 = 3 } dgc_scheme;
  * Sec. 2 "Preliminaries" (affine simplicial partition, facets). */
 dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int n_elem,
                            const int32_t* elems, void* stream, dgc_mesh** out);
+
+/* Build a handle for a conforming mesh of parallelograms of order k = 1..6.
+ * verts: host [n_vert][2]; elems: host [n_elem][4] vertex ids in cyclic order
+ * (either sense of rotation, any starting corner; the order is kept:
+ * x = X_0 + J xi with J[:, 0] = X_1 - X_0, J[:, 1] = X_3 - X_0 on [0,1]^2).
+ * Every element must satisfy |X_0 + X_2 - X_1 - X_3| <= 1e-12 times its size
+ * (a parallelogram: an uncurved quadrilateral, Sec. 2 "Preliminaries") and be
+ * non-degenerate; n_elem < 2^28.  Local facets: eta = 0 (X_0 -> X_1),
+ * xi = 1 (X_1 -> X_2), eta = 1 (X_3 -> X_2), xi = 0 (X_0 -> X_3).  Facets are
+ * numbered by their sorted vertex pairs in lexicographic order, each owned by
+ * its lower-index element.  Synchronizes `stream` once at the end.  Errors:
+ * DGC_ERR_ARG (bad arrays, non-conforming, not a parallelogram, degenerate),
+ * DGC_ERR_UNSUPPORTED (k), DGC_ERR_ALLOC, DGC_ERR_CUDA. */
+dgc_status dgc_mesh_upload_quad(int k, int n_vert, const double* verts, int n_elem,
+                                const int32_t* elems, void* stream, dgc_mesh** out);
 
 /* Release the handle and everything the library allocated for it. */
 dgc_status dgc_mesh_free(dgc_mesh* mesh);
@@ -314,6 +348,26 @@ dgc_status dgc_transfer_T_noalloc(dgc_mesh* mesh, const double* f_dg, double* g_
  * the BDM_k basis on the vector Dubiner basis.  Writes *count = entries; out
  * may be NULL to query the size. */
 dgc_status dgc_table(int dim, int k, const char* name, double* out, int64_t* count);
+
+/* Reference table `name` of the order-k parallelogram element (the square
+ * [0,1]^2), host double array: "Bv" [QV][N] basis at the volume points
+ * (q = p m + q', m = floor(3k/2) + 1 Gauss points per direction), "Gv"
+ * [QV][N][2] reference gradients, "wv" [QV], "xv" [QV][2], "wf" [m], "sf" [m]
+ * the 1D rule, "Bf" [4][m][N] the basis at the facet points, "Cb" [2N][2N] the
+ * W_h basis on the vector tensor basis (column j: local basis function j),
+ * "q1L" / "q1D" [m][k+1] l_a and l_a' at the Gauss points, "q1E" [2][k+1]
+ * l_a(0) and l_a(1).  Writes *count = entries; out may be NULL to query the
+ * size. */
+dgc_status dgc_quad_table(int k, const char* name, double* out, int64_t* count);
+
+/* Host connectivity exactly as dgc_mesh_upload_quad builds it: facet_id,
+ * nbr ((e' << 3) | (rev << 2) | f', rev = 1 when the neighbour's local facet
+ * parameter runs the other way; -1 on the boundary), orient (+1 owner /
+ * boundary, -1 otherwise) and flip (1 when the local facet parameter runs
+ * from the higher to the lower global vertex id), each [n_elem][4]; any output
+ * may be NULL. */
+dgc_status dgc_quad_connectivity(int n_vert, int n_elem, const int32_t* elems, int32_t* facet_id, int32_t* nbr,
+                                 int8_t* orient, int8_t* flip, int32_t* n_facets);
 
 /* Host connectivity exactly as dgc_mesh_upload builds it: facet_id
  * [n_elem][dim+1], nbr [n_elem][dim+1] ((neighbour << 2) | neighbour's local

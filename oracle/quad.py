@@ -157,8 +157,7 @@ class QuadMesh:
                 self.nbr[e1, f1], self.nbr_facet[e1, f1] = e0, f0
                 self.orient[e1, f1] = -1
         # local parameter runs against the global one (higher -> lower vertex id)
-        self.flip = np.array([[int(self.elems[e, a] > self.elems[e, b]) for (a, b) in F_LOC]
-                              for e in range(E)], dtype=np.int64).reshape(E, 4)
+        self.flip = np.stack([(self.elems[:, a] > self.elems[:, b]).astype(np.int64) for (a, b) in F_LOC], axis=1)
         # outward unit normals and lengths
         self.normal = np.empty((E, 4, 2))
         self.length = np.empty((E, 4))
@@ -291,14 +290,18 @@ def dofs_of_field(mesh, k, field_e) -> np.ndarray:
     m = k + 2
     s, ws = gauss01(m)
     out = np.zeros(n_hdiv)
-    for g in range(mesh.n_facets):
-        e, f = mesh.facet_owner[g]
-        xi = facet_point(f, s)
-        u = field_e(np.array([e]), xi)[0]                          # [Q, 2]
-        un = u @ mesh.normal[e, f]
-        sg = 1.0 - s if mesh.flip[e, f] else s
-        lm = np.stack([leg(mm, sg) for mm in range(n_fm)], axis=1)
-        out[g * n_fm:(g + 1) * n_fm] = mesh.length[e, f] * (ws * un) @ lm
+    e_own, f_own = mesh.facet_owner[:, 0], mesh.facet_owner[:, 1]
+    for f in range(4):                                             # facets grouped by the owner's local facet
+        gs = np.nonzero(f_own == f)[0]
+        if gs.size == 0:
+            continue
+        eo = e_own[gs]
+        u = field_e(eo, facet_point(f, s))                         # [g, Q, 2]
+        un = np.einsum("gqd,gd->gq", u, mesh.normal[eo, f])
+        sg = np.where(mesh.flip[eo, f][:, None] == 1, 1.0 - s[None, :], s[None, :])   # global parameter
+        lm = np.stack([leg(mm, sg) for mm in range(n_fm)], axis=2)                   # [g, Q, n_fm]
+        mom = mesh.length[eo, f][:, None] * np.einsum("q,gq,gqm->gm", ws, un, lm)
+        out[(gs[:, None] * n_fm + np.arange(n_fm)[None, :]).ravel()] = mom.ravel()
     if n_int:
         xq, wq = square_rule(m)
         T = interior_tests(k, xq)

@@ -117,6 +117,9 @@ cudaStream_t g_batch_streams[kBatchBranches + 1] = {nullptr};
 struct dgc_mesh {
   Sizes s;
   int E = 0, nF = 0, nV = 0;
+  int quad = 0;                    // 1: parallelograms (dgc_mesh_upload_quad)
+  DevBuf<signed char> flip;        // [E][4] facet-parameter flips of a parallelogram mesh
+  DevBuf<int> qnbr;                // [E][4] neighbour codes of the parallelogram stage kernel
   std::vector<double> h_verts;     // [nV][D]
   std::vector<int> h_elems;        // [E][NF] sorted
   double h_min = 0.0;
@@ -176,6 +179,8 @@ struct dgc_mesh {
     m.wfd = wfd.ptr;
     m.Qfd = Qfd.ptr;
     m.Bd = Bd.ptr;
+    m.quad = quad;
+    m.flip = flip.ptr;
     return m;
   }
 
@@ -197,6 +202,8 @@ struct dgc_mesh {
       b->release();
     for (auto* b : {&elems, &nbr, &facet_id, &facet_sides}) b->release();
     orient.release();
+    flip.release();
+    qnbr.release();
     tab32.release();
     tcblob.release();
     tcblob16.release();
@@ -239,6 +246,15 @@ std::vector<T> stage_blob(const dgc::Tables& t) {
   return out;
 }
 
+// the 1D tables of the parallelogram stage kernel: l at the Gauss points | l' there | l(0), l(1)
+template <typename T>
+std::vector<T> quad_stage_blob(const dgc::Tables& t) {
+  std::vector<T> out;
+  for (const std::vector<double>* v : {&t.q1L, &t.q1D, &t.q1E})
+    for (double x : *v) out.push_back((T)x);
+  return out;
+}
+
 dgc_status check_mesh(const dgc_mesh* m) {
   if (!m) return fail(DGC_ERR_ARG, "mesh handle is NULL");
   return DGC_OK;
@@ -247,8 +263,9 @@ dgc_status check_mesh(const dgc_mesh* m) {
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 dgc_status ensure_wind_scratch(dgc_mesh* m, bool fp32) {
-  cudaError_t perr = m->s.D == 2 ? dgc::launch_stage_2d(m->s.K, fp32, nullptr, nullptr)
-                                 : dgc::launch_stage_3d(m->s.K, fp32, nullptr, nullptr);
+  cudaError_t perr = m->quad       ? dgc::launch_stage_quad(m->s.K, fp32, nullptr, nullptr)
+                     : m->s.D == 2 ? dgc::launch_stage_2d(m->s.K, fp32, nullptr, nullptr)
+                                   : dgc::launch_stage_3d(m->s.K, fp32, nullptr, nullptr);
   if (perr != cudaSuccess) return fail(DGC_ERR_CUDA, "stage kernel setup failed: %s", cudaGetErrorString(perr));
   const size_t nu = (size_t)m->s.QV * m->s.D * m->E, nf = (size_t)m->s.NF * m->s.QF * m->E;
   if (fp32) {
@@ -270,13 +287,15 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
   a.vout = vout;
   a.Uw = fp32 ? (const void*)m->Uw32.ptr : (const void*)m->Uw64.ptr;
   a.Fw = fp32 ? (const void*)m->Fw32.ptr : (const void*)m->Fw64.ptr;
-  a.nbr = m->nbr.ptr;
+  a.nbr = m->quad ? m->qnbr.ptr : m->nbr.ptr;
   a.tab = fp32 ? (const void*)m->tab32.ptr : (const void*)m->tab64.ptr;
   a.E = m->E;
   a.alpha = alpha;
   a.beta = beta;
   a.gamma = gamma;
-  cudaError_t err = m->s.D == 2 ? dgc::launch_stage_2d(m->s.K, fp32, &a, st) : dgc::launch_stage_3d(m->s.K, fp32, &a, st);
+  cudaError_t err = m->quad       ? dgc::launch_stage_quad(m->s.K, fp32, &a, st)
+                    : m->s.D == 2 ? dgc::launch_stage_2d(m->s.K, fp32, &a, st)
+                                  : dgc::launch_stage_3d(m->s.K, fp32, &a, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "stage kernel launch failed: %s", cudaGetErrorString(err));
   return DGC_OK;
 }
@@ -284,12 +303,15 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
 // the tensor-core precisions (split operands on tcgen05)
 bool is_tc(dgc_prec prec) { return prec == DGC_TF32X3 || prec == DGC_BF16X3; }
 
+// the tensor-core stage kernel covers triangles with k <= 4
+bool mesh_tc(const dgc_mesh* m) { return !m->quad && dgc::tc_supported(m->s.D, m->s.K); }
+
 dgc_status check_prec(const dgc_mesh* m, dgc_prec prec) {
   if (prec == DGC_FP64 || prec == DGC_FP32) return DGC_OK;
   if (is_tc(prec)) {
-    if (dgc::tc_supported(m->s.D, m->s.K)) return DGC_OK;
-    return fail(DGC_ERR_UNSUPPORTED, "%s is available for triangles with k <= 4 (dim %d, k %d)",
-                prec == DGC_TF32X3 ? "DGC_TF32X3" : "DGC_BF16X3", m->s.D, m->s.K);
+    if (mesh_tc(m)) return DGC_OK;
+    return fail(DGC_ERR_UNSUPPORTED, "%s is available for triangles with k <= 4 (dim %d, k %d%s)",
+                prec == DGC_TF32X3 ? "DGC_TF32X3" : "DGC_BF16X3", m->s.D, m->s.K, m->quad ? ", parallelograms" : "");
   }
   return fail(DGC_ERR_ARG, "unknown precision %d", (int)prec);
 }
@@ -739,6 +761,96 @@ dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int 
   return DGC_OK;
 }
 
+dgc_status dgc_mesh_upload_quad(int k, int n_vert, const double* verts, int n_elem, const int32_t* elems,
+                                void* stream, dgc_mesh** out) {
+  DGC_RANGE();
+  if (!out) return fail(DGC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!dgc::quad_supported(k)) return fail(DGC_ERR_UNSUPPORTED, "order k=%d not supported for parallelograms", k);
+  if (n_vert <= 0 || n_elem <= 0 || !verts || !elems)
+    return fail(DGC_ERR_ARG, "empty mesh or NULL arrays (n_vert=%d, n_elem=%d)", n_vert, n_elem);
+  if (n_elem >= (1 << 28)) return fail(DGC_ERR_ARG, "at most 2^28 - 1 parallelograms (got %d)", n_elem);
+  dgc_mesh* m = new dgc_mesh();
+  m->quad = 1;
+  m->s = dgc::make_quad_sizes(k);
+  m->E = n_elem;
+  m->nV = n_vert;
+  m->h_verts.assign(verts, verts + (size_t)n_vert * 2);
+  m->h_elems.assign(elems, elems + (size_t)n_elem * 4);
+  dgc::Connectivity con;
+  std::vector<signed char> flip;
+  std::vector<int> qnbr;
+  std::string why = dgc::build_quad_connectivity(n_vert, n_elem, m->h_elems, con, flip, qnbr);
+  if (!why.empty()) {
+    delete m;
+    return fail(DGC_ERR_ARG, "%s", why.c_str());
+  }
+  m->nF = con.n_facets;
+  // ---- validate: parallelogram (X_0 + X_2 = X_1 + X_3), non-degenerate; shortest edge
+  double hmin = INFINITY;
+  for (int e = 0; e < n_elem; ++e) {
+    const int* v = &m->h_elems[(size_t)e * 4];
+    const double* X[4];
+    for (int a = 0; a < 4; ++a) X[a] = verts + (size_t)v[a] * 2;
+    double scale = 0.0, gap = 0.0;
+    for (int r = 0; r < 2; ++r) {
+      scale = std::max(scale, std::fabs(X[1][r] - X[0][r]) + std::fabs(X[3][r] - X[0][r]));
+      const double d = X[0][r] + X[2][r] - X[1][r] - X[3][r];
+      gap += d * d;
+    }
+    if (!(std::sqrt(gap) <= 1e-12 * scale)) {
+      delete m;
+      return fail(DGC_ERR_ARG, "element %d is not a parallelogram (|X0 + X2 - X1 - X3| = %g)", e, std::sqrt(gap));
+    }
+    const double det = (X[1][0] - X[0][0]) * (X[3][1] - X[0][1]) - (X[3][0] - X[0][0]) * (X[1][1] - X[0][1]);
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) {
+      delete m;
+      return fail(DGC_ERR_ARG, "element %d is degenerate (det J = %g)", e, det);
+    }
+    for (int f = 0; f < 4; ++f) {
+      const double* A = X[dgc::kQuadFacet[f][0]];
+      const double* B = X[dgc::kQuadFacet[f][1]];
+      hmin = std::min(hmin, std::hypot(B[0] - A[0], B[1] - A[1]));
+    }
+  }
+  m->h_min = hmin;
+  cudaStream_t st = as_stream(stream);
+  const dgc::Tables* tp;
+  try {
+    tp = &dgc::quad_tables(k);
+  } catch (const std::exception& ex) {
+    delete m;
+    return fail(DGC_ERR_ARG, "reference table build failed: %s", ex.what());
+  }
+  const dgc::Tables& t = *tp;
+  auto up = [&](cudaError_t err) -> bool { return err == cudaSuccess; };
+  bool ok = up(m->verts.upload(m->h_verts)) && up(m->elems.upload(m->h_elems)) && up(m->nbr.upload(con.nbr)) &&
+            up(m->facet_id.upload(con.facet_id)) && up(m->orient.upload(con.orient)) &&
+            up(m->facet_sides.upload(con.sides)) && up(m->flip.upload(flip)) && up(m->qnbr.upload(qnbr)) &&
+            up(m->J.alloc((size_t)n_elem * 4)) && up(m->detJ.alloc(n_elem)) && up(m->Bv.upload(t.Bv)) &&
+            up(m->wv.upload(t.wv)) && up(m->wf.upload(t.wf)) && up(m->Bf.upload(t.Bf)) && up(m->Cb.upload(t.Cb)) &&
+            up(m->Lg_int.upload(t.Lg_int)) && up(m->Lg_fac.upload(t.Lg_fac)) && up(m->Tint.upload(t.Tint)) &&
+            up(m->wd.upload(t.wd)) && up(m->wfd.upload(t.wfd)) && up(m->Qfd.upload(t.Qfd)) &&
+            up(m->Bd.upload(t.Bd)) && up(m->tab64.upload(quad_stage_blob<double>(t))) &&
+            up(m->tab32.upload(quad_stage_blob<float>(t))) && up(m->status.alloc(1)) &&
+            up(cudaMemset(m->status.ptr, 0, sizeof(int)));
+  if (!ok) {
+    cudaError_t err = cudaGetLastError();
+    m->release_all();
+    delete m;
+    return fail(DGC_ERR_ALLOC, "device upload failed: %s", cudaGetErrorString(err));
+  }
+  cudaError_t err = dgc::launch_geometry(m->view(), st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) {
+    m->release_all();
+    delete m;
+    return fail(DGC_ERR_CUDA, "geometry kernel failed: %s", cudaGetErrorString(err));
+  }
+  *out = m;
+  return DGC_OK;
+}
+
 dgc_status dgc_mesh_free(dgc_mesh* mesh) {
   if (!mesh) return DGC_OK;
   drop_batch_graphs(mesh);
@@ -904,6 +1016,7 @@ dgc_status dgc_autotune(dgc_mesh* mesh, const double* wind_hdiv, dgc_prec prec, 
   if (reps < 1 || reps > 1000) return fail(DGC_ERR_ARG, "reps must lie in 1..1000 (got %d)", reps);
   if (block_out) *block_out = 0;
   if (is_tc(prec)) return DGC_OK;   // the tensor-core kernel has one tile shape (128 x 288)
+  if (mesh->quad) return DGC_OK;    // the parallelogram kernel has one block shape (128)
   const bool fp32 = prec == DGC_FP32;
   const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
   if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
@@ -1084,7 +1197,7 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
     for (int j = 0; j < i; ++j)
       if (meshes[j] == m) return fail(DGC_ERR_ARG, "instances %d and %d share a mesh handle (scratch)", j, i);
     // the tensor-core path covers triangles k <= 4; other orders run their stages in FP32
-    pr[i] = (is_tc(prec) && !dgc::tc_supported(m->s.D, m->s.K)) ? DGC_FP32 : prec;
+    pr[i] = (is_tc(prec) && !mesh_tc(m)) ? DGC_FP32 : prec;
     if (dgc_status rc = ensure_prec_scratch(m, pr[i])) return rc;
     const size_t n = (size_t)m->E * m->s.D * m->s.N;
     DGC_CUDA(m->stage1.alloc(n));
@@ -1155,8 +1268,8 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
 dgc_status dgc_point_coords(const dgc_mesh* mesh, int kind, double* xyz, int64_t* count) {
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (kind < 0 || kind > 2) return fail(DGC_ERR_ARG, "kind must be 0, 1 or 2");
-  const dgc::Tables& t = dgc::tables(mesh->s.D, mesh->s.K);
-  const int D = mesh->s.D, NF = D + 1;
+  const dgc::Tables& t = mesh->quad ? dgc::quad_tables(mesh->s.K) : dgc::tables(mesh->s.D, mesh->s.K);
+  const int D = mesh->s.D, NF = mesh->s.NF;
   std::vector<double> dofpts;
   if (kind == 2) {   // facet DOF points of every local facet, then the interior points
     dofpts = t.xfd;
@@ -1172,7 +1285,10 @@ dgc_status dgc_point_coords(const dgc_mesh* mesh, int kind, double* xyz, int64_t
     for (int p = 0; p < P; ++p)
       for (int r = 0; r < D; ++r) {
         double x = X0[r];
-        for (int c = 0; c < D; ++c) x += (mesh->h_verts[(size_t)v[c + 1] * D + r] - X0[r]) * ref[p * D + c];
+        for (int c = 0; c < D; ++c) {
+          const int vc = v[mesh->quad && c == 1 ? 3 : c + 1];   // parallelogram: J[:, 1] = X_3 - X_0
+          x += (mesh->h_verts[(size_t)vc * D + r] - X0[r]) * ref[p * D + c];
+        }
         xyz[((size_t)e * P + p) * D + r] = x;
       }
   }
@@ -1244,6 +1360,55 @@ dgc_status dgc_table(int dim, int k, const char* name, double* out, int64_t* cou
   else return fail(DGC_ERR_ARG, "unknown table '%s'", name);
   *count = (int64_t)v->size();
   if (out) std::memcpy(out, v->data(), v->size() * sizeof(double));
+  return DGC_OK;
+}
+
+dgc_status dgc_quad_table(int k, const char* name, double* out, int64_t* count) {
+  if (!name || !count) return fail(DGC_ERR_ARG, "NULL argument");
+  if (!dgc::quad_supported(k)) return fail(DGC_ERR_UNSUPPORTED, "order k=%d not supported for parallelograms", k);
+  const dgc::Tables* tp;
+  try {
+    tp = &dgc::quad_tables(k);
+  } catch (const std::exception& ex) {
+    return fail(DGC_ERR_ARG, "reference table build failed: %s", ex.what());
+  }
+  const dgc::Tables& t = *tp;
+  const std::vector<double>* v = nullptr;
+  const std::string n(name);
+  if (n == "Bv") v = &t.Bv;
+  else if (n == "Gv") v = &t.Gv;
+  else if (n == "wv") v = &t.wv;
+  else if (n == "xv") v = &t.xv;
+  else if (n == "wf") v = &t.wf;
+  else if (n == "sf") v = &t.sf;
+  else if (n == "Bf") v = &t.Bf;
+  else if (n == "Cb") v = &t.Cb;
+  else if (n == "q1L") v = &t.q1L;
+  else if (n == "q1D") v = &t.q1D;
+  else if (n == "q1E") v = &t.q1E;
+  else return fail(DGC_ERR_ARG, "unknown table '%s'", name);
+  *count = (int64_t)v->size();
+  if (out) std::memcpy(out, v->data(), v->size() * sizeof(double));
+  return DGC_OK;
+}
+
+dgc_status dgc_quad_connectivity(int n_vert, int n_elem, const int32_t* elems, int32_t* facet_id, int32_t* nbr,
+                                 int8_t* orient, int8_t* flip, int32_t* n_facets) {
+  if (n_elem <= 0 || n_vert <= 0 || !elems) return fail(DGC_ERR_ARG, "empty mesh");
+  std::vector<int> el(elems, elems + (size_t)n_elem * 4);
+  dgc::Connectivity con;
+  std::vector<signed char> fl;
+  std::vector<int> qn;
+  std::string why = dgc::build_quad_connectivity(n_vert, n_elem, el, con, fl, qn);
+  if (!why.empty()) return fail(DGC_ERR_ARG, "%s", why.c_str());
+  const size_t n = (size_t)n_elem * 4;
+  for (size_t j = 0; j < n; ++j) {
+    if (facet_id) facet_id[j] = con.facet_id[j];
+    if (nbr) nbr[j] = qn[j];
+    if (orient) orient[j] = con.orient[j];
+    if (flip) flip[j] = fl[j];
+  }
+  if (n_facets) *n_facets = con.n_facets;
   return DGC_OK;
 }
 

@@ -20,18 +20,33 @@ constexpr int BLOCK = 128;
 
 inline int grid_for(long n) { return (int)((n + BLOCK - 1) / BLOCK); }
 
-// -grad lambda_f on the reference simplex: (1, .., 1) for f = 0, -e_{f-1} otherwise
-__device__ __forceinline__ double mgl(int f, int a) { return f == 0 ? 1.0 : (a == f - 1 ? -1.0 : 0.0); }
+// Direction of the reference facet flux: on the simplex -grad lambda_f ((1, .., 1)
+// for f = 0, -e_{f-1} otherwise; its length carries the facet measure), on the
+// square the outward unit normal of facet f (eta = 0, xi = 1, eta = 1, xi = 0).
+__device__ __forceinline__ double ref_dir(const DevMesh& m, int f, int a) {
+  if (m.quad) {
+    const double nq[4][2] = {{0.0, -1.0}, {1.0, 0.0}, {0.0, 1.0}, {-1.0, 0.0}};
+    return nq[f][a];
+  }
+  return f == 0 ? 1.0 : (a == f - 1 ? -1.0 : 0.0);
+}
+
+// (-1)^j where the local facet parameter of (e, f) runs against the global one
+// (parallelograms; simplices sort their vertices and never flip)
+__device__ __forceinline__ double flip_sign(const DevMesh& m, int e, int f, int j) {
+  return (m.flip && m.flip[(long)e * 4 + f] && (j & 1)) ? -1.0 : 1.0;
+}
 
 __global__ void geometry_kernel(DevMesh m) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m.E) return;
   const int D = m.s.D;
-  const int* v = m.elems + (long)e * (D + 1);
+  const int* v = m.elems + (long)e * m.s.NF;
   double X0[3], J[9];
   for (int a = 0; a < D; ++a) X0[a] = m.verts[(long)v[0] * D + a];
+  // simplex: J[:, c] = X_{c+1} - X_0; parallelogram: J[:, 0] = X_1 - X_0, J[:, 1] = X_3 - X_0
   for (int c = 0; c < D; ++c)
-    for (int r = 0; r < D; ++r) J[r * D + c] = m.verts[(long)v[c + 1] * D + r] - X0[r];
+    for (int r = 0; r < D; ++r) J[r * D + c] = m.verts[(long)v[m.quad && c == 1 ? 3 : c + 1] * D + r] - X0[r];
   double det;
   if (D == 2) {
     det = J[0] * J[3] - J[1] * J[2];
@@ -51,7 +66,7 @@ __device__ void gather_local(const DevMesh& m, int e, const double* __restrict__
   for (int f = 0; f < s.NF; ++f) {
     const long g = m.facet_id[(long)e * s.NF + f];
     const double sf = sg * (double)m.orient[(long)e * s.NF + f];
-    for (int j = 0; j < s.NFM; ++j) ut[f * s.NFM + j] = sf * u[g * s.NFM + j];
+    for (int j = 0; j < s.NFM; ++j) ut[f * s.NFM + j] = sf * flip_sign(m, e, f, j) * u[g * s.NFM + j];
   }
   const long base = (long)m.nF * s.NFM + (long)e * s.NINT;
   for (int j = 0; j < s.NINT; ++j) ut[s.NF * s.NFM + j] = u[base + j];
@@ -89,7 +104,7 @@ __global__ void wind_prep_kernel(DevMesh m, const double* __restrict__ u, T* __r
     for (int q = 0; q < s.QF; ++q) {
       double acc = 0.0;
       for (int a = 0; a < D; ++a) {
-        const double g = mgl(f, a);
+        const double g = ref_dir(m, f, a);
         if (g == 0.0) continue;
         double ua = 0.0;
         for (int i = 0; i < N; ++i) ua += m.Bf[(long)(f * s.QF + q) * N + i] * uc[a * N + i];
@@ -158,7 +173,7 @@ __global__ void transfer_T_kernel(DevMesh m, const double* __restrict__ f, doubl
     for (int b = 0; b < NW; ++b) z += m.Cb[(long)b * NW + j] * y[b];
     if (j < s.NF * s.NFM) {
       const int lf = j / s.NFM;
-      const double sf = sg * (double)m.orient[(long)e * s.NF + lf];
+      const double sf = sg * (double)m.orient[(long)e * s.NF + lf] * flip_sign(m, e, lf, j % s.NFM);
       zbuf[(long)e * s.NF * s.NFM + j] = sf * z;
     } else {
       g[(long)m.nF * s.NFM + (long)e * s.NINT + (j - s.NF * s.NFM)] = z;
@@ -257,11 +272,11 @@ __global__ void wind_from_potential_kernel(DevMesh m, const double* __restrict__
     for (int q = 0; q < s.QFD; ++q) {
       curl_ref(m, pot, m.Lg_fac + (long)(f * s.QFD + q) * NL * D, Jinv, det, uh);
       double flux = 0.0;
-      for (int a = 0; a < D; ++a) flux += mgl(f, a) * uh[a];
+      for (int a = 0; a < D; ++a) flux += ref_dir(m, f, a) * uh[a];
       for (int j = 0; j < s.NFM; ++j) acc[j] += m.wfd[q] * flux * m.Qfd[q * s.NFM + j];
     }
     const long g = m.facet_id[(long)e * s.NF + f];
-    for (int j = 0; j < s.NFM; ++j) u[g * s.NFM + j] = sg * acc[j];
+    for (int j = 0; j < s.NFM; ++j) u[g * s.NFM + j] = sg * flip_sign(m, e, f, j) * acc[j];
   }
   if (s.NINT) {
     double acc[MAXI];
@@ -308,11 +323,11 @@ __global__ void hdiv_interpolate_kernel(DevMesh m, const double* __restrict__ va
     for (int q = 0; q < s.QFD; ++q) {
       to_ref(ve + (long)(f * s.QFD + q) * D);
       double flux = 0.0;
-      for (int a = 0; a < D; ++a) flux += mgl(f, a) * uh[a];
+      for (int a = 0; a < D; ++a) flux += ref_dir(m, f, a) * uh[a];
       for (int j = 0; j < s.NFM; ++j) acc[j] += m.wfd[q] * flux * m.Qfd[q * s.NFM + j];
     }
     const long g = m.facet_id[(long)e * s.NF + f];
-    for (int j = 0; j < s.NFM; ++j) u[g * s.NFM + j] = sg * acc[j];
+    for (int j = 0; j < s.NFM; ++j) u[g * s.NFM + j] = sg * flip_sign(m, e, f, j) * acc[j];
   }
   if (s.NINT) {
     double acc[MAXI];

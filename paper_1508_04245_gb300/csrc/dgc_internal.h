@@ -74,10 +74,26 @@ struct Tables {
   std::vector<double> xfd;        // [NF][QFD][D]  facet DOF points on each local facet
   std::vector<double> xv;         // [QV][D]
   std::vector<double> sf;         // [QF][D-1]
+  // parallelograms only: 1D tables of the sum-factorised stage kernel
+  std::vector<double> q1L, q1D, q1E;
 };
 
 const Tables& tables(int D, int K);   // cached, thread-safe build
 bool supported(int D, int K);
+
+// Shared long-double helpers of the table builders.
+void gauss_legendre01(int n, std::vector<long double>& x, std::vector<long double>& w);   // n-point rule on [0,1]
+std::vector<long double> invert_matrix(const std::vector<long double>& A, int n);         // row-major n x n
+
+// Parallelograms (uncurved quadrilaterals, Sec. 2 "Preliminaries"): the same
+// table fields with the meaning they have on the reference square [0,1]^2
+// (basis psi_{ab} = l_a(xi) l_b(eta), i = a (k+1) + b, W_h = the H(div)
+// subspace of [Q^k]^2, see dgc_quad.cpp), plus the 1D tables of the
+// sum-factorised stage kernel: q1L [m][k+1] = l_a at the m Gauss points,
+// q1D the same for l_a', q1E [2][k+1] = l_a(0), l_a(1).
+Sizes make_quad_sizes(int K);
+const Tables& quad_tables(int K);
+bool quad_supported(int K);
 
 // Facet connectivity of a conforming simplicial mesh (elements' vertex ids
 // sorted in place).  Returns an empty string on success, else the reason.
@@ -87,5 +103,16 @@ struct Connectivity {
   std::vector<signed char> orient;
 };
 std::string build_connectivity(int D, int n_vert, int n_elem, std::vector<int>& elems, Connectivity& out);
+
+// Facet connectivity of a conforming parallelogram mesh, vertices of every
+// element in cyclic order (not reordered).  Local facet f runs from local
+// vertex kQuadFacet[f][0] to kQuadFacet[f][1]; flip[e][f] = 1 when that runs
+// from the higher to the lower global vertex id; qnbr[e][f] =
+// (e' << 3) | (rev << 2) | f' with rev = 1 when the neighbour's local facet
+// parameter runs the other way, -1 on the boundary.  Facets are numbered by
+// sorting their sorted vertex pairs; the lower-index element owns a facet.
+constexpr int kQuadFacet[4][2] = {{0, 1}, {1, 2}, {3, 2}, {0, 3}};
+std::string build_quad_connectivity(int n_vert, int n_elem, const std::vector<int>& elems, Connectivity& out,
+                                    std::vector<signed char>& flip, std::vector<int>& qnbr);
 
 }  // namespace dgc

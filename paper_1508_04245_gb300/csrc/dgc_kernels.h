@@ -37,11 +37,17 @@ struct DevMesh {
   const double* wfd;
   const double* Qfd;
   const double* Bd;
+  // parallelograms: element type and the facet-parameter flips [E][4]
+  int quad = 0;
+  const signed char* flip = nullptr;
 };
 
 // a == nullptr prepares the kernel (shared-memory attribute) without launching
 cudaError_t launch_stage_2d(int K, bool fp32, const StageArgs* a, cudaStream_t s);
 cudaError_t launch_stage_3d(int K, bool fp32, const StageArgs* a, cudaStream_t s);
+// parallelograms, sum-factorised; a->nbr holds the (e' << 3) | (rev << 2) | f' codes
+// and a->tab the 1D tables [l at the Gauss points | l' there | l(0), l(1)]
+cudaError_t launch_stage_quad(int K, bool fp32, const StageArgs* a, cudaStream_t s);
 
 // tensor-core stage kernel (triangles, k <= 4); a == nullptr prepares the kernel
 bool tc_supported(int D, int K);

@@ -483,6 +483,16 @@ Tables build(int D, int K) {
 
 }  // namespace
 
+void gauss_legendre01(int n, std::vector<long double>& x, std::vector<long double>& w) {
+  gauss_jacobi(n, 0, 0, x, w);
+  for (int i = 0; i < n; ++i) {
+    x[i] = (x[i] + 1) / 2;
+    w[i] /= 2;
+  }
+}
+
+std::vector<long double> invert_matrix(const std::vector<long double>& A, int n) { return invert(A, n); }
+
 Sizes make_sizes(int D, int K) {
   Sizes s;
   s.D = D;

@@ -24,6 +24,8 @@ _vp, _dp, _i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINT
 SIGNATURES = {
     "dgc_mesh_upload": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp,
                         ctypes.POINTER(ctypes.c_void_p)],
+    "dgc_mesh_upload_quad": [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp,
+                             ctypes.POINTER(ctypes.c_void_p)],
     "dgc_mesh_free": [_vp],
     "dgc_sizes": [_vp, _i64p, _i64p],
     "dgc_mesh_info": [_vp, _i64p],
@@ -54,6 +56,8 @@ SIGNATURES = {
     "dgc_table": [ctypes.c_int, ctypes.c_int, ctypes.c_char_p, _vp, _i64p],
     "dgc_connectivity": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
                          ctypes.POINTER(ctypes.c_int32)],
+    "dgc_quad_table": [ctypes.c_int, ctypes.c_char_p, _vp, _i64p],
+    "dgc_quad_connectivity": [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int32)],
     "dgc_last_error": [ctypes.c_char_p, ctypes.c_int],
 }
 
@@ -108,15 +112,26 @@ def _stream(stream):
 
 
 class Mesh:
-    """A dgc_mesh handle: affine simplicial mesh, order k, device geometry."""
+    """A dgc_mesh handle, order k, device geometry: affine simplices (``shape="simplex"``,
+    elems [E][dim+1]) or parallelograms (``shape="quad"``, dim 2, elems [E][4] in cyclic order)."""
 
-    def __init__(self, dim: int, k: int, verts, elems, stream=None):
+    def __init__(self, dim: int, k: int, verts, elems, stream=None, shape: str = "simplex"):
         verts = np.ascontiguousarray(verts, dtype=np.float64)
         elems = np.ascontiguousarray(elems, dtype=np.int32)
         h = ctypes.c_void_p()
-        check(lib().dgc_mesh_upload(dim, k, verts.shape[0], verts.ctypes.data_as(ctypes.c_void_p),
-                                    elems.shape[0], elems.ctypes.data_as(ctypes.c_void_p), _stream(stream),
-                                    ctypes.byref(h)))
+        self.shape = shape
+        if shape == "quad":
+            if dim != 2:
+                raise ValueError("parallelogram meshes are two-dimensional")
+            check(lib().dgc_mesh_upload_quad(k, verts.shape[0], verts.ctypes.data_as(ctypes.c_void_p),
+                                             elems.shape[0], elems.ctypes.data_as(ctypes.c_void_p),
+                                             _stream(stream), ctypes.byref(h)))
+        elif shape == "simplex":
+            check(lib().dgc_mesh_upload(dim, k, verts.shape[0], verts.ctypes.data_as(ctypes.c_void_p),
+                                        elems.shape[0], elems.ctypes.data_as(ctypes.c_void_p), _stream(stream),
+                                        ctypes.byref(h)))
+        else:
+            raise ValueError(f"unknown element shape {shape!r}")
         self._h = h
         info = (ctypes.c_int64 * 11)()
         check(lib().dgc_mesh_info(self._h, info))
@@ -338,6 +353,29 @@ def connectivity(dim: int, n_vert: int, elems):
     vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)      # noqa: E731
     check(lib().dgc_connectivity(dim, n_vert, E, vp(elems), vp(fid), vp(nbr), vp(ori), ctypes.byref(nf)))
     return fid, nbr, ori, nf.value
+
+
+def quad_table(k: int, name: str) -> np.ndarray:
+    """A reference table of the parallelogram element (host only, no GPU needed)."""
+    cnt = ctypes.c_int64()
+    check(lib().dgc_quad_table(k, name.encode(), None, ctypes.byref(cnt)))
+    out = np.empty(cnt.value)
+    check(lib().dgc_quad_table(k, name.encode(), out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)))
+    return out
+
+
+def quad_connectivity(n_vert: int, elems):
+    """(facet_id, nbr codes, orient, flip, n_facets) as the parallelogram upload builds them (host only)."""
+    elems = np.ascontiguousarray(elems, dtype=np.int32)
+    E = elems.shape[0]
+    fid = np.empty((E, 4), np.int32)
+    nbr = np.empty((E, 4), np.int32)
+    ori = np.empty((E, 4), np.int8)
+    flip = np.empty((E, 4), np.int8)
+    nf = ctypes.c_int32()
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)      # noqa: E731
+    check(lib().dgc_quad_connectivity(n_vert, E, vp(elems), vp(fid), vp(nbr), vp(ori), vp(flip), ctypes.byref(nf)))
+    return fid, nbr, ori, flip, nf.value
 
 
 def potential_values(mesh: Mesh, potential) -> np.ndarray:

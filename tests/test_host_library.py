@@ -131,3 +131,45 @@ def test_unsupported_order_is_rejected():
         dgconv.table(3, 6, "Bv")
     with pytest.raises(dgconv.DgcError):
         dgconv.table(2, 0, "Bv")
+
+
+# ---- parallelograms -------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 2, 4, 6])
+def test_quad_tables_match_oracle(k):
+    from oracle import quad as OQ
+    m = OQ.n_points(k)
+    xq, wq = OQ.square_rule(m)
+    N = (k + 1) ** 2
+    Bv = dgconv.quad_table(k, "Bv").reshape(m * m, N)
+    assert np.abs(Bv - OQ.vbasis(k, xq)).max() < 1e-13 * np.abs(Bv).max()
+    assert np.allclose(dgconv.quad_table(k, "wv"), wq, atol=1e-15)
+    t, w = OQ.gauss01(m)
+    assert np.allclose(dgconv.quad_table(k, "sf"), t, atol=1e-15) and np.allclose(dgconv.quad_table(k, "wf"), w)
+    L = dgconv.quad_table(k, "q1L").reshape(m, k + 1)
+    Dl = dgconv.quad_table(k, "q1D").reshape(m, k + 1)
+    E = dgconv.quad_table(k, "q1E").reshape(2, k + 1)
+    for a in range(k + 1):
+        assert np.allclose(L[:, a], OQ.leg(a, t), atol=1e-13) and np.allclose(Dl[:, a], OQ.dleg(a, t), atol=1e-11)
+        assert np.allclose(E[:, a], OQ.leg(a, np.array([0.0, 1.0])), atol=1e-13)
+    Cb = dgconv.quad_table(k, "Cb").reshape(2 * N, 2 * N)
+    ref = np.linalg.inv(OQ.local_dof_matrix(k))
+    assert np.abs(Cb - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_quad_connectivity_matches_oracle():
+    from oracle import quad as OQ
+    v, e = W.parallelogram_mesh(6, 4)
+    M = OQ.QuadMesh(v, e)
+    fid, nbr, ori, flip, nf = dgconv.quad_connectivity(v.shape[0], e)
+    assert nf == M.n_facets
+    assert (fid == M.facet_id).all() and (ori == M.orient).all() and (flip == M.flip).all()
+    inner = nbr >= 0
+    assert (inner == (M.nbr >= 0)).all()
+    assert (np.where(inner, nbr >> 3, -1) == M.nbr).all() and (np.where(inner, nbr & 3, -1) == M.nbr_facet).all()
+    rev = (nbr >> 2) & 1
+    nb_flip = M.flip[np.maximum(M.nbr, 0), np.maximum(M.nbr_facet, 0)]
+    assert (rev[inner] == (M.flip[inner] != nb_flip[inner])).all()
+    bad = e.copy()
+    bad[3, 1] = bad[3, 0]
+    with pytest.raises(dgconv.DgcError):
+        dgconv.quad_connectivity(v.shape[0], bad)
