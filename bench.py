@@ -38,6 +38,7 @@ from paper_1508_04245_gb300 import workloads as W  # noqa: E402
 METRIC = "DG convection DOF-stage updates/s, plain FP64 vs mixed/batched at ≤1e-6 err"
 TC_PRECS = ("tf32x3", "bf16x3")
 WORKLOAD = "square256_k4"
+FP64_TFLOPS = 1.25          # nominal dense FP64 rate of a GB300 (no measured figure in the peaks file)
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -53,7 +54,11 @@ def parse():
     ap.add_argument("--substeps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--no-quad", action="store_true", help="skip the parallelogram workload section")
+    args = ap.parse_args()
+    if W.WORKLOADS[args.workload].shape == "quad" and args.prec in TC_PRECS:
+        ap.error("the tensor-core precisions cover triangles; use --prec fp32 or fp64 on parallelograms")
+    return args
 
 
 def dist_env():
@@ -147,7 +152,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def make_inputs(wl, torch, dgconv):
     verts, elems = wl.mesh()
-    mesh = dgconv.Mesh(wl.dim, wl.k, verts, elems)
+    mesh = dgconv.Mesh(wl.dim, wl.k, verts, elems, shape=wl.shape)
     pot = dgconv.potential_values(mesh, wl.potential())
     wind = mesh.wind_from_potential(torch.tensor(pot, dtype=torch.float64, device="cuda"))
     if wl.unit_peak_speed:
@@ -168,6 +173,15 @@ def stage_bytes_flops(wl):
     contraction, traces and facet test contraction.
     """
     d, k = wl.dim, wl.k
+    if wl.shape == "quad":
+        # parallelograms, sum-factorised: per component m rows of (trace, m points,
+        # two row projections, outer update) and 4 facets of (own and neighbour
+        # trace, m points, scatter); the same bytes convention with 4 facets
+        n, m = k + 1, (3 * k) // 2 + 1
+        N = n * n
+        fma_c = m * (3 * n * n + m * (3 * n + 2)) + 4 * (3 * n * n + m * (3 * n + 1))
+        byts = 3 * N * d * 8 + d * N * 8 + (d * d + 1) * 8 + 4 * 4
+        return byts, 2 * d * fma_c, N
     N = math.comb(k + d, d)
     nq = (3 * k - 1) // 2 + 1
     nf = (3 * k) // 2 + 1
@@ -304,6 +318,78 @@ def measure_batched(torch, dgconv, rank: int, world: int, flush, stream, mixed_p
             "unit": "DOF-stage updates/s"}
 
 
+def measure_quad(torch, dgconv, rank: int, world: int, flush, stream, steps: int = 2):
+    """The parallelogram workload (sum-factorised stage kernel) in FP32 and FP64:
+    the same step as the headline (a1, a2, 100 SSP-RK3 substeps, M^V, a8), the
+    stage time from two graph lengths, and the stage kernel against the HBM roofline."""
+    wl = rank_workload(W.WORKLOADS["parallelogram256_k4"], rank)
+    mesh, wind, u_n, ds = make_inputs(wl, torch, dgconv)
+    v, mv, g = mesh.dg_zeros(), mesh.dg_zeros(), mesh.hdiv_zeros()
+    byts, flops, N = stage_bytes_flops(wl)
+    units = wl.n_elem * N * wl.dim * 3 * wl.substeps
+    hbm, hbm_src = peaks()
+    out = {"workload": wl.name, "elements": wl.n_elem, "k": wl.k, "substeps": wl.substeps,
+           "unit": "DOF-stage updates/s", "alg_bytes_per_elem_stage": byts, "alg_flops_per_elem_stage": flops,
+           "by_prec": {}}
+    ref = None
+    for prec in ("fp64", "fp32"):
+        def step(p=prec):
+            mesh.geometry()
+            mesh.transfer(u_n, out=v)
+            mesh.rk_substeps(wind, v, ds, wl.substeps, 3, p)
+            mesh.mass(v, out=mv)
+            mesh.transfer_T(mv, out=g)
+        step()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        x = mesh.transfer(u_n)
+        mesh.rk_substeps(wind, x, ds, wl.substeps, 3, prec)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = x
+        err = float((x - ref).abs().max() / ref.abs().max())
+
+        def time_rk(n, p=prec):
+            best = None
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.zero_()
+                a.record(stream)
+                mesh.rk_substeps(wind, v, ds, n, 3, p)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t = a.elapsed_time(b)
+                best = t if best is None else min(best, t)
+            return best
+        n_lo = wl.substeps // 2
+        mesh.rk_substeps(wind, v, ds, n_lo, 3, prec)
+        t_lo = time_rk(n_lo)
+        t_hi = time_rk(wl.substeps)
+        stage_ms = (t_hi - t_lo) / (3 * (wl.substeps - n_lo))
+        ms = max_over_ranks(statistics.mean(ts), world, "cuda")
+        achieved = byts * wl.n_elem / (stage_ms * 1e-3) / 1e9
+        tflops = flops * wl.n_elem / (stage_ms * 1e-3) / 1e12
+        roof = {"bound": "hbm", "kernel": "stage_quad_kernel", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_src, "achieved_tflops": tflops}
+        if prec == "fp64":
+            # FP64 FMAs bound this variant: against the nominal FP64 rate of the part
+            roof = {"bound": "alu", "kernel": "stage_quad_kernel", "achieved": tflops, "peak": FP64_TFLOPS,
+                    "unit": "TFLOP/s", "frac": tflops / FP64_TFLOPS, "peak_source": "nominal FP64 (no measured peak)",
+                    "hbm_frac": achieved / hbm}
+        out["by_prec"][prec] = {
+            "value": job_throughput(units, world, ms), "ms_per_step": ms, "max_rel_err_vs_fp64": err,
+            "stage_ms": stage_ms, "roofline": roof}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -316,6 +402,20 @@ class OracleRunner:
         from oracle import mesh as OM
         self.wl = wl
         verts, elems = wl.mesh()
+        if wl.shape == "quad":
+            from oracle import quad as OQ
+            om = OQ.QuadMesh(verts, elems)
+            nodes = OQ.lagrange_nodes(wl.k)
+            X = om.to_physical(np.repeat(np.arange(om.n_elem), nodes.shape[0]), np.tile(nodes, (om.n_elem, 1)))
+            pot = wl.potential()(X[:, 0], X[:, 1]).reshape(om.n_elem, -1)
+            wind = OQ.wind_from_potential(om, wl.k, pot)
+            field = W.fourier_field(wl.seed + 2000, wl.dim)
+            u_n = OQ.dofs_of_function(om, wl.k, lambda x: field(x))
+            self.op = OQ.QuadConvectionOracle(om, wl.k, wind)
+            self.v = OQ.transfer(om, wl.k, u_n)
+            self.ds = OQ.cfl_ds(om, wl.k, wind, wl.cfl)
+            self.units_per_stage = om.n_elem * (wl.k + 1) ** 2 * wl.dim
+            return
         om = OM.Mesh(verts, elems)
         wind = OH.wind_from_potential(om, wl.k, wl.potential())
         if wl.unit_peak_speed:
@@ -477,7 +577,8 @@ def main():
     achieved = byts * wl.n_elem / (stage_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": ncu_traffic(wl, args.prec), "peak_source": hbm_src,
-            "kernel": "stage_tc_kernel" if args.prec in TC_PRECS else "stage_kernel",
+            "kernel": ("stage_tc_kernel" if args.prec in TC_PRECS
+                       else "stage_quad_kernel" if wl.shape == "quad" else "stage_kernel"),
             "stage_ms": stage_ms, "alg_bytes_per_elem_stage": byts, "alg_flops_per_elem_stage": flops,
             "achieved_tflops": flops * wl.n_elem / (stage_ms * 1e-3) / 1e12}
     line = {
@@ -564,6 +665,8 @@ def main():
     if not args.no_batched:
         line["batched"] = measure_batched(torch, dgconv, rank, world, flush, stream,
                                           args.prec if args.prec in TC_PRECS else "bf16x3")
+    if not args.no_quad and wl.shape != "quad":
+        line["parallelogram"] = measure_quad(torch, dgconv, rank, world, flush, stream)
     # clocks sampled from before the first timed step to the end of the GPU measurements
     line["clocks"] = clocks.stop()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

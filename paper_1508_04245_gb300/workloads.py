@@ -272,12 +272,17 @@ class Workload:
     substeps: int
     cfl: float = 0.2
     unit_peak_speed: bool = False
+    shape: str = "simplex"    # "simplex" | "quad" (parallelograms, dim 2)
 
     @property
     def n_elem(self) -> int:
+        if self.shape == "quad":
+            return self.n * self.n
         return (2 if self.dim == 2 else 6) * self.n ** self.dim
 
     def mesh(self):
+        if self.shape == "quad":
+            return parallelogram_mesh(self.n, self.seed)
         if self.dim == 2:
             return square_mesh(self.n, self.jitter, self.seed)
         return cube_mesh(self.n, self.jitter, self.seed)
@@ -294,6 +299,9 @@ WORKLOADS = {
     "cube32_k3": Workload("cube32_k3", 3, 32, 3, 0.0, 3, "fixed", "uniform", 3, 50),
     "cube48_k4": Workload("cube48_k4", 3, 48, 4, 0.05, 4, "random", "uniform", 3, 200,
                           unit_peak_speed=True),
+    # parallelograms: 256 x 256 cells of varying size and shear (3.3M DOFs at k = 4)
+    "parallelogram256_k4": Workload("parallelogram256_k4", 2, 256, 4, 0.0, 6, "random", "fourier", 3, 100,
+                                    shape="quad"),
 }
 
 
