@@ -235,6 +235,30 @@ def parallelogram_mesh(n: int, seed: int | None = None, stretch: float = 0.4, sk
     return verts, elems.astype(np.int32)
 
 
+def curved_square_mesh(n: int, jitter: float = 0.0, seed: int | None = None, delta: float = 0.25,
+                       radius: float = 0.3):
+    """``square_mesh`` with quadratic (P2) elements curved inside a disk.
+
+    Every edge gets a mid-node: its chord midpoint m, moved by
+    ``delta * h * w(m) * (sin(2 pi m_y + phi), cos(2 pi m_x + phi))`` with the
+    cutoff ``w = (1 - r^2 / radius^2)^2`` for ``r = |m - (1/2, 1/2)| < radius``
+    and 0 outside (phi seeded).  Elements with an edge inside the disk are
+    curved, the others (and every boundary edge) stay straight.
+
+    Returns ``(verts, elems, edge_nodes [n_edges, 2])`` with the edges in the
+    order of their sorted vertex pairs, sorted lexicographically.
+    """
+    verts, elems = square_mesh(n, jitter, seed)
+    pairs = sorted({tuple(sorted((int(t[a]), int(t[b])))) for t in elems for a, b in ((0, 1), (0, 2), (1, 2))})
+    P = np.array(pairs)
+    mid = 0.5 * (verts[P[:, 0]] + verts[P[:, 1]])
+    phi = np.random.default_rng(None if seed is None else seed + 555).uniform(0.0, 2.0 * np.pi)
+    r2 = np.sum((mid - 0.5) ** 2, axis=1)
+    w = np.where(r2 < radius ** 2, (1.0 - r2 / radius ** 2) ** 2, 0.0)
+    disp = np.stack([np.sin(2 * np.pi * mid[:, 1] + phi), np.cos(2 * np.pi * mid[:, 0] + phi)], axis=1)
+    return verts, elems, mid + (delta / n) * w[:, None] * disp
+
+
 def tensor_coeffs(seed: int, n_elem: int, k: int) -> np.ndarray:
     """DG coefficients on parallelograms i.i.d. U[-1, 1], layout [E][2][(k+1)^2]."""
     rng = np.random.default_rng(seed)
