@@ -130,6 +130,27 @@ dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int 
 dgc_status dgc_mesh_upload_quad(int k, int n_vert, const double* verts, int n_elem,
                                 const int32_t* elems, void* stream, dgc_mesh** out);
 
+/* Build a handle for quadratic (curved) triangles of order k = 1..6 (remark on
+ * curved elements, Sec. 2.4).  verts, elems as for dgc_mesh_upload with dim = 2;
+ * edge_nodes: host [n_facets][2], the mid-node of every facet in the global facet
+ * order (sorted vertex pairs, lexicographic; dgc_connectivity gives it).  Each
+ * element is the image of the reference triangle under the P2 map through its
+ * three (sorted) vertices and three edge nodes; an element whose edge nodes are
+ * the chord midpoints (within 1e-14 of its shortest edge) is affine and keeps
+ * the affine path.  On curved elements V_h holds the mapped Dubiner
+ * polynomials, the mass matrix is a dense block (stored inverted, N*N doubles
+ * and floats per curved element), I is the L2 projection, I^T its transpose;
+ * the H(div) layout and DOFs are those of the affine case (Piola-mapped BDM_k).
+ * Accepted on such handles: every entry point accepted on affine triangles with
+ * DGC_FP64 / DGC_FP32, except dgc_richardson, dgc_hdiv_interpolate and
+ * dgc_project (DGC_ERR_UNSUPPORTED); the tensor-core precisions return
+ * DGC_ERR_UNSUPPORTED.  dgc_point_coords maps through the quadratic map.
+ * Errors: those of dgc_mesh_upload; DGC_ERR_ARG when det J changes sign inside
+ * an element (checked at the nodes and quadrature points).  Synchronizes
+ * `stream`. */
+dgc_status dgc_mesh_upload_curved(int k, int n_vert, const double* verts, int n_elem, const int32_t* elems,
+                                  const double* edge_nodes, void* stream, dgc_mesh** out);
+
 /* Release the handle and everything the library allocated for it. */
 dgc_status dgc_mesh_free(dgc_mesh* mesh);
 

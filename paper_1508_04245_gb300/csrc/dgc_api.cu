@@ -120,6 +120,13 @@ struct dgc_mesh {
   int quad = 0;                    // 1: parallelograms (dgc_mesh_upload_quad)
   DevBuf<signed char> flip;        // [E][4] facet-parameter flips of a parallelogram mesh
   DevBuf<int> qnbr;                // [E][4] neighbour codes of the parallelogram stage kernel
+  // curved (quadratic) triangles, dgc_mesh_upload_curved
+  int Ec = 0;
+  std::vector<int> h_cid;          // [E] curved index or -1
+  std::vector<double> h_cnodes;    // [Ec][6][2]
+  DevBuf<int> celem, cid;
+  DevBuf<double> cnodes, p2d, p2v, Minv64;
+  DevBuf<float> Minv32;
   std::vector<double> h_verts;     // [nV][D]
   std::vector<int> h_elems;        // [E][NF] sorted
   double h_min = 0.0;
@@ -181,6 +188,14 @@ struct dgc_mesh {
     m.Bd = Bd.ptr;
     m.quad = quad;
     m.flip = flip.ptr;
+    m.Ec = Ec;
+    m.celem = celem.ptr;
+    m.cid = Ec ? cid.ptr : nullptr;
+    m.cnodes = cnodes.ptr;
+    m.p2d = p2d.ptr;
+    m.p2v = p2v.ptr;
+    m.Minv64 = Minv64.ptr;
+    m.Minv32 = Minv32.ptr;
     return m;
   }
 
@@ -204,6 +219,9 @@ struct dgc_mesh {
     orient.release();
     flip.release();
     qnbr.release();
+    for (auto* b : {&celem, &cid}) b->release();
+    for (auto* b : {&cnodes, &p2d, &p2v, &Minv64}) b->release();
+    Minv32.release();
     tab32.release();
     tcblob.release();
     tcblob16.release();
@@ -293,6 +311,11 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
   a.alpha = alpha;
   a.beta = beta;
   a.gamma = gamma;
+  if (m->Ec > 0) {
+    a.cid = m->cid.ptr;
+    a.Minv = fp32 ? (const void*)m->Minv32.ptr : (const void*)m->Minv64.ptr;
+    a.Ec = m->Ec;
+  }
   cudaError_t err = m->quad       ? dgc::launch_stage_quad(m->s.K, fp32, &a, st)
                     : m->s.D == 2 ? dgc::launch_stage_2d(m->s.K, fp32, &a, st)
                                   : dgc::launch_stage_3d(m->s.K, fp32, &a, st);
@@ -304,14 +327,15 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
 bool is_tc(dgc_prec prec) { return prec == DGC_TF32X3 || prec == DGC_BF16X3; }
 
 // the tensor-core stage kernel covers triangles with k <= 4
-bool mesh_tc(const dgc_mesh* m) { return !m->quad && dgc::tc_supported(m->s.D, m->s.K); }
+bool mesh_tc(const dgc_mesh* m) { return !m->quad && m->Ec == 0 && dgc::tc_supported(m->s.D, m->s.K); }
 
 dgc_status check_prec(const dgc_mesh* m, dgc_prec prec) {
   if (prec == DGC_FP64 || prec == DGC_FP32) return DGC_OK;
   if (is_tc(prec)) {
     if (mesh_tc(m)) return DGC_OK;
-    return fail(DGC_ERR_UNSUPPORTED, "%s is available for triangles with k <= 4 (dim %d, k %d%s)",
-                prec == DGC_TF32X3 ? "DGC_TF32X3" : "DGC_BF16X3", m->s.D, m->s.K, m->quad ? ", parallelograms" : "");
+    return fail(DGC_ERR_UNSUPPORTED, "%s is available for affine triangles with k <= 4 (dim %d, k %d%s)",
+                prec == DGC_TF32X3 ? "DGC_TF32X3" : "DGC_BF16X3", m->s.D, m->s.K,
+                m->quad ? ", parallelograms" : (m->Ec ? ", curved elements" : ""));
   }
   return fail(DGC_ERR_ARG, "unknown precision %d", (int)prec);
 }
@@ -851,6 +875,104 @@ dgc_status dgc_mesh_upload_quad(int k, int n_vert, const double* verts, int n_el
   return DGC_OK;
 }
 
+dgc_status dgc_mesh_upload_curved(int k, int n_vert, const double* verts, int n_elem, const int32_t* elems,
+                                  const double* edge_nodes, void* stream, dgc_mesh** out) {
+  DGC_RANGE();
+  if (!out) return fail(DGC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!edge_nodes) return fail(DGC_ERR_ARG, "edge_nodes is NULL");
+  dgc_mesh* m = nullptr;
+  if (dgc_status rc = dgc_mesh_upload(2, k, n_vert, verts, n_elem, elems, stream, &m)) return rc;
+  // facet ids of the sorted elements (the same connectivity the upload built)
+  std::vector<int> el = m->h_elems;
+  dgc::Connectivity con;
+  dgc::build_connectivity(2, n_vert, n_elem, el, con);
+  const dgc::Tables& t = dgc::tables(2, k);
+  // six nodes per element: sorted vertices, then the edge nodes m_01, m_02, m_12
+  // (facets 2, 1, 0: local facet f is opposite local vertex f)
+  const int node_of_facet[3] = {5, 4, 3};
+  const int ends[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  std::vector<double> nodes((size_t)n_elem * 12);
+  m->h_cid.assign(n_elem, -1);
+  std::vector<int> celem;
+  for (int e = 0; e < n_elem; ++e) {
+    double* X = &nodes[(size_t)e * 12];
+    const int* v = &m->h_elems[(size_t)e * 3];
+    for (int a = 0; a < 3; ++a)
+      for (int r = 0; r < 2; ++r) X[a * 2 + r] = verts[(size_t)v[a] * 2 + r];
+    for (int f = 0; f < 3; ++f) {
+      const int g = con.facet_id[(size_t)e * 3 + f];
+      for (int r = 0; r < 2; ++r) X[node_of_facet[f] * 2 + r] = edge_nodes[(size_t)g * 2 + r];
+    }
+    double dev = 0.0, hmin = INFINITY;
+    for (int j = 3; j < 6; ++j) {
+      const double* A = X + ends[j][0] * 2;
+      const double* B = X + ends[j][1] * 2;
+      hmin = std::min(hmin, std::hypot(B[0] - A[0], B[1] - A[1]));
+      for (int r = 0; r < 2; ++r) dev = std::max(dev, std::fabs(X[j * 2 + r] - 0.5 * (A[r] + B[r])));
+    }
+    if (dev > 1e-14 * hmin) {
+      m->h_cid[e] = (int)celem.size();
+      celem.push_back(e);
+    }
+  }
+  // P2 reference gradients at a point
+  auto p2grad = [](double x1, double x2, double* g) {
+    const double x0 = 1.0 - x1 - x2;
+    const double gg[12] = {-(4 * x0 - 1), -(4 * x0 - 1), 4 * x1 - 1, 0.0, 0.0, 4 * x2 - 1,
+                           4 * (x0 - x1), -4 * x1, -4 * x2, 4 * (x0 - x2), 4 * x2, 4 * x1};
+    for (int j = 0; j < 12; ++j) g[j] = gg[j];
+  };
+  auto table_at = [&](const std::vector<double>& pts) {
+    std::vector<double> out(pts.size() / 2 * 12);
+    for (size_t q = 0; q < pts.size() / 2; ++q) p2grad(pts[2 * q], pts[2 * q + 1], &out[q * 12]);
+    return out;
+  };
+  const std::vector<double> p2d = table_at(t.xd), p2v = table_at(t.xv);
+  // the map must not fold: det J keeps the sign of the vertices' affine map at the
+  // nodes and at both rules
+  std::vector<double> checkpts = t.xd;
+  checkpts.insert(checkpts.end(), t.xv.begin(), t.xv.end());
+  const double refnodes[12] = {0, 0, 1, 0, 0, 1, 0.5, 0, 0, 0.5, 0.5, 0.5};
+  checkpts.insert(checkpts.end(), refnodes, refnodes + 12);
+  const std::vector<double> p2c = table_at(checkpts);
+  m->h_cnodes.clear();
+  for (int c = 0; c < (int)celem.size(); ++c) {
+    const int e = celem[c];
+    const double* X = &nodes[(size_t)e * 12];
+    const double* v0 = X;
+    const double sa = (X[2] - v0[0]) * (X[5] - v0[1]) - (X[4] - v0[0]) * (X[3] - v0[1]);
+    for (size_t q = 0; q < checkpts.size() / 2; ++q) {
+      double J[4] = {0, 0, 0, 0};
+      for (int j = 0; j < 6; ++j)
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) J[a * 2 + b] += X[j * 2 + a] * p2c[q * 12 + j * 2 + b];
+      const double det = J[0] * J[3] - J[1] * J[2];
+      if (!(det * sa > 0.0)) {
+        dgc_mesh_free(m);
+        return fail(DGC_ERR_ARG, "curved element %d folds over (det J changes sign)", e);
+      }
+    }
+    m->h_cnodes.insert(m->h_cnodes.end(), X, X + 12);
+  }
+  m->Ec = (int)celem.size();
+  if (m->Ec > 0) {
+    const size_t nn = (size_t)m->s.N * m->s.N * m->Ec;
+    cudaError_t err = cudaSuccess;
+    for (cudaError_t e2 : {m->celem.upload(celem), m->cid.upload(m->h_cid), m->cnodes.upload(m->h_cnodes),
+                           m->p2d.upload(p2d), m->p2v.upload(p2v), m->Minv64.alloc(nn), m->Minv32.alloc(nn)})
+      if (e2 != cudaSuccess) err = e2;
+    if (err == cudaSuccess) err = dgc::launch_geometry(m->view(), as_stream(stream));
+    if (err == cudaSuccess) err = cudaStreamSynchronize(as_stream(stream));
+    if (err != cudaSuccess) {
+      dgc_mesh_free(m);
+      return fail(DGC_ERR_CUDA, "curved geometry failed: %s", cudaGetErrorString(err));
+    }
+  }
+  *out = m;
+  return DGC_OK;
+}
+
 dgc_status dgc_mesh_free(dgc_mesh* mesh) {
   if (!mesh) return DGC_OK;
   drop_batch_graphs(mesh);
@@ -967,6 +1089,7 @@ dgc_status dgc_richardson(dgc_mesh* mesh, const double* wind_hdiv, const double*
                           double* res_dev, void* stream) {
   DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (mesh->Ec) return fail(DGC_ERR_UNSUPPORTED, "the pseudo-time solve takes affine meshes (its norm uses |det J|)");
   if (dgc_status rc = check_prec(mesh, prec)) return rc;
   if (!wind_hdiv || !g_dg || !v_dg || !iters_dev) return fail(DGC_ERR_ARG, "NULL argument");
   if (!(tau > 0.0) || !std::isfinite(tau)) return fail(DGC_ERR_ARG, "tau must be positive and finite (got %g)", tau);
@@ -1282,6 +1405,20 @@ dgc_status dgc_point_coords(const dgc_mesh* mesh, int kind, double* xyz, int64_t
   for (int e = 0; e < mesh->E; ++e) {
     const int* v = &mesh->h_elems[(size_t)e * NF];
     const double* X0 = &mesh->h_verts[(size_t)v[0] * D];
+    if (mesh->Ec && mesh->h_cid[e] >= 0) {   // curved: the quadratic map through the six nodes
+      const double* X = &mesh->h_cnodes[(size_t)mesh->h_cid[e] * 12];
+      for (int p = 0; p < P; ++p) {
+        const double x1 = ref[p * 2], x2 = ref[p * 2 + 1], x0 = 1.0 - x1 - x2;
+        const double phi[6] = {x0 * (2 * x0 - 1), x1 * (2 * x1 - 1), x2 * (2 * x2 - 1), 4 * x0 * x1, 4 * x0 * x2,
+                               4 * x1 * x2};
+        for (int r = 0; r < 2; ++r) {
+          double x = 0.0;
+          for (int j = 0; j < 6; ++j) x += phi[j] * X[j * 2 + r];
+          xyz[((size_t)e * P + p) * 2 + r] = x;
+        }
+      }
+      continue;
+    }
     for (int p = 0; p < P; ++p)
       for (int r = 0; r < D; ++r) {
         double x = X0[r];
@@ -1306,6 +1443,7 @@ dgc_status dgc_wind_from_potential(dgc_mesh* mesh, const double* pot, double* u_
 dgc_status dgc_hdiv_interpolate(dgc_mesh* mesh, const double* vals, double* u_hdiv, void* stream) {
   DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (mesh->Ec) return fail(DGC_ERR_UNSUPPORTED, "point-value input on curved elements is not available");
   if (!vals || !u_hdiv) return fail(DGC_ERR_ARG, "NULL vector");
   DGC_CUDA(dgc::launch_hdiv_interpolate(mesh->view(), vals, u_hdiv, as_stream(stream)));
   return DGC_OK;
@@ -1314,6 +1452,7 @@ dgc_status dgc_hdiv_interpolate(dgc_mesh* mesh, const double* vals, double* u_hd
 dgc_status dgc_project(dgc_mesh* mesh, const double* vals, double* w_dg, void* stream) {
   DGC_RANGE();
   if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (mesh->Ec) return fail(DGC_ERR_UNSUPPORTED, "point-value input on curved elements is not available");
   if (!vals || !w_dg) return fail(DGC_ERR_ARG, "NULL vector");
   DGC_CUDA(dgc::launch_project(mesh->view(), vals, w_dg, as_stream(stream)));
   return DGC_OK;

@@ -16,6 +16,7 @@ constexpr int MAXW = 168;   // BDM_5 on tetrahedra
 constexpr int MAXF = 21;    // dim P^5 on a triangle
 constexpr int MAXI = 84;    // interior moments of BDM_5 on tetrahedra
 constexpr int MAXL = 84;    // dim P^6 in 3D (Lagrange nodes of P^{k+1})
+constexpr int MAXN = 28;    // dim P^6 on a triangle (curved elements)
 constexpr int BLOCK = 128;
 
 inline int grid_for(long n) { return (int)((n + BLOCK - 1) / BLOCK); }
@@ -93,7 +94,10 @@ __global__ void wind_prep_kernel(DevMesh m, const double* __restrict__ u, T* __r
   double ut[MAXW], uc[MAXW];
   gather_local(m, e, u, ut);
   bdm_to_dubiner(m, ut, uc);
-  const double inv = 1.0 / m.detJ[e];
+  // affine: the diagonal mass |det J| folded in as 1/det J; curved: only the sign of
+  // det J, the stage kernel applies the inverse mass block
+  const bool curved = m.cid && m.cid[e] >= 0;
+  const double inv = curved ? (m.detJ[e] > 0 ? 1.0 : -1.0) : 1.0 / m.detJ[e];
   for (int q = 0; q < s.QV; ++q)
     for (int a = 0; a < D; ++a) {
       double acc = 0.0;
@@ -198,6 +202,7 @@ __global__ void mass_kernel(DevMesh m, const double* __restrict__ v, double* out
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long per = (long)m.s.D * m.s.N;
   if (t >= (long)m.E * per) return;
+  if (m.cid && m.cid[t / per] >= 0) return;   // curved elements: curved_mass_kernel
   const double a = fabs(m.detJ[t / per]);
   out[t] = inverse ? v[t] / a : v[t] * a;
 }
@@ -257,12 +262,18 @@ __global__ void wind_from_potential_kernel(DevMesh m, const double* __restrict__
   const Sizes& s = m.s;
   const int D = s.D, NL = s.NLAG, nc = D == 2 ? 1 : 3;
   const double* J = m.J + (long)e * D * D;
-  const double det = m.detJ[e];
+  double det = m.detJ[e];
   double Jinv[9];
   invert_jacobian(D, J, det, Jinv);
+  const double sg = det > 0 ? 1.0 : -1.0;
+  if (m.cid && m.cid[e] >= 0) {
+    // curved: det J J^{-1} curl(psi) = the reference curl of psi^ at every point, for any
+    // map (2D), so the DOFs need no Jacobian: evaluate with J = Id
+    for (int j = 0; j < 9; ++j) Jinv[j] = (j % (D + 1) == 0) ? 1.0 : 0.0;
+    det = 1.0;
+  }
   double pot[MAXL * 3];
   for (int j = 0; j < NL * nc; ++j) pot[j] = pot_all[(long)e * NL * nc + j];
-  const double sg = det > 0 ? 1.0 : -1.0;
   double uh[3];
   // facet moments, computed by the facet's owner (orient = +1)
   for (int f = 0; f < s.NF; ++f) {
@@ -361,6 +372,7 @@ __global__ void project_kernel(DevMesh m, const double* __restrict__ vals, doubl
 __global__ void max_speed_kernel(DevMesh m, const double* __restrict__ u, unsigned long long* out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m.E) return;
+  if (m.cid && m.cid[e] >= 0) return;         // curved elements: curved_max_speed_kernel
   const Sizes& s = m.s;
   const int D = s.D, N = s.N;
   double ut[MAXW], uc[MAXW];
@@ -387,11 +399,197 @@ __global__ void max_speed_kernel(DevMesh m, const double* __restrict__ u, unsign
   atomicMax(out, (unsigned long long)__double_as_longlong(vmax));
 }
 
+// ---- curved (quadratic) triangles: remark on curved elements, Sec. 2.4 ------------
+// J(xi_q) = sum_j X_j (grad^ phi_j(xi_q))^T of curved element c; returns det J
+__device__ double curved_jacobian(const DevMesh& m, int c, const double* p2g, double* J) {
+  const double* X = m.cnodes + (long)c * 12;
+  J[0] = J[1] = J[2] = J[3] = 0.0;
+  for (int j = 0; j < 6; ++j)
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) J[a * 2 + b] += X[j * 2 + a] * p2g[j * 2 + b];
+  return J[0] * J[3] - J[1] * J[2];
+}
+
+// M_T = sum_q w_q |det J(xi_q)| psi_i psi_j on the interior rule (degree 2k+2, exact),
+// Cholesky-factored and inverted column by column into Minv[(i*N + j)*Ec + c]
+__global__ void curved_geometry_kernel(DevMesh m) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.Ec) return;
+  const int N = m.s.N;
+  double L[MAXN * (MAXN + 1) / 2];                    // packed lower triangle, (i, j <= i)
+  for (int j = 0; j < N * (N + 1) / 2; ++j) L[j] = 0.0;
+  for (int q = 0; q < m.s.QD; ++q) {
+    double J[4];
+    const double w = m.wd[q] * fabs(curved_jacobian(m, c, m.p2d + (long)q * 12, J));
+    const double* B = m.Bd + (long)q * N;
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j <= i; ++j) L[i * (i + 1) / 2 + j] += w * B[i] * B[j];
+  }
+  for (int j = 0; j < N; ++j) {
+    double d = L[j * (j + 1) / 2 + j];
+    for (int l = 0; l < j; ++l) d -= L[j * (j + 1) / 2 + l] * L[j * (j + 1) / 2 + l];
+    const double ljj = sqrt(d);                         // d > 0: M_T is SPD on an unfolded element
+    L[j * (j + 1) / 2 + j] = ljj;
+    for (int i = j + 1; i < N; ++i) {
+      double x = L[i * (i + 1) / 2 + j];
+      for (int l = 0; l < j; ++l) x -= L[i * (i + 1) / 2 + l] * L[j * (j + 1) / 2 + l];
+      L[i * (i + 1) / 2 + j] = x / ljj;
+    }
+  }
+  for (int col = 0; col < N; ++col) {                 // M^{-1} e_col = L^{-T} L^{-1} e_col
+    double y[MAXN];
+    for (int i = 0; i < N; ++i) {
+      double x = i == col ? 1.0 : 0.0;
+      for (int l = 0; l < i; ++l) x -= L[i * (i + 1) / 2 + l] * y[l];
+      y[i] = x / L[i * (i + 1) / 2 + i];
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      double x = y[i];
+      for (int l = i + 1; l < N; ++l) x -= L[l * (l + 1) / 2 + i] * y[l];
+      y[i] = x / L[i * (i + 1) / 2 + i];
+    }
+    for (int i = 0; i < N; ++i) {
+      m.Minv64[(long)(i * N + col) * m.Ec + c] = y[i];
+      m.Minv32[(long)(i * N + col) * m.Ec + c] = (float)y[i];
+    }
+  }
+}
+
+// I u on curved elements, the L2 projection: w = M^{-1} sum_q w_q psi(xi_q) sign(det J) J(xi_q) u^(xi_q)
+__global__ void curved_transfer_kernel(DevMesh m, const double* __restrict__ u, double* __restrict__ w) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.Ec) return;
+  const int e = m.celem[c], N = m.s.N;
+  double ut[MAXW], uc[MAXW], b[2 * MAXN];
+  gather_local(m, e, u, ut);
+  bdm_to_dubiner(m, ut, uc);
+  const double sg = m.detJ[e] > 0 ? 1.0 : -1.0;
+  for (int j = 0; j < 2 * N; ++j) b[j] = 0.0;
+  for (int q = 0; q < m.s.QD; ++q) {
+    double J[4];
+    curved_jacobian(m, c, m.p2d + (long)q * 12, J);
+    const double* B = m.Bd + (long)q * N;
+    double uh[2] = {0.0, 0.0};
+    for (int i = 0; i < N; ++i) {
+      uh[0] += B[i] * uc[i];
+      uh[1] += B[i] * uc[N + i];
+    }
+    for (int cc = 0; cc < 2; ++cc) {
+      const double v = m.wd[q] * sg * (J[cc * 2] * uh[0] + J[cc * 2 + 1] * uh[1]);
+      for (int i = 0; i < N; ++i) b[cc * N + i] += v * B[i];
+    }
+  }
+  double* we = w + (long)e * 2 * N;
+  for (int cc = 0; cc < 2; ++cc)
+    for (int i = 0; i < N; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < N; ++j) acc += m.Minv64[(long)(i * N + j) * m.Ec + c] * b[cc * N + j];
+      we[cc * N + i] = acc;
+    }
+}
+
+// the transpose on curved elements: y = M^{-1} f, the adjoint of the point evaluation and
+// Piola factor, then Cb^T; facet entries (signed) to zbuf, interior entries to g
+__global__ void curved_transfer_T_kernel(DevMesh m, const double* __restrict__ f, double* __restrict__ g,
+                                         double* __restrict__ zbuf) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.Ec) return;
+  const Sizes& s = m.s;
+  const int e = m.celem[c], N = s.N, NW = s.NW;
+  const double* fe = f + (long)e * 2 * N;
+  double y[2 * MAXN], ua[MAXW];
+  for (int cc = 0; cc < 2; ++cc)
+    for (int i = 0; i < N; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < N; ++j) acc += m.Minv64[(long)(i * N + j) * m.Ec + c] * fe[cc * N + j];
+      y[cc * N + i] = acc;
+    }
+  for (int j = 0; j < NW; ++j) ua[j] = 0.0;
+  const double sg = m.detJ[e] > 0 ? 1.0 : -1.0;
+  for (int q = 0; q < s.QD; ++q) {
+    double J[4];
+    curved_jacobian(m, c, m.p2d + (long)q * 12, J);
+    const double* B = m.Bd + (long)q * N;
+    double Y[2] = {0.0, 0.0};
+    for (int i = 0; i < N; ++i) {
+      Y[0] += B[i] * y[i];
+      Y[1] += B[i] * y[N + i];
+    }
+    for (int a = 0; a < 2; ++a) {
+      const double v = m.wd[q] * sg * (J[a] * Y[0] + J[2 + a] * Y[1]);   // (J^T Y)_a
+      for (int i = 0; i < N; ++i) ua[a * N + i] += v * B[i];
+    }
+  }
+  for (int j = 0; j < NW; ++j) {
+    double z = 0.0;
+    for (int b = 0; b < NW; ++b) z += m.Cb[(long)b * NW + j] * ua[b];
+    if (j < s.NF * s.NFM) {
+      const int lf = j / s.NFM;
+      zbuf[(long)e * s.NF * s.NFM + j] = sg * (double)m.orient[(long)e * s.NF + lf] * z;
+    } else {
+      g[(long)m.nF * s.NFM + (long)e * s.NINT + (j - s.NF * s.NFM)] = z;
+    }
+  }
+}
+
+// M^V v or (M^V)^{-1} v on curved elements (M v by quadrature, M^{-1} from the blocks)
+__global__ void curved_mass_kernel(DevMesh m, const double* __restrict__ v, double* out, bool inverse) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.Ec) return;
+  const int e = m.celem[c], N = m.s.N;
+  double x[2 * MAXN], r[2 * MAXN];
+  for (int j = 0; j < 2 * N; ++j) {
+    x[j] = v[(long)e * 2 * N + j];
+    r[j] = 0.0;
+  }
+  if (inverse) {
+    for (int cc = 0; cc < 2; ++cc)
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) r[cc * N + i] += m.Minv64[(long)(i * N + j) * m.Ec + c] * x[cc * N + j];
+  } else {
+    for (int q = 0; q < m.s.QD; ++q) {
+      double J[4];
+      const double w = m.wd[q] * fabs(curved_jacobian(m, c, m.p2d + (long)q * 12, J));
+      const double* B = m.Bd + (long)q * N;
+      for (int cc = 0; cc < 2; ++cc) {
+        double val = 0.0;
+        for (int i = 0; i < N; ++i) val += B[i] * x[cc * N + i];
+        for (int i = 0; i < N; ++i) r[cc * N + i] += w * val * B[i];
+      }
+    }
+  }
+  for (int j = 0; j < 2 * N; ++j) out[(long)e * 2 * N + j] = r[j];
+}
+
+// max |u| = |J u^| / |det J| over the volume points of the curved elements
+__global__ void curved_max_speed_kernel(DevMesh m, const double* __restrict__ u, unsigned long long* out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.Ec) return;
+  const int e = m.celem[c], N = m.s.N;
+  double ut[MAXW], uc[MAXW];
+  gather_local(m, e, u, ut);
+  bdm_to_dubiner(m, ut, uc);
+  double vmax = 0.0;
+  for (int q = 0; q < m.s.QV; ++q) {
+    double J[4];
+    const double det = curved_jacobian(m, c, m.p2v + (long)q * 12, J);
+    double uh[2] = {0.0, 0.0};
+    for (int i = 0; i < N; ++i) {
+      uh[0] += m.Bv[q * N + i] * uc[i];
+      uh[1] += m.Bv[q * N + i] * uc[N + i];
+    }
+    const double x0 = J[0] * uh[0] + J[1] * uh[1], x1 = J[2] * uh[0] + J[3] * uh[1];
+    vmax = fmax(vmax, sqrt(x0 * x0 + x1 * x1) / fabs(det));
+  }
+  atomicMax(out, (unsigned long long)__double_as_longlong(vmax));
+}
+
 }  // namespace
 
 cudaError_t launch_geometry(const DevMesh& m, cudaStream_t s) {
   if (m.E == 0) return cudaSuccess;
   geometry_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m);
+  if (m.Ec > 0) curved_geometry_kernel<<<grid_for(m.Ec), BLOCK, 0, s>>>(m);
   return cudaGetLastError();
 }
 
@@ -413,12 +611,14 @@ cudaError_t launch_wind_coeffs(const DevMesh& m, const double* u, float* wc, int
 cudaError_t launch_transfer(const DevMesh& m, const double* u, double* w, cudaStream_t s) {
   if (m.E == 0) return cudaSuccess;
   transfer_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, u, w);
+  if (m.Ec > 0) curved_transfer_kernel<<<grid_for(m.Ec), BLOCK, 0, s>>>(m, u, w);   // overwrites
   return cudaGetLastError();
 }
 
 cudaError_t launch_transfer_T(const DevMesh& m, const double* f, double* g, double* zbuf, cudaStream_t s) {
   if (m.E == 0) return cudaSuccess;
   transfer_T_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, f, g, zbuf);
+  if (m.Ec > 0) curved_transfer_T_kernel<<<grid_for(m.Ec), BLOCK, 0, s>>>(m, f, g, zbuf);   // overwrites
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   facet_reduce_kernel<<<grid_for((long)m.nF * m.s.NFM), BLOCK, 0, s>>>(m, zbuf, g);
@@ -429,6 +629,7 @@ cudaError_t launch_mass(const DevMesh& m, const double* v, double* out, bool inv
   const long n = (long)m.E * m.s.D * m.s.N;
   if (n == 0) return cudaSuccess;
   mass_kernel<<<grid_for(n), BLOCK, 0, s>>>(m, v, out, inverse);
+  if (m.Ec > 0) curved_mass_kernel<<<grid_for(m.Ec), BLOCK, 0, s>>>(m, v, out, inverse);
   return cudaGetLastError();
 }
 
@@ -453,6 +654,7 @@ cudaError_t launch_project(const DevMesh& m, const double* vals, double* w, cuda
 cudaError_t launch_max_speed(const DevMesh& m, const double* u, unsigned long long* out, cudaStream_t s) {
   if (m.E == 0) return cudaSuccess;
   max_speed_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, u, out);
+  if (m.Ec > 0) curved_max_speed_kernel<<<grid_for(m.Ec), BLOCK, 0, s>>>(m, u, out);
   return cudaGetLastError();
 }
 

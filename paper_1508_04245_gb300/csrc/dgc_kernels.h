@@ -40,6 +40,18 @@ struct DevMesh {
   // parallelograms: element type and the facet-parameter flips [E][4]
   int quad = 0;
   const signed char* flip = nullptr;
+  // curved (quadratic) triangles: Ec of them, celem [Ec] their element ids, cid [E]
+  // the curved index of an element or -1, cnodes [Ec][6][2] their P2 nodes, the P2
+  // reference gradients at the interior rule (p2d [QD][6][2]) and at the volume rule
+  // (p2v [QV][6][2]), and their inverse mass blocks [N*N][Ec] (FP64 and FP32)
+  int Ec = 0;
+  const int* celem = nullptr;
+  const int* cid = nullptr;
+  const double* cnodes = nullptr;
+  const double* p2d = nullptr;
+  const double* p2v = nullptr;
+  double* Minv64 = nullptr;
+  float* Minv32 = nullptr;
 };
 
 // a == nullptr prepares the kernel (shared-memory attribute) without launching

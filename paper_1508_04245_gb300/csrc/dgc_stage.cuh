@@ -40,6 +40,12 @@ struct StageArgs {
   const void* tab;     // stage table blob (StageTab layout)
   int E;
   double alpha, beta, gamma;
+  // curved triangles (null cid: none): the residual of element e with cid[e] >= 0 is
+  // multiplied by its inverse mass block Minv[(i*N + j)*Ec + cid[e]] (T-typed), the
+  // frozen wind of such an element carrying sign(det J) instead of 1/det J
+  const int* cid = nullptr;
+  const void* Minv = nullptr;
+  int Ec = 0;
 };
 
 // Rows padded to multiples of 4 values (zero filled) so the kernel reads them in
@@ -94,7 +100,7 @@ constexpr int stage_block_default() {
 }
 int stage_block_get(int D, int K, bool fp32);   // tuned value or 0
 
-template <int D, int K, typename T, int CPT, bool SMEM>
+template <int D, int K, typename T, int CPT, bool SMEM, bool CURVED>
 __global__ void __launch_bounds__(256, 1) stage_kernel(StageArgs a) {
   using Dm = Dims<D, K>;
   using TB = StageTab<D, K>;
@@ -315,6 +321,27 @@ __global__ void __launch_bounds__(256, 1) stage_kernel(StageArgs a) {
   // ---- epilogue: RK stage combination in FP64 --------------------------------
   double* vout_e = a.vout + ((long)e * D + c0) * N;
   const double* vn_e = a.vn ? a.vn + ((long)e * D + c0) * N : nullptr;
+  if constexpr (CURVED) {
+    // curved element: the residual times its inverse mass block (remark on curved
+    // elements, Sec. 2.4), one output row at a time
+    const int ci = a.cid[e];
+    if (ci >= 0) {
+      const T* __restrict__ Mi = static_cast<const T*>(a.Minv) + ci;
+#pragma unroll 1
+      for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          T acc = (T)0;
+#pragma unroll
+          for (int j = 0; j < N; ++j) acc += Mi[(long)(i * N + j) * a.Ec] * r[c][j];
+          double x = a.beta * vin_e[c * N + i] - a.gamma * (double)acc;
+          if (vn_e) x += a.alpha * vn_e[c * N + i];
+          vout_e[c * N + i] = x;
+        }
+      }
+      return;
+    }
+  }
 #pragma unroll
   for (int c = 0; c < CPT; ++c)
 #pragma unroll
@@ -334,12 +361,20 @@ cudaError_t launch_stage_t(const StageArgs* ap, cudaStream_t stream) {
   const int tuned = stage_block_get(D, K, sizeof(T) == 4);
   const int BLOCK = tuned > 0 ? tuned : stage_block_default<T, D, K>();
   const size_t smem = SMEM ? StageTab<D, K>::size * sizeof(T) : 0;
-  auto kern = stage_kernel<D, K, T, CPT, SMEM>;
+  // the curved-element variant exists for triangles only
+  auto kern_c = stage_kernel<D, K, T, CPT, SMEM, D == 2>;
+  auto kern = stage_kernel<D, K, T, CPT, SMEM, false>;
   if (!ap) {
-    if (smem > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024) {
+      cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err == cudaSuccess && D == 2)
+        err = cudaFuncSetAttribute(kern_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      return err;
+    }
     return cudaSuccess;
   }
   const StageArgs& a = *ap;
+  if (D == 2 && a.cid) kern = kern_c;
   const long work = (long)a.E * (D / CPT);
   const int grid = (int)((work + BLOCK - 1) / BLOCK);
   if (grid == 0) return cudaSuccess;

@@ -26,6 +26,8 @@ SIGNATURES = {
                         ctypes.POINTER(ctypes.c_void_p)],
     "dgc_mesh_upload_quad": [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp,
                              ctypes.POINTER(ctypes.c_void_p)],
+    "dgc_mesh_upload_curved": [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
+                               ctypes.POINTER(ctypes.c_void_p)],
     "dgc_mesh_free": [_vp],
     "dgc_sizes": [_vp, _i64p, _i64p],
     "dgc_mesh_info": [_vp, _i64p],
@@ -113,9 +115,10 @@ def _stream(stream):
 
 class Mesh:
     """A dgc_mesh handle, order k, device geometry: affine simplices (``shape="simplex"``,
-    elems [E][dim+1]) or parallelograms (``shape="quad"``, dim 2, elems [E][4] in cyclic order)."""
+    elems [E][dim+1]), parallelograms (``shape="quad"``, dim 2, elems [E][4] in cyclic order) or
+    quadratic triangles (``shape="curved"``, dim 2, plus ``edge_nodes`` [n_facets][2])."""
 
-    def __init__(self, dim: int, k: int, verts, elems, stream=None, shape: str = "simplex"):
+    def __init__(self, dim: int, k: int, verts, elems, stream=None, shape: str = "simplex", edge_nodes=None):
         verts = np.ascontiguousarray(verts, dtype=np.float64)
         elems = np.ascontiguousarray(elems, dtype=np.int32)
         h = ctypes.c_void_p()
@@ -126,6 +129,14 @@ class Mesh:
             check(lib().dgc_mesh_upload_quad(k, verts.shape[0], verts.ctypes.data_as(ctypes.c_void_p),
                                              elems.shape[0], elems.ctypes.data_as(ctypes.c_void_p),
                                              _stream(stream), ctypes.byref(h)))
+        elif shape == "curved":
+            if dim != 2 or edge_nodes is None:
+                raise ValueError("curved meshes are two-dimensional and need edge_nodes [n_facets, 2]")
+            en = np.ascontiguousarray(edge_nodes, dtype=np.float64)
+            check(lib().dgc_mesh_upload_curved(k, verts.shape[0], verts.ctypes.data_as(ctypes.c_void_p),
+                                               elems.shape[0], elems.ctypes.data_as(ctypes.c_void_p),
+                                               en.ctypes.data_as(ctypes.c_void_p), _stream(stream),
+                                               ctypes.byref(h)))
         elif shape == "simplex":
             check(lib().dgc_mesh_upload(dim, k, verts.shape[0], verts.ctypes.data_as(ctypes.c_void_p),
                                         elems.shape[0], elems.ctypes.data_as(ctypes.c_void_p), _stream(stream),

@@ -235,7 +235,7 @@ def parallelogram_mesh(n: int, seed: int | None = None, stretch: float = 0.4, sk
     return verts, elems.astype(np.int32)
 
 
-def curved_square_mesh(n: int, jitter: float = 0.0, seed: int | None = None, delta: float = 0.25,
+def curved_square_mesh(n: int, jitter: float = 0.0, seed: int | None = None, delta: float = 0.15,
                        radius: float = 0.3):
     """``square_mesh`` with quadratic (P2) elements curved inside a disk.
 
