@@ -54,10 +54,11 @@ def parse():
     ap.add_argument("--substeps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--no-quad", action="store_true", help="skip the parallelogram workload section")
+    ap.add_argument("--no-shapes", action="store_true",
+                    help="skip the parallelogram and curved-triangle sections")
     args = ap.parse_args()
-    if W.WORKLOADS[args.workload].shape == "quad" and args.prec in TC_PRECS:
-        ap.error("the tensor-core precisions cover triangles; use --prec fp32 or fp64 on parallelograms")
+    if W.WORKLOADS[args.workload].shape != "simplex" and args.prec in TC_PRECS:
+        ap.error("the tensor-core precisions cover affine triangles; use --prec fp32 or fp64 on other shapes")
     return args
 
 
@@ -151,15 +152,20 @@ class ClockSampler:
 # workload construction (untimed)
 # ---------------------------------------------------------------------------
 def make_inputs(wl, torch, dgconv):
-    verts, elems = wl.mesh()
-    mesh = dgconv.Mesh(wl.dim, wl.k, verts, elems, shape=wl.shape)
+    m = wl.mesh()
+    mesh = dgconv.Mesh(wl.dim, wl.k, m[0], m[1], shape=wl.shape, edge_nodes=m[2] if len(m) > 2 else None)
     pot = dgconv.potential_values(mesh, wl.potential())
     wind = mesh.wind_from_potential(torch.tensor(pot, dtype=torch.float64, device="cuda"))
     if wl.unit_peak_speed:
         wind /= mesh.max_wind_speed(wind)
-    field = W.fourier_field(wl.seed + 2000, wl.dim)
-    X = mesh.point_coords(2)
-    u_n = mesh.hdiv_interpolate(torch.tensor(field(X), dtype=torch.float64, device="cuda"))
+    if wl.state == "wind":
+        # the transported velocity: another exactly divergence-free field
+        pot2 = dgconv.potential_values(mesh, W.stream_random(wl.seed + 2000))
+        u_n = mesh.wind_from_potential(torch.tensor(pot2, dtype=torch.float64, device="cuda"))
+    else:
+        field = W.fourier_field(wl.seed + 2000, wl.dim)
+        X = mesh.point_coords(2)
+        u_n = mesh.hdiv_interpolate(torch.tensor(field(X), dtype=torch.float64, device="cuda"))
     ds = mesh.cfl_ds(wind, wl.cfl)
     return mesh, wind, u_n, ds
 
@@ -318,19 +324,29 @@ def measure_batched(torch, dgconv, rank: int, world: int, flush, stream, mixed_p
             "unit": "DOF-stage updates/s"}
 
 
-def measure_quad(torch, dgconv, rank: int, world: int, flush, stream, steps: int = 2):
-    """The parallelogram workload (sum-factorised stage kernel) in FP32 and FP64:
-    the same step as the headline (a1, a2, 100 SSP-RK3 substeps, M^V, a8), the
-    stage time from two graph lengths, and the stage kernel against the HBM roofline."""
-    wl = rank_workload(W.WORKLOADS["parallelogram256_k4"], rank)
+def measure_shape(torch, dgconv, name: str, rank: int, world: int, flush, stream, steps: int = 2):
+    """Another element shape in FP32 and FP64 (parallelograms: the sum-factorised stage
+    kernel; curved triangles: the CUDA-core kernel with inverse mass blocks): the same
+    step as the headline (a1, a2, 100 SSP-RK3 substeps, M^V, a8), the stage time from two
+    graph lengths, and the stage kernel against its roofline."""
+    wl = rank_workload(W.WORKLOADS[name], rank)
     mesh, wind, u_n, ds = make_inputs(wl, torch, dgconv)
     v, mv, g = mesh.dg_zeros(), mesh.dg_zeros(), mesh.hdiv_zeros()
+    kernel = "stage_quad_kernel" if wl.shape == "quad" else "stage_kernel"
     byts, flops, N = stage_bytes_flops(wl)
+    curved_frac = mesh.n_curved / wl.n_elem if wl.shape == "curved" else None
+    if curved_frac:
+        # the curved elements' inverse mass block: read once per stage (FP32 or FP64 like
+        # the contraction; counted at 8 bytes) and multiplied into the residual
+        byts = byts + curved_frac * N * N * 8
+        flops = flops + curved_frac * 2 * N * N * wl.dim
     units = wl.n_elem * N * wl.dim * 3 * wl.substeps
     hbm, hbm_src = peaks()
     out = {"workload": wl.name, "elements": wl.n_elem, "k": wl.k, "substeps": wl.substeps,
            "unit": "DOF-stage updates/s", "alg_bytes_per_elem_stage": byts, "alg_flops_per_elem_stage": flops,
            "by_prec": {}}
+    if curved_frac is not None:
+        out["curved_elements"] = mesh.n_curved
     ref = None
     for prec in ("fp64", "fp32"):
         def step(p=prec):
@@ -377,11 +393,11 @@ def measure_quad(torch, dgconv, rank: int, world: int, flush, stream, steps: int
         ms = max_over_ranks(statistics.mean(ts), world, "cuda")
         achieved = byts * wl.n_elem / (stage_ms * 1e-3) / 1e9
         tflops = flops * wl.n_elem / (stage_ms * 1e-3) / 1e12
-        roof = {"bound": "hbm", "kernel": "stage_quad_kernel", "achieved": achieved, "peak": hbm,
+        roof = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_src, "achieved_tflops": tflops}
         if prec == "fp64":
             # FP64 FMAs bound this variant: against the nominal FP64 rate of the part
-            roof = {"bound": "alu", "kernel": "stage_quad_kernel", "achieved": tflops, "peak": FP64_TFLOPS,
+            roof = {"bound": "alu", "kernel": kernel, "achieved": tflops, "peak": FP64_TFLOPS,
                     "unit": "TFLOP/s", "frac": tflops / FP64_TFLOPS, "peak_source": "nominal FP64 (no measured peak)",
                     "hbm_frac": achieved / hbm}
         out["by_prec"][prec] = {
@@ -665,8 +681,9 @@ def main():
     if not args.no_batched:
         line["batched"] = measure_batched(torch, dgconv, rank, world, flush, stream,
                                           args.prec if args.prec in TC_PRECS else "bf16x3")
-    if not args.no_quad and wl.shape != "quad":
-        line["parallelogram"] = measure_quad(torch, dgconv, rank, world, flush, stream)
+    if not args.no_shapes and wl.shape == "simplex":
+        line["parallelogram"] = measure_shape(torch, dgconv, "parallelogram256_k4", rank, world, flush, stream)
+        line["curved"] = measure_shape(torch, dgconv, "curved256_k4", rank, world, flush, stream)
     # clocks sampled from before the first timed step to the end of the GPU measurements
     line["clocks"] = clocks.stop()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

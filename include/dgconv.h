@@ -157,9 +157,11 @@ dgc_status dgc_mesh_free(dgc_mesh* mesh);
 /* Lengths of the dg and hdiv vectors of this mesh. */
 dgc_status dgc_sizes(const dgc_mesh* mesh, int64_t* n_dg, int64_t* n_hdiv);
 
-/* info[0..10] = dim, k, n_elem, n_facets, N, N_W (=dim*N), n_fm, n_int,
- * n_lagrange (=dim P^{k+1}), n_proj (points of the projection rule),
- * n_dofpts (points per element of the H(div) interpolation). */
+/* info[0..12] = dim, k, n_elem, n_facets, N, N_W (=dim*N), n_fm, n_int,
+ * n_lagrange (nodes of the potential interpolation per element), n_proj
+ * (points of the projection rule), n_dofpts (points per element of the H(div)
+ * interpolation), shape (0 simplices, 1 parallelograms, 2 quadratic triangles),
+ * n_curved (curved elements; 0 unless shape 2).  info holds 13 entries. */
 dgc_status dgc_mesh_info(const dgc_mesh* mesh, int64_t* info);
 
 /* Step a1: recompute J (columns x_{i+1}-x_0 of the sorted vertices) and

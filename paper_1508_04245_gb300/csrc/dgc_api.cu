@@ -992,7 +992,9 @@ dgc_status dgc_mesh_info(const dgc_mesh* mesh, int64_t* info) {
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (!info) return fail(DGC_ERR_ARG, "info is NULL");
   const Sizes& s = mesh->s;
-  int64_t v[11] = {s.D, s.K, mesh->E, mesh->nF, s.N, s.NW, s.NFM, s.NINT, s.NLAG, s.QD, s.NF * s.QFD + s.QD};
+  const int64_t shape = mesh->quad ? 1 : (mesh->h_cid.empty() ? 0 : 2);
+  int64_t v[13] = {s.D, s.K, mesh->E, mesh->nF, s.N, s.NW, s.NFM, s.NINT, s.NLAG, s.QD, s.NF * s.QFD + s.QD,
+                   shape, mesh->Ec};
   std::memcpy(info, v, sizeof(v));
   return DGC_OK;
 }

@@ -144,10 +144,10 @@ class Mesh:
         else:
             raise ValueError(f"unknown element shape {shape!r}")
         self._h = h
-        info = (ctypes.c_int64 * 11)()
+        info = (ctypes.c_int64 * 13)()
         check(lib().dgc_mesh_info(self._h, info))
         (self.dim, self.k, self.n_elem, self.n_facets, self.N, self.NW, self.n_fm, self.n_int,
-         self.n_lagrange, self.n_proj, self.n_dofpts) = [int(x) for x in info]
+         self.n_lagrange, self.n_proj, self.n_dofpts, _shape, self.n_curved) = [int(x) for x in info]
         a, b = ctypes.c_int64(), ctypes.c_int64()
         check(lib().dgc_sizes(self._h, ctypes.byref(a), ctypes.byref(b)))
         self.n_dg, self.n_hdiv = a.value, b.value

@@ -291,12 +291,12 @@ class Workload:
     jitter: float
     seed: int
     wind: str         # "single" | "random" (2D stream fn) / "fixed" | "random" (3D potential)
-    state: str        # "uniform" | "fourier"
+    state: str        # "uniform" | "fourier" | "wind" (a second divergence-free field)
     scheme: int       # 2 = SSP-RK2, 3 = SSP-RK3
     substeps: int
     cfl: float = 0.2
     unit_peak_speed: bool = False
-    shape: str = "simplex"    # "simplex" | "quad" (parallelograms, dim 2)
+    shape: str = "simplex"    # "simplex" | "quad" (parallelograms) | "curved" (quadratic triangles), dim 2
 
     @property
     def n_elem(self) -> int:
@@ -305,8 +305,11 @@ class Workload:
         return (2 if self.dim == 2 else 6) * self.n ** self.dim
 
     def mesh(self):
+        """(verts, elems), or (verts, elems, edge_nodes) for curved meshes."""
         if self.shape == "quad":
             return parallelogram_mesh(self.n, self.seed)
+        if self.shape == "curved":
+            return curved_square_mesh(self.n, self.jitter, self.seed)
         if self.dim == 2:
             return square_mesh(self.n, self.jitter, self.seed)
         return cube_mesh(self.n, self.jitter, self.seed)
@@ -326,6 +329,8 @@ WORKLOADS = {
     # parallelograms: 256 x 256 cells of varying size and shear (3.3M DOFs at k = 4)
     "parallelogram256_k4": Workload("parallelogram256_k4", 2, 256, 4, 0.0, 6, "random", "fourier", 3, 100,
                                     shape="quad"),
+    # quadratic triangles, edges inside a disk of radius 0.3 curved (about 28% of the elements)
+    "curved256_k4": Workload("curved256_k4", 2, 256, 4, 0.10, 7, "random", "wind", 3, 100, shape="curved"),
 }
 
 
