@@ -857,7 +857,8 @@ dgc_status dgc_mesh_upload_quad(int k, int n_vert, const double* verts, int n_el
             up(m->wd.upload(t.wd)) && up(m->wfd.upload(t.wfd)) && up(m->Qfd.upload(t.Qfd)) &&
             up(m->Bd.upload(t.Bd)) && up(m->tab64.upload(quad_stage_blob<double>(t))) &&
             up(m->tab32.upload(quad_stage_blob<float>(t))) && up(m->status.alloc(1)) &&
-            up(cudaMemset(m->status.ptr, 0, sizeof(int)));
+            up(cudaMemset(m->status.ptr, 0, sizeof(int))) &&
+            up(dgc::quad_tables_to_constant(k, quad_stage_blob<double>(t)));
   if (!ok) {
     cudaError_t err = cudaGetLastError();
     m->release_all();

@@ -60,6 +60,9 @@ cudaError_t launch_stage_3d(int K, bool fp32, const StageArgs* a, cudaStream_t s
 // parallelograms, sum-factorised; a->nbr holds the (e' << 3) | (rev << 2) | f' codes
 // and a->tab the 1D tables [l at the Gauss points | l' there | l(0), l(1)]
 cudaError_t launch_stage_quad(int K, bool fp32, const StageArgs* a, cudaStream_t s);
+// copy the order-K 1D tables [l at the Gauss points | l' there | l(0), l(1)] into the
+// kernel's constant-memory slot (synchronous; call before any stream capture)
+cudaError_t quad_tables_to_constant(int K, const std::vector<double>& tab);
 
 // tensor-core stage kernel (triangles, k <= 4); a == nullptr prepares the kernel
 bool tc_supported(int D, int K);

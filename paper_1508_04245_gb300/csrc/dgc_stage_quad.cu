@@ -24,12 +24,28 @@
 //     way, the upwind values at the facet points, their projection on l_j and
 //     its outer product with l(0) or l(1) back into r.
 //
+// The 1D tables live in constant memory (one slot per order).
 // Epilogue (a7): vout = alpha vn + beta vin - gamma r in FP64.
 #include "dgc_kernels.h"
 #include "dgc_stage.cuh"
 
 namespace dgc {
 namespace {
+
+// The 1D tables of every order, in constant memory: every thread reads the same
+// entry at the same time, so the FMAs take them as constant-bank operands with no
+// load instruction (filled by quad_tables_to_constant at mesh upload).
+constexpr int kQuadTabMax = 2 * 10 * 7 + 2 * 7;   // m <= 10 points, n <= 7 modes (k <= 6)
+__constant__ float kQuadTab32[7][kQuadTabMax];
+__constant__ double kQuadTab64[7][kQuadTabMax];
+
+template <int K, typename T>
+__device__ __forceinline__ T qtab(int j) {
+  if constexpr (sizeof(T) == 4)
+    return kQuadTab32[K][j];
+  else
+    return kQuadTab64[K][j];
+}
 
 template <int K>
 struct QuadDims {
@@ -45,14 +61,10 @@ template <int K, typename T>
 __global__ void __launch_bounds__(128) stage_quad_kernel(StageArgs a) {
   using Q = QuadDims<K>;
   constexpr int n = Q::n, N = Q::N, m = Q::m, QV = Q::QV;
-  __shared__ T tab[Q::size];
-  const T* gtab = static_cast<const T*>(a.tab);
-  for (int j = threadIdx.x; j < Q::size; j += blockDim.x) tab[j] = gtab[j];
-  __syncthreads();
-  const T* L = tab + Q::oL;
-  const T* Dl = tab + Q::oD;
-  const T* E0 = tab + Q::oE;
-  const T* E1 = tab + Q::oE + n;
+  auto L = [](int j) { return qtab<K, T>(Q::oL + j); };
+  auto Dl = [](int j) { return qtab<K, T>(Q::oD + j); };
+  auto E0 = [](int j) { return qtab<K, T>(Q::oE + j); };
+  auto E1 = [](int j) { return qtab<K, T>(Q::oE + n + j); };
 
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2L * a.E) return;
@@ -77,7 +89,7 @@ __global__ void __launch_bounds__(128) stage_quad_kernel(StageArgs a) {
     for (int b = 0; b < n; ++b) {
       T acc = (T)0;
 #pragma unroll
-      for (int aa = 0; aa < n; ++aa) acc += w[aa * n + b] * L[p * n + aa];
+      for (int aa = 0; aa < n; ++aa) acc += w[aa * n + b] * L(p * n + aa);
       tb[b] = acc;
       P0[b] = (T)0;
       P1[b] = (T)0;
@@ -86,19 +98,19 @@ __global__ void __launch_bounds__(128) stage_quad_kernel(StageArgs a) {
     for (int q = 0; q < m; ++q) {
       T W = (T)0;
 #pragma unroll
-      for (int b = 0; b < n; ++b) W += tb[b] * L[q * n + b];
+      for (int b = 0; b < n; ++b) W += tb[b] * L(q * n + b);
       const int pq = p * m + q;
       const T f0 = Uw[(long)(pq * 2) * E + e] * W;
       const T f1 = Uw[(long)(pq * 2 + 1) * E + e] * W;
 #pragma unroll
       for (int b = 0; b < n; ++b) {
-        P0[b] += f0 * L[q * n + b];
-        P1[b] += f1 * Dl[q * n + b];
+        P0[b] += f0 * L(q * n + b);
+        P1[b] += f1 * Dl(q * n + b);
       }
     }
 #pragma unroll
     for (int aa = 0; aa < n; ++aa) {
-      const T la = L[p * n + aa], da = Dl[p * n + aa];
+      const T la = L(p * n + aa), da = Dl(p * n + aa);
 #pragma unroll
       for (int b = 0; b < n; ++b) r[aa * n + b] -= da * P0[b] + la * P1[b];
     }
@@ -111,13 +123,14 @@ __global__ void __launch_bounds__(128) stage_quad_kernel(StageArgs a) {
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     const bool along_xi = (f & 1) == 0;
-    const T* Ef = (f == 0 || f == 3) ? E0 : E1;   // the normal coordinate is 0 (f = 0, 3) or 1
+    // the basis at the normal coordinate 0 (f = 0, 3) or 1 (f = 1, 2)
+    auto Ef = [f](int j) { return (f == 0 || f == 3) ? qtab<K, T>(Q::oE + j) : qtab<K, T>(Q::oE + n + j); };
     T to[n], tn[n], ph[n];
 #pragma unroll
     for (int j = 0; j < n; ++j) {
       T acc = (T)0;
 #pragma unroll
-      for (int l = 0; l < n; ++l) acc += (along_xi ? w[j * n + l] : w[l * n + j]) * Ef[l];
+      for (int l = 0; l < n; ++l) acc += (along_xi ? w[j * n + l] : w[l * n + j]) * Ef(l);
       to[j] = acc;
       tn[j] = (T)0;
       ph[j] = (T)0;
@@ -127,13 +140,13 @@ __global__ void __launch_bounds__(128) stage_quad_kernel(StageArgs a) {
       const int ne = code >> 3, fn = code & 3;
       const bool rev = (code & 4) != 0;
       const bool nxi = (fn & 1) == 0;
-      const T* En = (fn == 0 || fn == 3) ? E0 : E1;
+      const int oEn = Q::oE + ((fn == 0 || fn == 3) ? 0 : n);   // runtime facet of the neighbour
       const double* __restrict__ wn = a.vin + ((long)ne * 2 + c) * N;
 #pragma unroll
       for (int j = 0; j < n; ++j) {
         T acc = (T)0;
 #pragma unroll
-        for (int l = 0; l < n; ++l) acc += (T)(nxi ? wn[j * n + l] : wn[l * n + j]) * En[l];
+        for (int l = 0; l < n; ++l) acc += (T)(nxi ? wn[j * n + l] : wn[l * n + j]) * qtab<K, T>(oEn + l);
         tn[j] = (rev && (j & 1)) ? -acc : acc;
       }
     }
@@ -142,22 +155,22 @@ __global__ void __launch_bounds__(128) stage_quad_kernel(StageArgs a) {
       T o = (T)0, nb = (T)0;
 #pragma unroll
       for (int j = 0; j < n; ++j) {
-        o += to[j] * L[q * n + j];
-        nb += tn[j] * L[q * n + j];
+        o += to[j] * L(q * n + j);
+        nb += tn[j] * L(q * n + j);
       }
       const T fw = Fw[(long)(f * m + q) * E + e];
       const T val = fw * (fw >= (T)0 ? o : nb);
 #pragma unroll
-      for (int j = 0; j < n; ++j) ph[j] += val * L[q * n + j];
+      for (int j = 0; j < n; ++j) ph[j] += val * L(q * n + j);
     }
 #pragma unroll
     for (int j = 0; j < n; ++j)
 #pragma unroll
       for (int l = 0; l < n; ++l) {
         if (along_xi)
-          r[j * n + l] += ph[j] * Ef[l];
+          r[j * n + l] += ph[j] * Ef(l);
         else
-          r[l * n + j] += ph[j] * Ef[l];
+          r[l * n + j] += ph[j] * Ef(l);
       }
   }
 
@@ -185,6 +198,15 @@ cudaError_t launch_quad_t(const StageArgs* ap, cudaStream_t stream) {
 }
 
 }  // namespace
+
+cudaError_t quad_tables_to_constant(int K, const std::vector<double>& tab) {
+  if (K < 1 || K > 6 || (int)tab.size() > kQuadTabMax) return cudaErrorInvalidValue;
+  std::vector<float> t32(tab.begin(), tab.end());
+  cudaError_t err = cudaMemcpyToSymbol(kQuadTab64, tab.data(), tab.size() * sizeof(double),
+                                       (size_t)K * kQuadTabMax * sizeof(double));
+  if (err != cudaSuccess) return err;
+  return cudaMemcpyToSymbol(kQuadTab32, t32.data(), t32.size() * sizeof(float), (size_t)K * kQuadTabMax * sizeof(float));
+}
 
 cudaError_t launch_stage_quad(int K, bool fp32, const StageArgs* a, cudaStream_t s) {
   switch (K) {
