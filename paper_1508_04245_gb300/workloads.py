@@ -259,6 +259,57 @@ def curved_square_mesh(n: int, jitter: float = 0.0, seed: int | None = None, del
     return verts, elems, mid + (delta / n) * w[:, None] * disp
 
 
+def parallelepiped_mesh(n: int, seed: int | None = None, stretch: float = 0.4, skew: float = 0.3,
+                        reorient: bool = True):
+    """``n^3`` parallelepipeds (uncurved hexahedra).
+
+    Vertex (i, j, l) sits at ``(x_i + a_j + b_l, y_j + c_l, z_l)`` with random
+    spacings of x, y, z (each ``1 + U[-stretch, stretch]``, normalised) and
+    random-walk shifts a, b, c (steps ``U[-skew, skew]`` times the layer
+    thickness): separable coordinates make every cell a parallelepiped, each
+    with its own size and shear.  With ``reorient`` the vertex numbering is a
+    random permutation and every cell lists its vertices under one of the 48
+    symmetries of the cube (axis permutation and reflections), so every face
+    orientation and both signs of det J occur.
+
+    Returns ``(verts [ (n+1)^3, 3 ], elems [ n^3, 8 ] int32)``, local vertex order
+    (0,0,0), (1,0,0), (1,1,0), (0,1,0), (0,0,1), (1,0,1), (1,1,1), (0,1,1).
+    """
+    rng = np.random.default_rng(seed)
+    axes = []
+    for _ in range(3):
+        w = 1.0 + rng.uniform(-stretch, stretch, n)
+        axes.append(np.concatenate([[0.0], np.cumsum(w / w.sum())]))
+    x, y, z = axes
+    dy, dz = np.diff(y), np.diff(z)
+    a = np.concatenate([[0.0], np.cumsum(rng.uniform(-skew, skew, n) * dy)])
+    b = np.concatenate([[0.0], np.cumsum(rng.uniform(-skew, skew, n) * dz)])
+    c = np.concatenate([[0.0], np.cumsum(rng.uniform(-skew, skew, n) * dz)])
+    m = n + 1
+    vid = lambda i, j, l: i + m * (j + m * l)                   # noqa: E731
+    verts = np.array([(x[i] + a[j] + b[l], y[j] + c[l], z[l]) for l in range(m) for j in range(m) for i in range(m)])
+    corners = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+    elems = np.array([[vid(i + ci, j + cj, l + cl) for ci, cj, cl in corners]
+                      for l in range(n) for j in range(n) for i in range(n)], dtype=np.int64)
+    if reorient:
+        perm = rng.permutation(verts.shape[0])
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        verts = verts[inv]
+        elems = perm[elems]
+        index = {cc: t for t, cc in enumerate(corners)}
+        for e in range(elems.shape[0]):
+            p = rng.permutation(3)
+            fl = rng.integers(0, 2, 3)
+            old = elems[e].copy()
+            for t, cn in enumerate(corners):
+                co = [0, 0, 0]
+                for d in range(3):
+                    co[p[d]] = cn[d] ^ int(fl[d])
+                elems[e, t] = old[index[tuple(co)]]
+    return verts, elems.astype(np.int32)
+
+
 def tensor_coeffs(seed: int, n_elem: int, k: int) -> np.ndarray:
     """DG coefficients on parallelograms i.i.d. U[-1, 1], layout [E][2][(k+1)^2]."""
     rng = np.random.default_rng(seed)
