@@ -130,6 +130,26 @@ dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int 
 dgc_status dgc_mesh_upload_quad(int k, int n_vert, const double* verts, int n_elem,
                                 const int32_t* elems, void* stream, dgc_mesh** out);
 
+/* Build a handle for a conforming mesh of parallelepipeds (uncurved hexahedra)
+ * of order k = 1..3.  verts: host [n_vert][3]; elems: host [n_elem][8] vertex
+ * ids in the local order (0,0,0), (1,0,0), (1,1,0), (0,1,0), (0,0,1), (1,0,1),
+ * (1,1,1), (0,1,1) of the reference cube (kept: x = X_0 + J xi with
+ * J = [X_1 - X_0, X_3 - X_0, X_4 - X_0]); every vertex must sit at X_0 + J c within
+ * 1e-12 of the element's size.  V_h = [Q^k]^3 on psi_{abc} = l_a l_b l_c,
+ * i = (a (k+1) + b)(k+1) + c; W_h the H(div) subspace of the Piola images of
+ * [Q^k]^3.  H(div) layout: [n_faces][(k+1)^2] face moments
+ * int_F u.n_F l_a(s1) l_b(s2) dS, mode a (k+1) + b, in the face's global parameter
+ * (origin at its lowest vertex id, s1 towards the lower-id of the origin's two
+ * face neighbours, s2 towards the other; n_F the lower-index element's outward
+ * normal), then [E][3(k+1)^2(k-1)] interior moments of the reference field
+ * against l_a l_b l_c in component d with the d-th degree <= k-2 (d outer, then
+ * a, b, c).  Faces are numbered by their sorted vertex quadruples.  The same
+ * entry points as for parallelograms accept such handles (DGC_FP64, DGC_FP32);
+ * dgc_wind_from_potential takes the vector potential at the (k+1)^3 nodes
+ * (a/k, b/k, c/k), [E][(k+1)^3][3].  Synchronizes `stream`. */
+dgc_status dgc_mesh_upload_hex(int k, int n_vert, const double* verts, int n_elem, const int32_t* elems,
+                               void* stream, dgc_mesh** out);
+
 /* Build a handle for quadratic (curved) triangles of order k = 1..6 (remark on
  * curved elements, Sec. 2.4).  verts, elems as for dgc_mesh_upload with dim = 2;
  * edge_nodes: host [n_facets][2], the mid-node of every facet in the global facet
@@ -160,7 +180,8 @@ dgc_status dgc_sizes(const dgc_mesh* mesh, int64_t* n_dg, int64_t* n_hdiv);
 /* info[0..12] = dim, k, n_elem, n_facets, N, N_W (=dim*N), n_fm, n_int,
  * n_lagrange (nodes of the potential interpolation per element), n_proj
  * (points of the projection rule), n_dofpts (points per element of the H(div)
- * interpolation), shape (0 simplices, 1 parallelograms, 2 quadratic triangles),
+ * interpolation), shape (0 simplices, 1 parallelograms, 2 quadratic triangles,
+ * 3 parallelepipeds),
  * n_curved (curved elements; 0 unless shape 2).  info holds 13 entries. */
 dgc_status dgc_mesh_info(const dgc_mesh* mesh, int64_t* info);
 

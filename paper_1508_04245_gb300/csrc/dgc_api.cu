@@ -118,6 +118,8 @@ struct dgc_mesh {
   Sizes s;
   int E = 0, nF = 0, nV = 0;
   int quad = 0;                    // 1: parallelograms (dgc_mesh_upload_quad)
+  int hex = 0;                     // 1: parallelepipeds (dgc_mesh_upload_hex)
+  DevBuf<signed char> fcode;       // [E][6] face codes of a parallelepiped mesh
   DevBuf<signed char> flip;        // [E][4] facet-parameter flips of a parallelogram mesh
   DevBuf<int> qnbr;                // [E][4] neighbour codes of the parallelogram stage kernel
   // curved (quadratic) triangles, dgc_mesh_upload_curved
@@ -188,6 +190,8 @@ struct dgc_mesh {
     m.Bd = Bd.ptr;
     m.quad = quad;
     m.flip = flip.ptr;
+    m.hex = hex;
+    m.fcode = fcode.ptr;
     m.Ec = Ec;
     m.celem = celem.ptr;
     m.cid = Ec ? cid.ptr : nullptr;
@@ -218,6 +222,7 @@ struct dgc_mesh {
     for (auto* b : {&elems, &nbr, &facet_id, &facet_sides}) b->release();
     orient.release();
     flip.release();
+    fcode.release();
     qnbr.release();
     for (auto* b : {&celem, &cid}) b->release();
     for (auto* b : {&cnodes, &p2d, &p2v, &Minv64}) b->release();
@@ -281,7 +286,8 @@ dgc_status check_mesh(const dgc_mesh* m) {
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 dgc_status ensure_wind_scratch(dgc_mesh* m, bool fp32) {
-  cudaError_t perr = m->quad       ? dgc::launch_stage_quad(m->s.K, fp32, nullptr, nullptr)
+  cudaError_t perr = m->hex        ? dgc::launch_stage_hex(m->s.K, fp32, nullptr, nullptr, nullptr)
+                     : m->quad     ? dgc::launch_stage_quad(m->s.K, fp32, nullptr, nullptr)
                      : m->s.D == 2 ? dgc::launch_stage_2d(m->s.K, fp32, nullptr, nullptr)
                                    : dgc::launch_stage_3d(m->s.K, fp32, nullptr, nullptr);
   if (perr != cudaSuccess) return fail(DGC_ERR_CUDA, "stage kernel setup failed: %s", cudaGetErrorString(perr));
@@ -305,7 +311,7 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
   a.vout = vout;
   a.Uw = fp32 ? (const void*)m->Uw32.ptr : (const void*)m->Uw64.ptr;
   a.Fw = fp32 ? (const void*)m->Fw32.ptr : (const void*)m->Fw64.ptr;
-  a.nbr = m->quad ? m->qnbr.ptr : m->nbr.ptr;
+  a.nbr = (m->quad || m->hex) ? m->qnbr.ptr : m->nbr.ptr;
   a.tab = fp32 ? (const void*)m->tab32.ptr : (const void*)m->tab64.ptr;
   a.E = m->E;
   a.alpha = alpha;
@@ -316,7 +322,8 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
     a.Minv = fp32 ? (const void*)m->Minv32.ptr : (const void*)m->Minv64.ptr;
     a.Ec = m->Ec;
   }
-  cudaError_t err = m->quad       ? dgc::launch_stage_quad(m->s.K, fp32, &a, st)
+  cudaError_t err = m->hex        ? dgc::launch_stage_hex(m->s.K, fp32, &a, m->fcode.ptr, st)
+                    : m->quad     ? dgc::launch_stage_quad(m->s.K, fp32, &a, st)
                     : m->s.D == 2 ? dgc::launch_stage_2d(m->s.K, fp32, &a, st)
                                   : dgc::launch_stage_3d(m->s.K, fp32, &a, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "stage kernel launch failed: %s", cudaGetErrorString(err));
@@ -327,7 +334,9 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
 bool is_tc(dgc_prec prec) { return prec == DGC_TF32X3 || prec == DGC_BF16X3; }
 
 // the tensor-core stage kernel covers triangles with k <= 4
-bool mesh_tc(const dgc_mesh* m) { return !m->quad && m->Ec == 0 && dgc::tc_supported(m->s.D, m->s.K); }
+bool mesh_tc(const dgc_mesh* m) {
+  return !m->quad && !m->hex && m->Ec == 0 && dgc::tc_supported(m->s.D, m->s.K);
+}
 
 dgc_status check_prec(const dgc_mesh* m, dgc_prec prec) {
   if (prec == DGC_FP64 || prec == DGC_FP32) return DGC_OK;
@@ -335,7 +344,7 @@ dgc_status check_prec(const dgc_mesh* m, dgc_prec prec) {
     if (mesh_tc(m)) return DGC_OK;
     return fail(DGC_ERR_UNSUPPORTED, "%s is available for affine triangles with k <= 4 (dim %d, k %d%s)",
                 prec == DGC_TF32X3 ? "DGC_TF32X3" : "DGC_BF16X3", m->s.D, m->s.K,
-                m->quad ? ", parallelograms" : (m->Ec ? ", curved elements" : ""));
+                m->quad ? ", parallelograms" : (m->hex ? ", parallelepipeds" : (m->Ec ? ", curved elements" : "")));
   }
   return fail(DGC_ERR_ARG, "unknown precision %d", (int)prec);
 }
@@ -876,6 +885,102 @@ dgc_status dgc_mesh_upload_quad(int k, int n_vert, const double* verts, int n_el
   return DGC_OK;
 }
 
+dgc_status dgc_mesh_upload_hex(int k, int n_vert, const double* verts, int n_elem, const int32_t* elems,
+                               void* stream, dgc_mesh** out) {
+  DGC_RANGE();
+  if (!out) return fail(DGC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!dgc::hex_supported(k)) return fail(DGC_ERR_UNSUPPORTED, "order k=%d not supported for parallelepipeds", k);
+  if (n_vert <= 0 || n_elem <= 0 || !verts || !elems)
+    return fail(DGC_ERR_ARG, "empty mesh or NULL arrays (n_vert=%d, n_elem=%d)", n_vert, n_elem);
+  if (n_elem >= (1 << 28)) return fail(DGC_ERR_ARG, "at most 2^28 - 1 parallelepipeds (got %d)", n_elem);
+  dgc_mesh* m = new dgc_mesh();
+  m->hex = 1;
+  m->s = dgc::make_hex_sizes(k);
+  m->E = n_elem;
+  m->nV = n_vert;
+  m->h_verts.assign(verts, verts + (size_t)n_vert * 3);
+  m->h_elems.assign(elems, elems + (size_t)n_elem * 8);
+  dgc::Connectivity con;
+  std::vector<signed char> fcode;
+  std::vector<int> qnbr;
+  std::string why = dgc::build_hex_connectivity(n_vert, n_elem, m->h_elems, con, fcode, qnbr);
+  if (!why.empty()) {
+    delete m;
+    return fail(DGC_ERR_ARG, "%s", why.c_str());
+  }
+  m->nF = con.n_facets;
+  // ---- validate: every vertex at X_0 + J c for its reference corner c; shortest edge
+  const int corner[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0}, {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+  double hmin = INFINITY;
+  for (int e = 0; e < n_elem; ++e) {
+    const int* v = &m->h_elems[(size_t)e * 8];
+    const double* X0 = verts + (size_t)v[0] * 3;
+    double J[3][3], scale = 0.0;
+    const int cols[3] = {1, 3, 4};
+    for (int c = 0; c < 3; ++c)
+      for (int r = 0; r < 3; ++r) {
+        J[r][c] = verts[(size_t)v[cols[c]] * 3 + r] - X0[r];
+        scale += std::fabs(J[r][c]);
+      }
+    double gap = 0.0;
+    for (int a = 0; a < 8; ++a)
+      for (int r = 0; r < 3; ++r) {
+        double x = X0[r];
+        for (int c = 0; c < 3; ++c) x += J[r][c] * corner[a][c];
+        gap = std::max(gap, std::fabs(x - verts[(size_t)v[a] * 3 + r]));
+      }
+    if (!(gap <= 1e-12 * scale)) {
+      delete m;
+      return fail(DGC_ERR_ARG, "element %d is not a parallelepiped (vertex off by %g)", e, gap);
+    }
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) {
+      delete m;
+      return fail(DGC_ERR_ARG, "element %d is degenerate (det J = %g)", e, det);
+    }
+    for (int c = 0; c < 3; ++c) hmin = std::min(hmin, std::sqrt(J[0][c] * J[0][c] + J[1][c] * J[1][c] + J[2][c] * J[2][c]));
+  }
+  m->h_min = hmin;
+  cudaStream_t st = as_stream(stream);
+  const dgc::Tables* tp;
+  try {
+    tp = &dgc::hex_tables(k);
+  } catch (const std::exception& ex) {
+    delete m;
+    return fail(DGC_ERR_ARG, "reference table build failed: %s", ex.what());
+  }
+  const dgc::Tables& t = *tp;
+  auto up = [&](cudaError_t err) -> bool { return err == cudaSuccess; };
+  bool ok = up(m->verts.upload(m->h_verts)) && up(m->elems.upload(m->h_elems)) && up(m->nbr.upload(con.nbr)) &&
+            up(m->facet_id.upload(con.facet_id)) && up(m->orient.upload(con.orient)) &&
+            up(m->facet_sides.upload(con.sides)) && up(m->fcode.upload(fcode)) && up(m->qnbr.upload(qnbr)) &&
+            up(m->J.alloc((size_t)n_elem * 9)) && up(m->detJ.alloc(n_elem)) && up(m->Bv.upload(t.Bv)) &&
+            up(m->wv.upload(t.wv)) && up(m->wf.upload(t.wf)) && up(m->Bf.upload(t.Bf)) && up(m->Cb.upload(t.Cb)) &&
+            up(m->Lg_int.upload(t.Lg_int)) && up(m->Lg_fac.upload(t.Lg_fac)) && up(m->Tint.upload(t.Tint)) &&
+            up(m->wd.upload(t.wd)) && up(m->wfd.upload(t.wfd)) && up(m->Qfd.upload(t.Qfd)) &&
+            up(m->Bd.upload(t.Bd)) && up(m->tab64.upload(quad_stage_blob<double>(t))) &&
+            up(m->tab32.upload(quad_stage_blob<float>(t))) && up(m->status.alloc(1)) &&
+            up(cudaMemset(m->status.ptr, 0, sizeof(int)));
+  if (!ok) {
+    cudaError_t err = cudaGetLastError();
+    m->release_all();
+    delete m;
+    return fail(DGC_ERR_ALLOC, "device upload failed: %s", cudaGetErrorString(err));
+  }
+  cudaError_t err = dgc::launch_geometry(m->view(), st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) {
+    m->release_all();
+    delete m;
+    return fail(DGC_ERR_CUDA, "geometry kernel failed: %s", cudaGetErrorString(err));
+  }
+  *out = m;
+  return DGC_OK;
+}
+
 dgc_status dgc_mesh_upload_curved(int k, int n_vert, const double* verts, int n_elem, const int32_t* elems,
                                   const double* edge_nodes, void* stream, dgc_mesh** out) {
   DGC_RANGE();
@@ -993,7 +1098,7 @@ dgc_status dgc_mesh_info(const dgc_mesh* mesh, int64_t* info) {
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (!info) return fail(DGC_ERR_ARG, "info is NULL");
   const Sizes& s = mesh->s;
-  const int64_t shape = mesh->quad ? 1 : (mesh->h_cid.empty() ? 0 : 2);
+  const int64_t shape = mesh->quad ? 1 : mesh->hex ? 3 : (mesh->h_cid.empty() ? 0 : 2);
   int64_t v[13] = {s.D, s.K, mesh->E, mesh->nF, s.N, s.NW, s.NFM, s.NINT, s.NLAG, s.QD, s.NF * s.QFD + s.QD,
                    shape, mesh->Ec};
   std::memcpy(info, v, sizeof(v));
@@ -1142,7 +1247,7 @@ dgc_status dgc_autotune(dgc_mesh* mesh, const double* wind_hdiv, dgc_prec prec, 
   if (reps < 1 || reps > 1000) return fail(DGC_ERR_ARG, "reps must lie in 1..1000 (got %d)", reps);
   if (block_out) *block_out = 0;
   if (is_tc(prec)) return DGC_OK;   // the tensor-core kernel has one tile shape (128 x 288)
-  if (mesh->quad) return DGC_OK;    // the parallelogram kernel has one block shape (128)
+  if (mesh->quad || mesh->hex) return DGC_OK;   // the tensor-product kernels have one block shape (128)
   const bool fp32 = prec == DGC_FP32;
   const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
   if (dgc_status rc = ensure_prec_scratch(mesh, prec)) return rc;
@@ -1394,7 +1499,9 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
 dgc_status dgc_point_coords(const dgc_mesh* mesh, int kind, double* xyz, int64_t* count) {
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (kind < 0 || kind > 2) return fail(DGC_ERR_ARG, "kind must be 0, 1 or 2");
-  const dgc::Tables& t = mesh->quad ? dgc::quad_tables(mesh->s.K) : dgc::tables(mesh->s.D, mesh->s.K);
+  const dgc::Tables& t = mesh->quad  ? dgc::quad_tables(mesh->s.K)
+                         : mesh->hex ? dgc::hex_tables(mesh->s.K)
+                                     : dgc::tables(mesh->s.D, mesh->s.K);
   const int D = mesh->s.D, NF = mesh->s.NF;
   std::vector<double> dofpts;
   if (kind == 2) {   // facet DOF points of every local facet, then the interior points
@@ -1406,7 +1513,7 @@ dgc_status dgc_point_coords(const dgc_mesh* mesh, int kind, double* xyz, int64_t
   if (count) *count = (int64_t)mesh->E * P;
   if (!xyz) return DGC_OK;
   for (int e = 0; e < mesh->E; ++e) {
-    const int* v = &mesh->h_elems[(size_t)e * NF];
+    const int* v = &mesh->h_elems[(size_t)e * (mesh->hex ? 8 : NF)];   // vertices per element
     const double* X0 = &mesh->h_verts[(size_t)v[0] * D];
     if (mesh->Ec && mesh->h_cid[e] >= 0) {   // curved: the quadratic map through the six nodes
       const double* X = &mesh->h_cnodes[(size_t)mesh->h_cid[e] * 12];
@@ -1426,7 +1533,8 @@ dgc_status dgc_point_coords(const dgc_mesh* mesh, int kind, double* xyz, int64_t
       for (int r = 0; r < D; ++r) {
         double x = X0[r];
         for (int c = 0; c < D; ++c) {
-          const int vc = v[mesh->quad && c == 1 ? 3 : c + 1];   // parallelogram: J[:, 1] = X_3 - X_0
+          // simplex: X_{c+1}; parallelogram: X_1, X_3; parallelepiped: X_1, X_3, X_4
+          const int vc = v[c == 0 ? 1 : (mesh->quad || mesh->hex) ? (c == 1 ? 3 : 4) : c + 1];
           x += (mesh->h_verts[(size_t)vc * D + r] - X0[r]) * ref[p * D + c];
         }
         xyz[((size_t)e * P + p) * D + r] = x;

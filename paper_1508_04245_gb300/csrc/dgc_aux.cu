@@ -12,9 +12,9 @@
 namespace dgc {
 namespace {
 
-constexpr int MAXW = 168;   // BDM_5 on tetrahedra
+constexpr int MAXW = 192;   // W_h of parallelepipeds, k = 3 (BDM_5 on tetrahedra: 168)
 constexpr int MAXF = 21;    // dim P^5 on a triangle
-constexpr int MAXI = 84;    // interior moments of BDM_5 on tetrahedra
+constexpr int MAXI = 96;    // interior moments of parallelepipeds, k = 3 (BDM_5 on tetrahedra: 84)
 constexpr int MAXL = 84;    // dim P^6 in 3D (Lagrange nodes of P^{k+1})
 constexpr int MAXN = 28;    // dim P^6 on a triangle (curved elements)
 constexpr int BLOCK = 128;
@@ -23,31 +23,48 @@ inline int grid_for(long n) { return (int)((n + BLOCK - 1) / BLOCK); }
 
 // Direction of the reference facet flux: on the simplex -grad lambda_f ((1, .., 1)
 // for f = 0, -e_{f-1} otherwise; its length carries the facet measure), on the
-// square the outward unit normal of facet f (eta = 0, xi = 1, eta = 1, xi = 0).
+// square the outward unit normal of facet f (eta = 0, xi = 1, eta = 1, xi = 0),
+// on the cube that of face f (zeta = 0, eta = 0, xi = 1, eta = 1, xi = 0, zeta = 1).
 __device__ __forceinline__ double ref_dir(const DevMesh& m, int f, int a) {
   if (m.quad) {
     const double nq[4][2] = {{0.0, -1.0}, {1.0, 0.0}, {0.0, 1.0}, {-1.0, 0.0}};
     return nq[f][a];
   }
+  if (m.hex) {
+    const double nh[6][3] = {{0, 0, -1}, {0, -1, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, 0, 1}};
+    return nh[f][a];
+  }
   return f == 0 ? 1.0 : (a == f - 1 ? -1.0 : 0.0);
 }
 
-// (-1)^j where the local facet parameter of (e, f) runs against the global one
-// (parallelograms; simplices sort their vertices and never flip)
-__device__ __forceinline__ double flip_sign(const DevMesh& m, int e, int f, int j) {
-  return (m.flip && m.flip[(long)e * 4 + f] && (j & 1)) ? -1.0 : 1.0;
+// Local facet mode j of element e's facet f against the global facet modes: returns
+// the factor and sets *jg to the global mode.  Simplices sort their vertices (identity);
+// parallelograms flip (-1)^j where the local parameter runs against the global one;
+// parallelepipeds map (alpha, beta) to (beta, alpha) when transposed, with the factor
+// (-1)^(alpha o1 + beta o2).
+__device__ __forceinline__ double facet_mode(const DevMesh& m, int e, int f, int j, int* jg) {
+  *jg = j;
+  if (m.flip) return (m.flip[(long)e * 4 + f] && (j & 1)) ? -1.0 : 1.0;
+  if (m.fcode) {
+    const int n = m.s.K + 1, al = j / n, be = j % n, c = m.fcode[(long)e * 6 + f];
+    const int o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
+    if (c & 1) *jg = be * n + al;
+    return ((al * o1 + be * o2) & 1) ? -1.0 : 1.0;
+  }
+  return 1.0;
 }
 
 __global__ void geometry_kernel(DevMesh m) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m.E) return;
   const int D = m.s.D;
-  const int* v = m.elems + (long)e * m.s.NF;
+  const int* v = m.elems + (long)e * (m.hex ? 8 : m.s.NF);   // vertices per element
   double X0[3], J[9];
   for (int a = 0; a < D; ++a) X0[a] = m.verts[(long)v[0] * D + a];
-  // simplex: J[:, c] = X_{c+1} - X_0; parallelogram: J[:, 0] = X_1 - X_0, J[:, 1] = X_3 - X_0
+  // simplex: J[:, c] = X_{c+1} - X_0; parallelogram: [X_1, X_3] - X_0; parallelepiped: [X_1, X_3, X_4] - X_0
+  const int cols[3] = {1, (m.quad || m.hex) ? 3 : 2, m.hex ? 4 : 3};
   for (int c = 0; c < D; ++c)
-    for (int r = 0; r < D; ++r) J[r * D + c] = m.verts[(long)v[m.quad && c == 1 ? 3 : c + 1] * D + r] - X0[r];
+    for (int r = 0; r < D; ++r) J[r * D + c] = m.verts[(long)v[cols[c]] * D + r] - X0[r];
   double det;
   if (D == 2) {
     det = J[0] * J[3] - J[1] * J[2];
@@ -67,7 +84,11 @@ __device__ void gather_local(const DevMesh& m, int e, const double* __restrict__
   for (int f = 0; f < s.NF; ++f) {
     const long g = m.facet_id[(long)e * s.NF + f];
     const double sf = sg * (double)m.orient[(long)e * s.NF + f];
-    for (int j = 0; j < s.NFM; ++j) ut[f * s.NFM + j] = sf * flip_sign(m, e, f, j) * u[g * s.NFM + j];
+    for (int j = 0; j < s.NFM; ++j) {
+      int jg;
+      const double fm = facet_mode(m, e, f, j, &jg);
+      ut[f * s.NFM + j] = sf * fm * u[g * s.NFM + jg];
+    }
   }
   const long base = (long)m.nF * s.NFM + (long)e * s.NINT;
   for (int j = 0; j < s.NINT; ++j) ut[s.NF * s.NFM + j] = u[base + j];
@@ -102,7 +123,7 @@ __global__ void wind_prep_kernel(DevMesh m, const double* __restrict__ u, T* __r
     for (int a = 0; a < D; ++a) {
       double acc = 0.0;
       for (int i = 0; i < N; ++i) acc += m.Bv[q * N + i] * uc[a * N + i];
-      Uw[(long)(q * D + a) * E + e] = (T)(inv * m.wv[q] * acc);
+      Uw[m.hex ? ((long)e * s.QV + q) * D + a : (long)(q * D + a) * E + e] = (T)(inv * m.wv[q] * acc);
     }
   for (int f = 0; f < s.NF; ++f)
     for (int q = 0; q < s.QF; ++q) {
@@ -114,7 +135,7 @@ __global__ void wind_prep_kernel(DevMesh m, const double* __restrict__ u, T* __r
         for (int i = 0; i < N; ++i) ua += m.Bf[(long)(f * s.QF + q) * N + i] * uc[a * N + i];
         acc += g * ua;
       }
-      Fw[(long)(f * s.QF + q) * E + e] = (T)(inv * m.wf[q] * acc);
+      Fw[m.hex ? ((long)e * s.NF + f) * s.QF + q : (long)(f * s.QF + q) * E + e] = (T)(inv * m.wf[q] * acc);
     }
 }
 
@@ -177,8 +198,9 @@ __global__ void transfer_T_kernel(DevMesh m, const double* __restrict__ f, doubl
     for (int b = 0; b < NW; ++b) z += m.Cb[(long)b * NW + j] * y[b];
     if (j < s.NF * s.NFM) {
       const int lf = j / s.NFM;
-      const double sf = sg * (double)m.orient[(long)e * s.NF + lf] * flip_sign(m, e, lf, j % s.NFM);
-      zbuf[(long)e * s.NF * s.NFM + j] = sf * z;
+      int jg;
+      const double sf = sg * (double)m.orient[(long)e * s.NF + lf] * facet_mode(m, e, lf, j % s.NFM, &jg);
+      zbuf[(long)e * s.NF * s.NFM + lf * s.NFM + jg] = sf * z;
     } else {
       g[(long)m.nF * s.NFM + (long)e * s.NINT + (j - s.NF * s.NFM)] = z;
     }
@@ -193,8 +215,9 @@ __global__ void facet_reduce_kernel(DevMesh m, const double* __restrict__ zbuf, 
   const long fg = t / NFM;
   const int j = (int)(t % NFM);
   const int s0 = m.facet_sides[2 * fg], s1 = m.facet_sides[2 * fg + 1];
-  double v = zbuf[((long)(s0 >> 2) * NF + (s0 & 3)) * NFM + j];
-  if (s1 >= 0) v += zbuf[((long)(s1 >> 2) * NF + (s1 & 3)) * NFM + j];
+  const int sh = NF > 4 ? 3 : 2, mk = (1 << sh) - 1;     // (e << sh) | f
+  double v = zbuf[((long)(s0 >> sh) * NF + (s0 & mk)) * NFM + j];
+  if (s1 >= 0) v += zbuf[((long)(s1 >> sh) * NF + (s1 & mk)) * NFM + j];
   g[t] = v;
 }
 
@@ -287,7 +310,11 @@ __global__ void wind_from_potential_kernel(DevMesh m, const double* __restrict__
       for (int j = 0; j < s.NFM; ++j) acc[j] += m.wfd[q] * flux * m.Qfd[q * s.NFM + j];
     }
     const long g = m.facet_id[(long)e * s.NF + f];
-    for (int j = 0; j < s.NFM; ++j) u[g * s.NFM + j] = sg * flip_sign(m, e, f, j) * acc[j];
+    for (int j = 0; j < s.NFM; ++j) {
+      int jg;
+      const double fm = facet_mode(m, e, f, j, &jg);
+      u[g * s.NFM + jg] = sg * fm * acc[j];
+    }
   }
   if (s.NINT) {
     double acc[MAXI];
@@ -338,7 +365,11 @@ __global__ void hdiv_interpolate_kernel(DevMesh m, const double* __restrict__ va
       for (int j = 0; j < s.NFM; ++j) acc[j] += m.wfd[q] * flux * m.Qfd[q * s.NFM + j];
     }
     const long g = m.facet_id[(long)e * s.NF + f];
-    for (int j = 0; j < s.NFM; ++j) u[g * s.NFM + j] = sg * flip_sign(m, e, f, j) * acc[j];
+    for (int j = 0; j < s.NFM; ++j) {
+      int jg;
+      const double fm = facet_mode(m, e, f, j, &jg);
+      u[g * s.NFM + jg] = sg * fm * acc[j];
+    }
   }
   if (s.NINT) {
     double acc[MAXI];

@@ -95,6 +95,15 @@ Sizes make_quad_sizes(int K);
 const Tables& quad_tables(int K);
 bool quad_supported(int K);
 
+// Parallelepipeds (uncurved hexahedra): the same fields on [0,1]^3 with
+// psi_{abc} = l_a(xi) l_b(eta) l_c(zeta), i = (a (k+1) + b)(k+1) + c, six faces
+// (zeta = 0, eta = 0, xi = 1, eta = 1, xi = 0, zeta = 1), face modes
+// l_alpha(s1) l_beta(s2), j = alpha (k+1) + beta, in the local face parameter
+// (the tangential reference coordinates in increasing axis order).
+Sizes make_hex_sizes(int K);
+const Tables& hex_tables(int K);
+bool hex_supported(int K);
+
 // Facet connectivity of a conforming simplicial mesh (elements' vertex ids
 // sorted in place).  Returns an empty string on success, else the reason.
 struct Connectivity {
@@ -114,5 +123,18 @@ std::string build_connectivity(int D, int n_vert, int n_elem, std::vector<int>& 
 constexpr int kQuadFacet[4][2] = {{0, 1}, {1, 2}, {3, 2}, {0, 3}};
 std::string build_quad_connectivity(int n_vert, int n_elem, const std::vector<int>& elems, Connectivity& out,
                                     std::vector<signed char>& flip, std::vector<int>& qnbr);
+
+// Face connectivity of a conforming parallelepiped mesh, local vertex order
+// (0,0,0), (1,0,0), (1,1,0), (0,1,0), (0,0,1), (1,0,1), (1,1,1), (0,1,1) (kept).
+// kHexFace[f] = local vertices at the face corners (s1, s2) = (0,0), (1,0),
+// (0,1), (1,1).  fcode[e][f] = T | o1 << 1 | o2 << 2 relates the local face
+// parameter to the global one (origin at the lowest global vertex id, s1
+// towards the lower-id of its two face neighbours): (o1, o2) is the local corner
+// of the origin and T = 1 when the global s1 runs along the local s2.
+// qnbr[e][f] = (e' << 3) | f', -1 on the boundary.  Faces are numbered by their
+// sorted vertex quadruples; the lower-index element owns a face.
+constexpr int kHexFace[6][4] = {{0, 1, 3, 2}, {0, 1, 4, 5}, {1, 2, 5, 6}, {3, 2, 7, 6}, {0, 3, 4, 7}, {4, 5, 7, 6}};
+std::string build_hex_connectivity(int n_vert, int n_elem, const std::vector<int>& elems, Connectivity& out,
+                                   std::vector<signed char>& fcode, std::vector<int>& qnbr);
 
 }  // namespace dgc

@@ -40,6 +40,9 @@ struct DevMesh {
   // parallelograms: element type and the facet-parameter flips [E][4]
   int quad = 0;
   const signed char* flip = nullptr;
+  // parallelepipeds: element type and the face codes [E][6] (T | o1 << 1 | o2 << 2)
+  int hex = 0;
+  const signed char* fcode = nullptr;
   // curved (quadratic) triangles: Ec of them, celem [Ec] their element ids, cid [E]
   // the curved index of an element or -1, cnodes [Ec][6][2] their P2 nodes, the P2
   // reference gradients at the interior rule (p2d [QD][6][2]) and at the volume rule
@@ -60,6 +63,9 @@ cudaError_t launch_stage_3d(int K, bool fp32, const StageArgs* a, cudaStream_t s
 // parallelograms, sum-factorised; a->nbr holds the (e' << 3) | (rev << 2) | f' codes
 // and a->tab the 1D tables [l at the Gauss points | l' there | l(0), l(1)]
 cudaError_t launch_stage_quad(int K, bool fp32, const StageArgs* a, cudaStream_t s);
+// parallelepipeds, one block per element; a->nbr holds (e' << 3) | f', the frozen wind
+// is element-major (Uw [E][QV][3], Fw [E][6][QF]), fcode the face codes [E][6]
+cudaError_t launch_stage_hex(int K, bool fp32, const StageArgs* a, const signed char* fcode, cudaStream_t s);
 // copy the order-K 1D tables [l at the Gauss points | l' there | l(0), l(1)] into the
 // kernel's constant-memory slot (synchronous; call before any stream capture)
 cudaError_t quad_tables_to_constant(int K, const std::vector<double>& tab);

@@ -28,6 +28,8 @@ SIGNATURES = {
                              ctypes.POINTER(ctypes.c_void_p)],
     "dgc_mesh_upload_curved": [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
                                ctypes.POINTER(ctypes.c_void_p)],
+    "dgc_mesh_upload_hex": [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp,
+                            ctypes.POINTER(ctypes.c_void_p)],
     "dgc_mesh_free": [_vp],
     "dgc_sizes": [_vp, _i64p, _i64p],
     "dgc_mesh_info": [_vp, _i64p],
@@ -115,7 +117,8 @@ def _stream(stream):
 
 class Mesh:
     """A dgc_mesh handle, order k, device geometry: affine simplices (``shape="simplex"``,
-    elems [E][dim+1]), parallelograms (``shape="quad"``, dim 2, elems [E][4] in cyclic order) or
+    elems [E][dim+1]), parallelograms (``shape="quad"``, dim 2, elems [E][4] in cyclic order),
+    parallelepipeds (``shape="hex"``, dim 3, elems [E][8] in the reference-cube order) or
     quadratic triangles (``shape="curved"``, dim 2, plus ``edge_nodes`` [n_facets][2])."""
 
     def __init__(self, dim: int, k: int, verts, elems, stream=None, shape: str = "simplex", edge_nodes=None):
@@ -129,6 +132,12 @@ class Mesh:
             check(lib().dgc_mesh_upload_quad(k, verts.shape[0], verts.ctypes.data_as(ctypes.c_void_p),
                                              elems.shape[0], elems.ctypes.data_as(ctypes.c_void_p),
                                              _stream(stream), ctypes.byref(h)))
+        elif shape == "hex":
+            if dim != 3:
+                raise ValueError("parallelepiped meshes are three-dimensional")
+            check(lib().dgc_mesh_upload_hex(k, verts.shape[0], verts.ctypes.data_as(ctypes.c_void_p),
+                                            elems.shape[0], elems.ctypes.data_as(ctypes.c_void_p),
+                                            _stream(stream), ctypes.byref(h)))
         elif shape == "curved":
             if dim != 2 or edge_nodes is None:
                 raise ValueError("curved meshes are two-dimensional and need edge_nodes [n_facets, 2]")
