@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-shapes", action="store_true",
                     help="skip the parallelogram and curved-triangle sections")
     args = ap.parse_args()
-    if W.WORKLOADS[args.workload].shape != "simplex" and args.prec in TC_PRECS:
+    if args.impl == "dgconv" and W.WORKLOADS[args.workload].shape != "simplex" and args.prec in TC_PRECS:
         ap.error("the tensor-core precisions cover affine triangles; use --prec fp32 or fp64 on other shapes")
     return args
 
@@ -188,6 +188,16 @@ def stage_bytes_flops(wl):
         fma_c = m * (3 * n * n + m * (3 * n + 2)) + 4 * (3 * n * n + m * (3 * n + 1))
         byts = 3 * N * d * 8 + d * N * 8 + (d * d + 1) * 8 + 4 * 4
         return byts, 2 * d * fma_c, N
+    if wl.shape == "hex":
+        # parallelepipeds, sum-factorised per component: three contractions to the m^3
+        # points, the wind products, three back; per face the two traces (own and
+        # neighbour), values at the m^2 points, projection back and the scatter
+        n, m = k + 1, (3 * k) // 2 + 1
+        N = n ** 3
+        vol = m * n ** 3 + m * m * n * n + m ** 3 * n + 3 * m ** 3 + 3 * m ** 3 * n + 3 * m * m * n * n + 2 * m * n ** 3
+        face = 3 * n ** 3 + 3 * m * n * n + 3 * m * m * n
+        byts = 3 * N * d * 8 + d * N * 8 + (d * d + 1) * 8 + 6 * 4
+        return byts, 2 * d * (vol + 6 * face), N
     N = math.comb(k + d, d)
     nq = (3 * k - 1) // 2 + 1
     nf = (3 * k) // 2 + 1
@@ -332,7 +342,7 @@ def measure_shape(torch, dgconv, name: str, rank: int, world: int, flush, stream
     wl = rank_workload(W.WORKLOADS[name], rank)
     mesh, wind, u_n, ds = make_inputs(wl, torch, dgconv)
     v, mv, g = mesh.dg_zeros(), mesh.dg_zeros(), mesh.hdiv_zeros()
-    kernel = "stage_quad_kernel" if wl.shape == "quad" else "stage_kernel"
+    kernel = {"quad": "stage_quad_kernel", "hex": "stage_hex_kernel"}.get(wl.shape, "stage_kernel")
     byts, flops, N = stage_bytes_flops(wl)
     curved_frac = mesh.n_curved / wl.n_elem if wl.shape == "curved" else None
     if curved_frac:
@@ -424,6 +434,15 @@ def _oracle_setup(wl):
         wind = OQ.wind_from_potential(om, wl.k, wl.potential()(X[:, 0], X[:, 1]).reshape(om.n_elem, -1))
         v = OQ.transfer(om, wl.k, OQ.dofs_of_function(om, wl.k, lambda x: field(x)))
         return om, wind, v, OQ.cfl_ds(om, wl.k, wind, wl.cfl), (wl.k + 1) ** 2
+    if wl.shape == "hex":
+        from oracle import hexa as OX
+        om = OX.HexMesh(verts, elems)
+        nodes = OX.lagrange_nodes(wl.k)
+        X = om.to_physical(np.repeat(np.arange(om.n_elem), nodes.shape[0]), np.tile(nodes, (om.n_elem, 1)))
+        pot = np.moveaxis(np.asarray(wl.potential()(X[:, 0], X[:, 1], X[:, 2])), 0, -1).reshape(om.n_elem, -1, 3)
+        wind = OX.wind_from_potential(om, wl.k, pot)
+        v = OX.transfer(om, wl.k, OX.dofs_of_function(om, wl.k, lambda x: field(x)))
+        return om, wind, v, OX.cfl_ds(om, wl.k, wind, wl.cfl), (wl.k + 1) ** 3
     om = OM.Mesh(verts, elems)
     wind = OH.wind_from_potential(om, wl.k, wl.potential())
     if wl.unit_peak_speed:
@@ -441,6 +460,9 @@ def _oracle_block(wl_name, lo, hi, wind, v, ds, warm, steps, barrier, queue):
     if wl.shape == "quad":
         from oracle import quad as OQ
         op = OQ.QuadConvectionOracle(OQ.QuadMesh(verts, elems), wl.k, wind, sel=sel)
+    elif wl.shape == "hex":
+        from oracle import hexa as OX
+        op = OX.HexConvectionOracle(OX.HexMesh(verts, elems), wl.k, wind, sel=sel)
     else:
         from oracle import dg as ODG
         from oracle import mesh as OM
@@ -465,7 +487,7 @@ class OracleTimer:
 
     def __init__(self, wl):
         if wl.shape == "curved":
-            raise ValueError("the timed oracle covers affine simplices and parallelograms")
+            raise ValueError("the timed oracle covers affine simplices, parallelograms and parallelepipeds")
         self.wl = wl
         om, self.wind, self.v, self.ds, N = _oracle_setup(wl)
         self.E = om.n_elem
@@ -643,7 +665,7 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": ncu_traffic(wl, args.prec), "peak_source": hbm_src,
             "kernel": ("stage_tc_kernel" if args.prec in TC_PRECS
-                       else "stage_quad_kernel" if wl.shape == "quad" else "stage_kernel"),
+                       else {"quad": "stage_quad_kernel", "hex": "stage_hex_kernel"}.get(wl.shape, "stage_kernel")),
             "stage_ms": stage_ms, "alg_bytes_per_elem_stage": byts, "alg_flops_per_elem_stage": flops,
             "achieved_tflops": flops * wl.n_elem / (stage_ms * 1e-3) / 1e12}
     line = {
@@ -735,6 +757,7 @@ def main():
     if not args.no_shapes and wl.shape == "simplex":
         line["parallelogram"] = measure_shape(torch, dgconv, "parallelogram256_k4", rank, world, flush, stream)
         line["curved"] = measure_shape(torch, dgconv, "curved256_k4", rank, world, flush, stream)
+        line["parallelepiped"] = measure_shape(torch, dgconv, "parallelepiped32_k3", rank, world, flush, stream)
     # clocks sampled from before the first timed step to the end of the GPU measurements
     line["clocks"] = clocks.stop()
     if rank == 0 and world == 1 and not args.no_cpu_baseline and wl.shape != "curved":

@@ -347,18 +347,22 @@ class Workload:
     substeps: int
     cfl: float = 0.2
     unit_peak_speed: bool = False
-    shape: str = "simplex"    # "simplex" | "quad" (parallelograms) | "curved" (quadratic triangles), dim 2
+    shape: str = "simplex"    # "simplex" | "quad" (parallelograms) | "curved" (quadratic triangles) | "hex"
 
     @property
     def n_elem(self) -> int:
         if self.shape == "quad":
             return self.n * self.n
+        if self.shape == "hex":
+            return self.n ** 3
         return (2 if self.dim == 2 else 6) * self.n ** self.dim
 
     def mesh(self):
         """(verts, elems), or (verts, elems, edge_nodes) for curved meshes."""
         if self.shape == "quad":
             return parallelogram_mesh(self.n, self.seed)
+        if self.shape == "hex":
+            return parallelepiped_mesh(self.n, self.seed)
         if self.shape == "curved":
             return curved_square_mesh(self.n, self.jitter, self.seed)
         if self.dim == 2:
@@ -382,6 +386,9 @@ WORKLOADS = {
                                     shape="quad"),
     # quadratic triangles, edges inside a disk of radius 0.3 curved (about 28% of the elements)
     "curved256_k4": Workload("curved256_k4", 2, 256, 4, 0.10, 7, "random", "wind", 3, 100, shape="curved"),
+    # parallelepipeds: 32^3 cells of varying size and shear (6.3M DOFs at k = 3)
+    "parallelepiped32_k3": Workload("parallelepiped32_k3", 3, 32, 3, 0.0, 8, "random", "fourier", 3, 50,
+                                    shape="hex"),
 }
 
 
