@@ -120,6 +120,7 @@ struct dgc_mesh {
   int quad = 0;                    // 1: parallelograms (dgc_mesh_upload_quad)
   int hex = 0;                     // 1: parallelepipeds (dgc_mesh_upload_hex)
   DevBuf<signed char> fcode;       // [E][6] face codes of a parallelepiped mesh
+  DevBuf<float> q32[3];            // FP32 copies of v, v1, v2 in an FP32 parallelogram RK sequence
   DevBuf<signed char> flip;        // [E][4] facet-parameter flips of a parallelogram mesh
   DevBuf<int> qnbr;                // [E][4] neighbour codes of the parallelogram stage kernel
   // curved (quadratic) triangles, dgc_mesh_upload_curved
@@ -223,6 +224,7 @@ struct dgc_mesh {
     orient.release();
     flip.release();
     fcode.release();
+    for (auto& b : q32) b.release();
     qnbr.release();
     for (auto* b : {&celem, &cid}) b->release();
     for (auto* b : {&cnodes, &p2d, &p2v, &Minv64}) b->release();
@@ -303,7 +305,8 @@ dgc_status ensure_wind_scratch(dgc_mesh* m, bool fp32) {
 }
 
 dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double* vn, double* vout,
-                        double alpha, double beta, double gamma, cudaStream_t st) {
+                        double alpha, double beta, double gamma, cudaStream_t st, const float* vin32 = nullptr,
+                        float* vout32 = nullptr) {
   if (injected("launch")) return fail(DGC_ERR_CUDA, "stage kernel launch failed (injected)");
   dgc::StageArgs a;
   a.vin = vin;
@@ -317,6 +320,8 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
   a.alpha = alpha;
   a.beta = beta;
   a.gamma = gamma;
+  a.vin32 = vin32;
+  a.vout32 = vout32;
   if (m->Ec > 0) {
     a.cid = m->cid.ptr;
     a.Minv = fp32 ? (const void*)m->Minv32.ptr : (const void*)m->Minv64.ptr;
@@ -489,8 +494,8 @@ dgc_status rk_sequence_tc(dgc_mesh* m, dgc_prec prec, double* v, double ds, int 
 
 // one stage vout = alpha vn + beta vin + gamma L(vin), any precision
 dgc_status stage(dgc_mesh* m, dgc_prec prec, const double* vin, const double* vn, double* vout, double alpha,
-                 double beta, double gamma, cudaStream_t st) {
-  return launch_stage(m, prec == DGC_FP32, vin, vn, vout, alpha, beta, gamma, st);
+                 double beta, double gamma, cudaStream_t st, const float* vin32 = nullptr, float* vout32 = nullptr) {
+  return launch_stage(m, prec == DGC_FP32, vin, vn, vout, alpha, beta, gamma, st, vin32, vout32);
 }
 
 // frozen-wind data for the chosen precision
@@ -509,6 +514,8 @@ dgc_status prepare_wind(dgc_mesh* m, dgc_prec prec, const double* wind, cudaStre
 
 dgc_status ensure_prec_scratch(dgc_mesh* m, dgc_prec prec) {
   if (is_tc(prec)) return ensure_tc_scratch(m);
+  if (m->quad && prec == DGC_FP32)
+    for (auto& b : m->q32) DGC_CUDA(b.alloc((size_t)m->E * m->s.D * m->s.N));
   return ensure_wind_scratch(m, prec == DGC_FP32);
 }
 
@@ -525,18 +532,24 @@ dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, in
   if (is_tc(prec)) return rk_sequence_tc(m, prec, v, ds, nsteps, scheme, wp, st);
   double* v1 = m->stage1.ptr;
   double* v2 = m->stage2.ptr;
+  // FP32 parallelograms carry FP32 copies of v, v1, v2 from stage to stage
+  const bool mirror = m->quad && prec == DGC_FP32 && nsteps > 0;
+  float* f0 = mirror ? m->q32[0].ptr : nullptr;
+  float* f1 = mirror ? m->q32[1].ptr : nullptr;
+  float* f2 = mirror ? m->q32[2].ptr : nullptr;
+  if (mirror) DGC_CUDA(dgc::launch_to_float(v, f0, (long)m->E * m->s.D * m->s.N, st));
   for (int n = 0; n < nsteps; ++n) {
     dgc_status rc;
     if ((rc = substep_wind(m, prec, wp, ds, n, st))) return rc;
     if (scheme == DGC_SSPRK2) {
       // v1 = v + ds L(v);  v = 1/2 v + 1/2 (v1 + ds L(v1))
-      if ((rc = stage(m, prec, v, nullptr, v1, 0.0, 1.0, ds, st))) return rc;
-      if ((rc = stage(m, prec, v1, v, v, 0.5, 0.5, 0.5 * ds, st))) return rc;
+      if ((rc = stage(m, prec, v, nullptr, v1, 0.0, 1.0, ds, st, f0, f1))) return rc;
+      if ((rc = stage(m, prec, v1, v, v, 0.5, 0.5, 0.5 * ds, st, f1, f0))) return rc;
     } else {
       // Shu-Osher SSP-RK3
-      if ((rc = stage(m, prec, v, nullptr, v1, 0.0, 1.0, ds, st))) return rc;
-      if ((rc = stage(m, prec, v1, v, v2, 0.75, 0.25, 0.25 * ds, st))) return rc;
-      if ((rc = stage(m, prec, v2, v, v, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * ds, st))) return rc;
+      if ((rc = stage(m, prec, v, nullptr, v1, 0.0, 1.0, ds, st, f0, f1))) return rc;
+      if ((rc = stage(m, prec, v1, v, v2, 0.75, 0.25, 0.25 * ds, st, f1, f2))) return rc;
+      if ((rc = stage(m, prec, v2, v, v, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * ds, st, f2, f0))) return rc;
     }
   }
   return DGC_OK;

@@ -114,6 +114,8 @@ struct CombineArgs {
   int nterms;
 };
 cudaError_t launch_combine(double* out, const CombineArgs& a, long n, cudaStream_t s);
+// y = (float) x over n values
+cudaError_t launch_to_float(const double* x, float* y, long n, cudaStream_t s);
 
 // pseudo-time (Richardson) solve: residual + deterministic norm partials, update, control
 int rich_blocks(long n);

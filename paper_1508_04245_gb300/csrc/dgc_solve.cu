@@ -97,7 +97,18 @@ __global__ void __launch_bounds__(kBlock) combine_kernel(double* out, CombineArg
   }
 }
 
+__global__ void __launch_bounds__(kBlock) to_float_kernel(const double* __restrict__ x, float* __restrict__ y, long n) {
+  for (long j = (long)blockIdx.x * kBlock + threadIdx.x; j < n; j += (long)gridDim.x * kBlock) y[j] = (float)x[j];
+}
+
 }  // namespace
+
+cudaError_t launch_to_float(const double* x, float* y, long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long b = (n + kBlock - 1) / kBlock;
+  to_float_kernel<<<(unsigned)(b > 4096 ? 4096 : b), kBlock, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_combine(double* out, const CombineArgs& a, long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

@@ -46,6 +46,11 @@ struct StageArgs {
   const int* cid = nullptr;
   const void* Minv = nullptr;
   int Ec = 0;
+  // FP32 contraction of parallelograms inside an RK sequence: an FP32 copy of vin
+  // (read instead of converting vin and the neighbours' coefficients) and the FP32
+  // copy of vout to write; null outside such a sequence
+  const float* vin32 = nullptr;
+  float* vout32 = nullptr;
 };
 
 // Rows padded to multiples of 4 values (zero filled) so the kernel reads them in

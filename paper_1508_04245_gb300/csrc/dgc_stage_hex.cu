@@ -1,6 +1,7 @@
 // Fused RK stage kernel for parallelepipeds with sum-factorised contractions:
-// steps a3-a7 of the explicit upwind-DG convection step on [Q^k]^3, one thread
-// block per element, the three velocity components one after the other.
+// steps a3-a7 of the explicit upwind-DG convection step on [Q^k]^3, one warp per
+// element (four elements per block, warp-level synchronisation only), the three
+// velocity components one after the other.
 //
 // On the reference cube (contravariant Piola, as for simplices and
 // parallelograms) the operator of Sec. 2.3 divided by the mass |det J| is
@@ -31,13 +32,21 @@ namespace {
 __device__ __forceinline__ int face_axis(int f) { return (f == 2 || f == 4) ? 0 : (f == 1 || f == 3) ? 1 : 2; }
 __device__ __forceinline__ int face_side(int f) { return (f == 2 || f == 3 || f == 5) ? 1 : 0; }
 
+constexpr int kHexWarps = 4;   // elements (warps) per block
+
 template <int K, typename T>
-__global__ void __launch_bounds__(128) stage_hex_kernel(StageArgs a, const signed char* __restrict__ fcode) {
+struct HexScratch {                  // one element's working set in shared memory
+  static constexpr int n = K + 1, N = n * n * n, m = (3 * K) / 2 + 1, QV = m * m * m, QF = m * m, NFM = n * n;
+  T w[N], r[3 * N];
+  T t1[m * n * n], t2[m * m * n], F[3][QV], G[3][m * m * n], H[2][m * n * n];
+  T to[NFM], tn[NFM], vo[m * n], vn[m * n], P[QF], Qb[m * n];
+};
+
+template <int K, typename T>
+__global__ void __launch_bounds__(32 * kHexWarps) stage_hex_kernel(StageArgs a, const signed char* __restrict__ fcode) {
   constexpr int n = K + 1, N = n * n * n, m = (3 * K) / 2 + 1, QV = m * m * m, QF = m * m, NFM = n * n;
   __shared__ T L[m * n], Dl[m * n], Eb[2 * n];
-  __shared__ T w[N], r[3 * N];
-  __shared__ T t1[m * n * n], t2[m * m * n], F[3][QV], G[3][m * m * n], H[2][m * n * n];
-  __shared__ T to[NFM], tn[NFM], vo[m * n], vn[m * n], P[QF], Qb[m * n];
+  __shared__ HexScratch<K, T> scr[kHexWarps];
   const T* gtab = static_cast<const T*>(a.tab);
   for (int j = threadIdx.x; j < 2 * m * n + 2 * n; j += blockDim.x) {
     const T v = gtab[j];
@@ -48,17 +57,34 @@ __global__ void __launch_bounds__(128) stage_hex_kernel(StageArgs a, const signe
     else
       Eb[j - 2 * m * n] = v;
   }
-  const int e = blockIdx.x;
+  __syncthreads();
+  const int wid = threadIdx.x >> 5;
+  const int e = blockIdx.x * kHexWarps + wid;
+  if (e >= a.E) return;                                  // whole warps leave; no block barrier follows
   const long E = a.E;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x & 31, nt = 32;
+  HexScratch<K, T>& S = scr[wid];
+  T* w = S.w;
+  T* r = S.r;
+  T* t1 = S.t1;
+  T* t2 = S.t2;
+  T(*F)[QV] = S.F;
+  T(*G)[m * m * n] = S.G;
+  T(*H)[m * n * n] = S.H;
+  T* to = S.to;
+  T* tn = S.tn;
+  T* vo = S.vo;
+  T* vn = S.vn;
+  T* P = S.P;
+  T* Qb = S.Qb;
   const T* __restrict__ Uw = static_cast<const T*>(a.Uw) + (long)e * QV * 3;
   const T* __restrict__ Fw = static_cast<const T*>(a.Fw) + (long)e * 6 * QF;
   const double* __restrict__ vin_e = a.vin + (long)e * 3 * N;
 
   for (int c = 0; c < 3; ++c) {
-    __syncthreads();
+    __syncwarp();
     for (int j = tid; j < N; j += nt) w[j] = (T)vin_e[c * N + j];
-    __syncthreads();
+    __syncwarp();
     // ---- volume: to the points ------------------------------------------------------
     for (int o = tid; o < m * n * n; o += nt) {        // t1[p][b][cc] = sum_a l_a(g_p) w[a][b][cc]
       const int p = o / (n * n), bc = o % (n * n);
@@ -66,21 +92,21 @@ __global__ void __launch_bounds__(128) stage_hex_kernel(StageArgs a, const signe
       for (int aa = 0; aa < n; ++aa) acc += L[p * n + aa] * w[aa * n * n + bc];
       t1[o] = acc;
     }
-    __syncthreads();
+    __syncwarp();
     for (int o = tid; o < m * m * n; o += nt) {        // t2[p][q][cc] = sum_b l_b(g_q) t1[p][b][cc]
       const int p = o / (m * n), q = (o / n) % m, cc = o % n;
       T acc = (T)0;
       for (int b = 0; b < n; ++b) acc += L[q * n + b] * t1[(p * n + b) * n + cc];
       t2[o] = acc;
     }
-    __syncthreads();
+    __syncwarp();
     for (int o = tid; o < QV; o += nt) {               // W at (p, q, s), times the wind
       const int pq = o / m, s = o % m;
       T W = (T)0;
       for (int cc = 0; cc < n; ++cc) W += L[s * n + cc] * t2[pq * n + cc];
       for (int d = 0; d < 3; ++d) F[d][o] = Uw[(long)o * 3 + d] * W;
     }
-    __syncthreads();
+    __syncwarp();
     // ---- volume: back to the modes ---------------------------------------------------
     for (int o = tid; o < m * m * n; o += nt) {        // last direction: l_c, l_c, l_c'
       const int pq = o / n, cc = o % n;
@@ -94,7 +120,7 @@ __global__ void __launch_bounds__(128) stage_hex_kernel(StageArgs a, const signe
       G[1][o] = g1;
       G[2][o] = g2;
     }
-    __syncthreads();
+    __syncwarp();
     for (int o = tid; o < m * n * n; o += nt) {        // middle direction: l_b, l_b' (+) l_b
       const int p = o / (n * n), b = (o / n) % n, cc = o % n;
       T h0 = (T)0, h1 = (T)0;
@@ -106,7 +132,7 @@ __global__ void __launch_bounds__(128) stage_hex_kernel(StageArgs a, const signe
       H[0][o] = h0;
       H[1][o] = h1;
     }
-    __syncthreads();
+    __syncwarp();
     for (int o = tid; o < N; o += nt) {                // first direction: l_a', l_a
       const int aa = o / (n * n), bc = o % (n * n);
       T acc = (T)0;
@@ -119,7 +145,7 @@ __global__ void __launch_bounds__(128) stage_hex_kernel(StageArgs a, const signe
       const int ta = ax == 0 ? 1 : 0, tb = ax == 2 ? 1 : 2;     // tangential axes, increasing
       const T* Es = Eb + face_side(f) * n;
       const int code = a.nbr[(long)e * 6 + f];
-      __syncthreads();
+      __syncwarp();
       for (int j = tid; j < NFM; j += nt) {            // own modal trace, and the neighbour's
         const int al = j / n, be = j % n;
         int deg[3];
@@ -157,7 +183,7 @@ __global__ void __launch_bounds__(128) stage_hex_kernel(StageArgs a, const signe
         }
         tn[j] = nbv;
       }
-      __syncthreads();
+      __syncwarp();
       for (int o = tid; o < m * n; o += nt) {          // first face direction to the points
         const int pa = o / n, be = o % n;
         T x0 = (T)0, x1 = (T)0;
@@ -168,7 +194,7 @@ __global__ void __launch_bounds__(128) stage_hex_kernel(StageArgs a, const signe
         vo[o] = x0;
         vn[o] = x1;
       }
-      __syncthreads();
+      __syncwarp();
       for (int o = tid; o < QF; o += nt) {             // values, upwind flux
         const int pa = o / m, pb = o % m;
         T x0 = (T)0, x1 = (T)0;
@@ -179,14 +205,14 @@ __global__ void __launch_bounds__(128) stage_hex_kernel(StageArgs a, const signe
         const T fw = Fw[f * QF + o];
         P[o] = fw * (fw >= (T)0 ? x0 : (code >= 0 ? x1 : (T)0));
       }
-      __syncthreads();
+      __syncwarp();
       for (int o = tid; o < m * n; o += nt) {          // back: second face direction
         const int pa = o / n, be = o % n;
         T acc = (T)0;
         for (int pb = 0; pb < m; ++pb) acc += P[pa * m + pb] * L[pb * n + be];
         Qb[o] = acc;
       }
-      __syncthreads();
+      __syncwarp();
       for (int o = tid; o < NFM; o += nt) {            // first face direction, into r
         const int al = o / n, be = o % n;
         T acc = (T)0;
@@ -201,7 +227,7 @@ __global__ void __launch_bounds__(128) stage_hex_kernel(StageArgs a, const signe
       }
     }
   }
-  __syncthreads();
+  __syncwarp();
   // ---- epilogue: RK stage combination in FP64 -----------------------------------------
   double* vout_e = a.vout + (long)e * 3 * N;
   const double* vn_e = a.vn ? a.vn + (long)e * 3 * N : nullptr;
@@ -217,7 +243,7 @@ template <int K, typename T>
 cudaError_t launch_hex_t(const StageArgs* ap, const signed char* fcode, cudaStream_t stream) {
   if (!ap) return cudaSuccess;
   if (ap->E == 0) return cudaSuccess;
-  stage_hex_kernel<K, T><<<ap->E, 128, 0, stream>>>(*ap, fcode);
+  stage_hex_kernel<K, T><<<(ap->E + kHexWarps - 1) / kHexWarps, 32 * kHexWarps, 0, stream>>>(*ap, fcode);
   return cudaGetLastError();
 }
 

@@ -74,10 +74,14 @@ __global__ void __launch_bounds__(128) stage_quad_kernel(StageArgs a) {
   const T* __restrict__ Uw = static_cast<const T*>(a.Uw);
   const T* __restrict__ Fw = static_cast<const T*>(a.Fw);
 
+  // FP32 inside an RK sequence: the FP32 copy of the stage input, so that neither
+  // the own nor the neighbours' coefficients go through FP64 -> FP32 conversions
+  // (they run on the FP64 pipe, 1/64 of the FP32 rate on this part)
+  const float* __restrict__ v32 = sizeof(T) == 4 ? a.vin32 : nullptr;
   T w[N], r[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    w[i] = (T)vin_e[i];
+    w[i] = v32 ? (T)v32[((long)e * 2 + c) * N + i] : (T)vin_e[i];
     r[i] = (T)0;
   }
 
@@ -146,7 +150,10 @@ __global__ void __launch_bounds__(128) stage_quad_kernel(StageArgs a) {
       for (int j = 0; j < n; ++j) {
         T acc = (T)0;
 #pragma unroll
-        for (int l = 0; l < n; ++l) acc += (T)(nxi ? wn[j * n + l] : wn[l * n + j]) * qtab<K, T>(oEn + l);
+        for (int l = 0; l < n; ++l) {
+          const int i2 = nxi ? j * n + l : l * n + j;
+          acc += (v32 ? (T)v32[((long)ne * 2 + c) * N + i2] : (T)wn[i2]) * qtab<K, T>(oEn + l);
+        }
         tn[j] = (rev && (j & 1)) ? -acc : acc;
       }
     }
@@ -178,10 +185,12 @@ __global__ void __launch_bounds__(128) stage_quad_kernel(StageArgs a) {
   double* vout_e = a.vout + ((long)e * 2 + c) * N;
   const double* vn_e = a.vn ? a.vn + ((long)e * 2 + c) * N : nullptr;
 #pragma unroll
+  float* out32 = a.vout32 ? a.vout32 + ((long)e * 2 + c) * N : nullptr;
   for (int i = 0; i < N; ++i) {
     double x = a.beta * vin_e[i] - a.gamma * (double)r[i];
     if (vn_e) x += a.alpha * vn_e[i];
     vout_e[i] = x;
+    if (out32) out32[i] = (float)x;
   }
 }
 
