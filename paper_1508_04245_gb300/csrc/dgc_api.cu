@@ -120,7 +120,7 @@ struct dgc_mesh {
   int quad = 0;                    // 1: parallelograms (dgc_mesh_upload_quad)
   int hex = 0;                     // 1: parallelepipeds (dgc_mesh_upload_hex)
   DevBuf<signed char> fcode;       // [E][6] face codes of a parallelepiped mesh
-  DevBuf<float> q32[3];            // FP32 copies of v, v1, v2 in an FP32 parallelogram RK sequence
+  DevBuf<float> q32[3];            // FP32 copies of v, v1, v2 in an FP32 RK sequence
   DevBuf<signed char> flip;        // [E][4] facet-parameter flips of a parallelogram mesh
   DevBuf<int> qnbr;                // [E][4] neighbour codes of the parallelogram stage kernel
   // curved (quadratic) triangles, dgc_mesh_upload_curved
@@ -514,7 +514,7 @@ dgc_status prepare_wind(dgc_mesh* m, dgc_prec prec, const double* wind, cudaStre
 
 dgc_status ensure_prec_scratch(dgc_mesh* m, dgc_prec prec) {
   if (is_tc(prec)) return ensure_tc_scratch(m);
-  if (m->quad && prec == DGC_FP32)
+  if (prec == DGC_FP32 && !m->hex)
     for (auto& b : m->q32) DGC_CUDA(b.alloc((size_t)m->E * m->s.D * m->s.N));
   return ensure_wind_scratch(m, prec == DGC_FP32);
 }
@@ -532,8 +532,9 @@ dgc_status rk_sequence(dgc_mesh* m, const double* wind, double* v, double ds, in
   if (is_tc(prec)) return rk_sequence_tc(m, prec, v, ds, nsteps, scheme, wp, st);
   double* v1 = m->stage1.ptr;
   double* v2 = m->stage2.ptr;
-  // FP32 parallelograms carry FP32 copies of v, v1, v2 from stage to stage
-  const bool mirror = m->quad && prec == DGC_FP32 && nsteps > 0;
+  // FP32 contractions (simplices, curved triangles, parallelograms) carry FP32 copies
+  // of v, v1, v2 from stage to stage
+  const bool mirror = prec == DGC_FP32 && !m->hex && nsteps > 0;
   float* f0 = mirror ? m->q32[0].ptr : nullptr;
   float* f1 = mirror ? m->q32[1].ptr : nullptr;
   float* f2 = mirror ? m->q32[2].ptr : nullptr;

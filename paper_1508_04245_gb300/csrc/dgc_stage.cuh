@@ -134,12 +134,16 @@ __global__ void __launch_bounds__(256, 1) stage_kernel(StageArgs a) {
   const T* __restrict__ Uw = static_cast<const T*>(a.Uw);
   const T* __restrict__ Fw = static_cast<const T*>(a.Fw);
 
+  // FP32 inside an RK sequence: the FP32 copy of the stage input, so that neither the
+  // own nor the neighbours' coefficients go through FP64 -> FP32 conversions (those
+  // run on the FP64 pipe, 1/64 of the FP32 rate on this part)
+  const float* __restrict__ v32 = sizeof(T) == 4 ? a.vin32 : nullptr;
   T w[CPT][N], r[CPT][N];
 #pragma unroll
   for (int c = 0; c < CPT; ++c)
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      w[c][i] = (T)vin_e[c * N + i];
+      w[c][i] = v32 ? (T)v32[((long)e * D + c0 + c) * N + i] : (T)vin_e[c * N + i];
       r[c][i] = (T)0;
     }
 
@@ -240,12 +244,13 @@ __global__ void __launch_bounds__(256, 1) stage_kernel(StageArgs a) {
       const int ne = code >> 2, fn = code & 3;
       const T* En = Ef + fn * NFM * NP4;
       const double* __restrict__ wn = a.vin + ((long)ne * D + c0) * N;
+      const float* __restrict__ wn32 = v32 ? v32 + ((long)ne * D + c0) * N : nullptr;
       if constexpr (!VEC) {
 #pragma unroll
         for (int i = 0; i < N; ++i)
 #pragma unroll
           for (int c = 0; c < CPT; ++c) {
-            const T x = (T)wn[c * N + i];
+            const T x = wn32 ? (T)wn32[c * N + i] : (T)wn[c * N + i];
 #pragma unroll
             for (int m = 0; m < NFM; ++m) tn[c][m] += En[m * NP4 + i] * x;
           }
@@ -256,7 +261,10 @@ __global__ void __launch_bounds__(256, 1) stage_kernel(StageArgs a) {
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
 #pragma unroll
-          for (int u = 0; u < 4; ++u) x[c][u] = i4 + u < N ? (T)wn[c * N + (i4 + u < N ? i4 + u : 0)] : (T)0;
+          for (int u = 0; u < 4; ++u) {
+            const int i = i4 + u < N ? i4 + u : 0;
+            x[c][u] = i4 + u < N ? (wn32 ? (T)wn32[c * N + i] : (T)wn[c * N + i]) : (T)0;
+          }
 #pragma unroll
         for (int m = 0; m < NFM; ++m) {
           T ev[4];
@@ -342,6 +350,7 @@ __global__ void __launch_bounds__(256, 1) stage_kernel(StageArgs a) {
           double x = a.beta * vin_e[c * N + i] - a.gamma * (double)acc;
           if (vn_e) x += a.alpha * vn_e[c * N + i];
           vout_e[c * N + i] = x;
+          if (a.vout32) a.vout32[((long)e * D + c0) * N + c * N + i] = (float)x;
         }
       }
       return;
@@ -354,6 +363,7 @@ __global__ void __launch_bounds__(256, 1) stage_kernel(StageArgs a) {
       double x = a.beta * vin_e[c * N + i] - a.gamma * (double)r[c][i];
       if (vn_e) x += a.alpha * vn_e[c * N + i];
       vout_e[c * N + i] = x;
+      if (a.vout32) a.vout32[((long)e * D + c0) * N + c * N + i] = (float)x;
     }
 }
 
