@@ -209,17 +209,27 @@ def stage_bytes_flops(wl):
     return byts, flops, N
 
 
+# committed ncu summaries: (workload, precision) -> (summary file, kernel source it measured)
+PROFILES = {
+    ("square256_k4", "bf16x3"): ("stage_tc_kernel_square256_k4.md", "dgc_stage_tc.cuh"),
+    ("parallelogram256_k4", "fp32"): ("stage_quad_kernel_parallelogram256_k4.md", "dgc_stage_quad.cu"),
+    ("parallelepiped32_k3", "fp32"): ("stage_hex_kernel_parallelepiped32_k3.md", "dgc_stage_hex.cu"),
+}
+
+
 def ncu_traffic(wl, prec):
     """DRAM bytes per stage launch from the committed ncu capture, if it still applies.
 
-    The capture records the sha1 of the kernel source it measured; after any
-    change of that source the figure is stale and None is returned.
+    The capture records the sha1 of the kernel source it measured and the
+    precision; after any change of that source the figure is stale and None is
+    returned.
     """
-    if prec not in TC_PRECS or wl.name != "square256_k4":
+    entry = PROFILES.get((wl.name, prec))
+    if entry is None:
         return None
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "stage_tc_kernel_square256_k4.md")
-    src = os.path.join(ROOT, "paper_1508_04245_gb300", "csrc", "dgc_stage_tc.cuh")
+    prof = os.path.join(ROOT, "profiles", entry[0])
+    src = os.path.join(ROOT, "paper_1508_04245_gb300", "csrc", entry[1])
     try:
         text = open(prof).read()
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
@@ -229,7 +239,7 @@ def ncu_traffic(wl, prec):
                   if ln.startswith(("kernel_source_sha1:", "traffic_bytes_per_launch:", "prec:")))
     if fields.get("kernel_source_sha1", "").split()[0:1] != [sha]:
         return None
-    if fields.get("prec", "tf32x3").strip() != prec:
+    if fields.get("prec", "").strip() != prec:
         return None
     return float(fields["traffic_bytes_per_launch"].strip())
 
@@ -404,7 +414,8 @@ def measure_shape(torch, dgconv, name: str, rank: int, world: int, flush, stream
         achieved = byts * wl.n_elem / (stage_ms * 1e-3) / 1e9
         tflops = flops * wl.n_elem / (stage_ms * 1e-3) / 1e12
         roof = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_src, "achieved_tflops": tflops}
+                "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_src, "achieved_tflops": tflops,
+                "traffic": ncu_traffic(wl, prec)}
         if prec == "fp64":
             # FP64 FMAs bound this variant: against the nominal FP64 rate of the part
             roof = {"bound": "alu", "kernel": kernel, "achieved": tflops, "peak": FP64_TFLOPS,
