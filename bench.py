@@ -592,7 +592,9 @@ def main():
         mesh.mass(v, out=mv)                              # a6 (M^V)
         mesh.transfer_T(mv, out=g)                        # a8
     # geometry, transfer, [wind prep (+ layout in/out on the tensor-core path), stages], mass, transfer_T (2)
-    launches_per_step = 1 + 1 + (1 + 3 * substeps + (2 if args.prec in TC_PRECS else 0)) + 1 + 2
+    # (+1 in FP32: the FP32 copy of the state at the start of the RK sequence)
+    launches_per_step = 1 + 1 + (1 + 3 * substeps + (2 if args.prec in TC_PRECS else 0)
+                                 + (1 if args.prec == "fp32" else 0)) + 1 + 2
 
     for _ in range(args.warmup):
         step()

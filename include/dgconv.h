@@ -413,6 +413,21 @@ dgc_status dgc_quad_table(int k, const char* name, double* out, int64_t* count);
 dgc_status dgc_quad_connectivity(int n_vert, int n_elem, const int32_t* elems, int32_t* facet_id, int32_t* nbr,
                                  int8_t* orient, int8_t* flip, int32_t* n_facets);
 
+/* Reference table `name` of the order-k parallelepiped element (the cube
+ * [0,1]^3), host double array: "Bv" [QV][N] basis at the volume points
+ * (q = (p m + q') m + q'', m = floor(3k/2) + 1), "wv" [QV], "xv" [QV][3], "wf"
+ * [m^2] the face rule, "Bf" [6][m^2][N] the basis at the face points, "Cb"
+ * [3N][3N] the W_h basis on the vector tensor basis, "q1L" / "q1D" [m][k+1],
+ * "q1E" [2][k+1].  Writes *count = entries; out may be NULL. */
+dgc_status dgc_hex_table(int k, const char* name, double* out, int64_t* count);
+
+/* Host connectivity exactly as dgc_mesh_upload_hex builds it: facet_id, nbr
+ * ((e' << 3) | f', -1 on the boundary), orient and fcode (T | o1 << 1 | o2 << 2:
+ * the local corner (o1, o2) of the face's global origin, T = 1 when the global
+ * s1 runs along the local s2), each [n_elem][6]; any output may be NULL. */
+dgc_status dgc_hex_connectivity(int n_vert, int n_elem, const int32_t* elems, int32_t* facet_id, int32_t* nbr,
+                                int8_t* orient, int8_t* fcode, int32_t* n_facets);
+
 /* Host connectivity exactly as dgc_mesh_upload builds it: facet_id
  * [n_elem][dim+1], nbr [n_elem][dim+1] ((neighbour << 2) | neighbour's local
  * facet, or -1 on the boundary), orient [n_elem][dim+1] (+1 owner/boundary,

@@ -1676,6 +1676,53 @@ dgc_status dgc_quad_connectivity(int n_vert, int n_elem, const int32_t* elems, i
   return DGC_OK;
 }
 
+dgc_status dgc_hex_table(int k, const char* name, double* out, int64_t* count) {
+  if (!name || !count) return fail(DGC_ERR_ARG, "NULL argument");
+  if (!dgc::hex_supported(k)) return fail(DGC_ERR_UNSUPPORTED, "order k=%d not supported for parallelepipeds", k);
+  const dgc::Tables* tp;
+  try {
+    tp = &dgc::hex_tables(k);
+  } catch (const std::exception& ex) {
+    return fail(DGC_ERR_ARG, "reference table build failed: %s", ex.what());
+  }
+  const dgc::Tables& t = *tp;
+  const std::vector<double>* v = nullptr;
+  const std::string n(name);
+  if (n == "Bv") v = &t.Bv;
+  else if (n == "wv") v = &t.wv;
+  else if (n == "xv") v = &t.xv;
+  else if (n == "wf") v = &t.wf;
+  else if (n == "Bf") v = &t.Bf;
+  else if (n == "Cb") v = &t.Cb;
+  else if (n == "q1L") v = &t.q1L;
+  else if (n == "q1D") v = &t.q1D;
+  else if (n == "q1E") v = &t.q1E;
+  else return fail(DGC_ERR_ARG, "unknown table '%s'", name);
+  *count = (int64_t)v->size();
+  if (out) std::memcpy(out, v->data(), v->size() * sizeof(double));
+  return DGC_OK;
+}
+
+dgc_status dgc_hex_connectivity(int n_vert, int n_elem, const int32_t* elems, int32_t* facet_id, int32_t* nbr,
+                                int8_t* orient, int8_t* fcode, int32_t* n_facets) {
+  if (n_elem <= 0 || n_vert <= 0 || !elems) return fail(DGC_ERR_ARG, "empty mesh");
+  std::vector<int> el(elems, elems + (size_t)n_elem * 8);
+  dgc::Connectivity con;
+  std::vector<signed char> fc;
+  std::vector<int> qn;
+  std::string why = dgc::build_hex_connectivity(n_vert, n_elem, el, con, fc, qn);
+  if (!why.empty()) return fail(DGC_ERR_ARG, "%s", why.c_str());
+  const size_t n = (size_t)n_elem * 6;
+  for (size_t j = 0; j < n; ++j) {
+    if (facet_id) facet_id[j] = con.facet_id[j];
+    if (nbr) nbr[j] = qn[j];
+    if (orient) orient[j] = con.orient[j];
+    if (fcode) fcode[j] = fc[j];
+  }
+  if (n_facets) *n_facets = con.n_facets;
+  return DGC_OK;
+}
+
 dgc_status dgc_connectivity(int dim, int n_vert, int n_elem, const int32_t* elems, int32_t* facet_id, int32_t* nbr,
                             int8_t* orient, int32_t* n_facets) {
   if (dim != 2 && dim != 3) return fail(DGC_ERR_UNSUPPORTED, "dim must be 2 or 3");

@@ -62,6 +62,8 @@ SIGNATURES = {
                          ctypes.POINTER(ctypes.c_int32)],
     "dgc_quad_table": [ctypes.c_int, ctypes.c_char_p, _vp, _i64p],
     "dgc_quad_connectivity": [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int32)],
+    "dgc_hex_table": [ctypes.c_int, ctypes.c_char_p, _vp, _i64p],
+    "dgc_hex_connectivity": [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int32)],
     "dgc_last_error": [ctypes.c_char_p, ctypes.c_int],
 }
 
@@ -396,6 +398,29 @@ def quad_connectivity(n_vert: int, elems):
     vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)      # noqa: E731
     check(lib().dgc_quad_connectivity(n_vert, E, vp(elems), vp(fid), vp(nbr), vp(ori), vp(flip), ctypes.byref(nf)))
     return fid, nbr, ori, flip, nf.value
+
+
+def hex_table(k: int, name: str) -> np.ndarray:
+    """A reference table of the parallelepiped element (host only, no GPU needed)."""
+    cnt = ctypes.c_int64()
+    check(lib().dgc_hex_table(k, name.encode(), None, ctypes.byref(cnt)))
+    out = np.empty(cnt.value)
+    check(lib().dgc_hex_table(k, name.encode(), out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)))
+    return out
+
+
+def hex_connectivity(n_vert: int, elems):
+    """(facet_id, nbr codes, orient, fcode, n_faces) as the parallelepiped upload builds them (host only)."""
+    elems = np.ascontiguousarray(elems, dtype=np.int32)
+    E = elems.shape[0]
+    fid = np.empty((E, 6), np.int32)
+    nbr = np.empty((E, 6), np.int32)
+    ori = np.empty((E, 6), np.int8)
+    fc = np.empty((E, 6), np.int8)
+    nf = ctypes.c_int32()
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)      # noqa: E731
+    check(lib().dgc_hex_connectivity(n_vert, E, vp(elems), vp(fid), vp(nbr), vp(ori), vp(fc), ctypes.byref(nf)))
+    return fid, nbr, ori, fc, nf.value
 
 
 def potential_values(mesh: Mesh, potential) -> np.ndarray:

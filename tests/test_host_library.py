@@ -173,3 +173,35 @@ def test_quad_connectivity_matches_oracle():
     bad[3, 1] = bad[3, 0]
     with pytest.raises(dgconv.DgcError):
         dgconv.quad_connectivity(v.shape[0], bad)
+
+
+# ---- parallelepipeds ------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_hex_tables_match_oracle(k):
+    from oracle import hexa as OX
+    from oracle import quad as OQ
+    m = OQ.n_points(k)
+    xq, wq = OX.cube_rule(m)
+    N = (k + 1) ** 3
+    Bv = dgconv.hex_table(k, "Bv").reshape(m ** 3, N)
+    assert np.abs(Bv - OX.vbasis(k, xq)).max() < 1e-13 * np.abs(Bv).max()
+    assert np.allclose(dgconv.hex_table(k, "wv"), wq, atol=1e-15)
+    s1, s2, ws = OX.square_rule(m)
+    Bf = dgconv.hex_table(k, "Bf").reshape(6, m * m, N)
+    for f in range(6):
+        assert np.abs(Bf[f] - OX.vbasis(k, OX.face_point(f, s1, s2))).max() < 1e-13 * np.abs(Bv).max()
+    Cb = dgconv.hex_table(k, "Cb").reshape(3 * N, 3 * N)
+    ref = np.linalg.inv(OX.local_dof_matrix(k))
+    assert np.abs(Cb - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_hex_connectivity_matches_oracle():
+    from oracle import hexa as OX
+    v, e = W.parallelepiped_mesh(3, 6)
+    M = OX.HexMesh(v, e)
+    fid, nbr, ori, fc, nf = dgconv.hex_connectivity(v.shape[0], e)
+    assert nf == M.n_facets and (fid == M.facet_id).all() and (ori == M.orient).all()
+    code = M.fcode[..., 0] | (M.fcode[..., 1] << 1) | (M.fcode[..., 2] << 2)
+    assert (fc == code).all()
+    inner = nbr >= 0
+    assert (np.where(inner, nbr >> 3, -1) == M.nbr).all() and (np.where(inner, nbr & 7, -1) == M.nbr_facet).all()
