@@ -4,7 +4,8 @@
  * for unsteady incompressible flows" (arXiv:1508.04245), on one GB300 GPU.
  *
  * The library evaluates, for affine triangles (dim = 2) and tetrahedra
- * (dim = 3) of polynomial order k:
+ * (dim = 3) of polynomial order k, and for parallelograms, parallelepipeds and
+ * quadratic (curved) triangles (dgc_mesh_upload_quad / _hex / _curved):
  *
  *   I        the transfer from the H(div)-conforming velocity space W_h
  *            (BDM_k) to the DG space V_h = [P^k]^dim            (Sec. 2.4)

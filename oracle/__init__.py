@@ -18,7 +18,12 @@ What it computes (Lehrenfeld & Schoeberl, arXiv:1508.04245):
   (the L2 problem that defines it) and its transpose I^T;
 * ``hdiv`` -- the H(div)-conforming BDM_k velocity space of Sec. 2.1.1
   (facet normal moments + Nedelec interior moments), the DOFs of analytic
-  fields and the divergence-free winds built as curls of potentials.
+  fields and the divergence-free winds built as curls of potentials;
+* ``quad`` / ``hexa`` -- the same for parallelograms and parallelepipeds
+  (uncurved quadrilaterals and hexahedra of Sec. 2: [Q^k]^d with tensor
+  Legendre bases, the H(div) subspace of the Piola images);
+* ``curved`` -- quadratic (curved) triangles (remark on curved elements in
+  Sec. 2.4: dense mass blocks, I as the L2 projection).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants the paper states (exact divergence, upwind stability, the
