@@ -212,6 +212,7 @@ def stage_bytes_flops(wl):
 # committed ncu summaries: (workload, precision) -> (summary file, kernel source it measured)
 PROFILES = {
     ("square256_k4", "bf16x3"): ("stage_tc_kernel_square256_k4.md", "dgc_stage_tc.cuh"),
+    ("square256_k4", "fp32"): ("stage_kernel_square256_k4_fp32.md", "dgc_stage.cuh"),
     ("parallelogram256_k4", "fp32"): ("stage_quad_kernel_parallelogram256_k4.md", "dgc_stage_quad.cu"),
     ("parallelepiped32_k3", "fp32"): ("stage_hex_kernel_parallelepiped32_k3.md", "dgc_stage_hex.cu"),
 }
