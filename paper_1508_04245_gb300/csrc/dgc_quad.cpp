@@ -475,9 +475,7 @@ Tables build_hex(int K) {
   };
   t.Lg_int.resize((size_t)s.QD * s.NLAG * 3);
   for (int q = 0; q < s.QD; ++q) {
-    const LD xi[3] = {(LD)t.xd[3 * q], (LD)t.xd[3 * q + 1], (LD)t.xd[3 * q + 2]};
-    const LD xg[3] = {gd[q / (nd * nd)], gd[(q / nd) % nd], gd[q % nd]};
-    (void)xi;
+    const LD xg[3] = {gd[q / (nd * nd)], gd[(q / nd) % nd], gd[q % nd]};   // the interior point q
     lag_grad(xg, &t.Lg_int[(size_t)q * s.NLAG * 3]);
   }
   t.Lg_fac.resize((size_t)6 * s.QFD * s.NLAG * 3);
