@@ -205,3 +205,27 @@ def test_hex_connectivity_matches_oracle():
     assert (fc == code).all()
     inner = nbr >= 0
     assert (np.where(inner, nbr >> 3, -1) == M.nbr).all() and (np.where(inner, nbr & 7, -1) == M.nbr_facet).all()
+
+
+def test_quad_and_hex_host_inputs_are_validated():
+    v, e = W.parallelogram_mesh(3, 1, reorient=False)
+    # a third element on an existing edge: not conforming
+    extra = np.array([[e[0, 0], e[0, 1], v.shape[0], v.shape[0] + 1]], dtype=np.int32)
+    with pytest.raises(dgconv.DgcError):
+        dgconv.quad_connectivity(v.shape[0] + 2, np.vstack([e, extra, extra[:, [1, 0, 3, 2]]]))
+    bad = e.copy()
+    bad[0, 3] = v.shape[0] + 5                                  # vertex out of range
+    with pytest.raises(dgconv.DgcError):
+        dgconv.quad_connectivity(v.shape[0], bad)
+    hv, he = W.parallelepiped_mesh(2, 1, reorient=False)
+    bad = he.copy()
+    bad[1, 7] = bad[1, 0]                                       # repeated vertex
+    with pytest.raises(dgconv.DgcError):
+        dgconv.hex_connectivity(hv.shape[0], bad)
+    for fn in (dgconv.quad_table, dgconv.hex_table):
+        with pytest.raises(dgconv.DgcError):
+            fn(2, "no_such_table")
+    with pytest.raises(dgconv.DgcError):
+        dgconv.hex_table(4, "Bv")                               # parallelepipeds: k <= 3
+    with pytest.raises(dgconv.DgcError):
+        dgconv.quad_table(7, "Bv")
