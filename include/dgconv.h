@@ -99,10 +99,17 @@ typedef int dgc_status;
  *               three BF16 pieces, six products, FP32 accumulation; the test
  *               contractions in FP32 on CUDA cores; FP32 stage increments,
  *               FP64 accumulation once per substep
- *   DGC_TF32X3  the same with kind::tf32 and a two-piece TF32 split (about 22
- *               significand bits per operand), three products
- * Other orders and tetrahedra return DGC_ERR_UNSUPPORTED for the tensor-core
- * precisions. */
+ *               tetrahedra, k <= 4: both contractions of the volume term on
+ *               tcgen05 (the evaluation at the quadrature points and the test
+ *               contraction against the basis gradients), the same split, each
+ *               chunk of 16 quadrature points accumulated separately and the
+ *               chunks added in FP32 on CUDA cores; the facet terms in FP32 on
+ *               CUDA cores; FP32 increments, FP64 accumulation once per substep
+ *   DGC_TF32X3  triangles, k <= 4: as DGC_BF16X3 with kind::tf32 and a
+ *               two-piece TF32 split (about 22 significand bits per operand),
+ *               three products
+ * Other orders, other element shapes and DGC_TF32X3 on tetrahedra return
+ * DGC_ERR_UNSUPPORTED for the tensor-core precisions. */
 typedef enum { DGC_FP64 = 0, DGC_FP32 = 1, DGC_BF16X3 = 2, DGC_TF32X3 = 3 } dgc_prec;
 typedef enum { DGC_SSPRK2 = 2, DGC_SSPRK3 = 3 } dgc_scheme;
 
@@ -366,21 +373,23 @@ dgc_status dgc_min_edge(const dgc_mesh* mesh, double* out);
 #define DGC_NOALLOC_SCRATCH_DOUBLES 2097152LL
 
 /* g = I^T f exactly as dgc_transfer_T, for callers that cannot allocate
- * device memory when they call: code that runs while a stream is captured
- * into a CUDA graph, or applications that fix their device memory at start-up
- * (dgc_transfer_T allocates its facet scratch on the handle at its first call).
+ * device memory when they call: applications that reserve all their device
+ * memory at start-up, and host loops that must not block on the device-wide
+ * synchronisation a cudaMalloc or cudaFree implies (dgc_transfer_T allocates its
+ * facet scratch on the handle at its first call).
  * The paper has no counterpart; this is a library service.
  * Scratch: a fixed file-scope device array of DGC_NOALLOC_SCRATCH_DOUBLES
  * doubles, held on every GPU that loads the library until the process exits.
- * The mesh must need at most that many (n_elem * (dim+1) * n_fm); larger
- * meshes get DGC_ERR_ARG and a message, and nothing is launched.  The call
- * performs no allocation (no cudaMalloc / cudaFree).  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) for that
- * device; make that first call before any stream capture.  All calls share
- * the one array, so calls that overlap on the GPU (different streams, or
- * different handles concurrently) race; serialise them.  Every scratch entry a
- * call reads is written by the same call first.  Arguments, layouts and
- * errors as dgc_transfer_T. */
+ * The mesh must need at most that many: n_elem * (facets per element) * n_fm
+ * doubles, with 3 facets per triangle, 4 per tetrahedron or parallelogram and
+ * 6 per parallelepiped; larger meshes get DGC_ERR_ARG and a message, and
+ * nothing is launched.  The call performs no allocation (no cudaMalloc /
+ * cudaFree).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  All calls share the one array, so calls that overlap on the
+ * GPU (different streams, or different handles concurrently) race; serialise
+ * them.  Every scratch entry a call reads is written by the same call first.
+ * Arguments, layouts and errors as dgc_transfer_T. */
 dgc_status dgc_transfer_T_noalloc(dgc_mesh* mesh, const double* f_dg, double* g_hdiv, void* stream);
 
 /* Host-only introspection (no GPU needed) -------------------------------- */

@@ -4,10 +4,11 @@
 // dgc_transfer_T keeps its facet scratch (one value per element, local facet
 // and facet moment) in a buffer the library allocates on the mesh handle at
 // the first call.  Callers that may not allocate device memory when they
-// call -- code running while a stream is being captured into a CUDA graph,
-// or a host application that fixes its device memory at start-up -- use
-// this variant instead: its scratch is a file-scope device array of fixed
-// size, present on every GPU that loads the library until the process ends.
+// call -- an application that reserves its device memory at start-up, or a
+// host loop that must not block on the device-wide synchronisation of
+// cudaMalloc / cudaFree -- use this variant instead: its scratch is a
+// file-scope device array of fixed size, present on every GPU that loads the
+// library until the process ends.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -18,7 +19,7 @@
 
 namespace {
 
-// 16 MiB of FP64 scratch: E * (dim+1) * n_fm doubles must fit.
+// 16 MiB of FP64 scratch: E * (facets per element) * n_fm doubles must fit.
 constexpr long long kNoallocScratchDoubles = DGC_NOALLOC_SCRATCH_DOUBLES;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles];
 

@@ -1,6 +1,7 @@
 """GPU test of dgc_transfer_T_noalloc, the variant of I^T for callers that
-cannot allocate device memory at call time (graph-capture regions,
-applications with a fixed memory budget).
+cannot allocate device memory at call time (applications that reserve their
+device memory at start-up, host loops that must not block on the device-wide
+synchronisation of cudaMalloc / cudaFree).
 
 It must give the same result as dgc_transfer_T, call after call (the shared
 fixed scratch keeps the previous call's contents), and reject meshes whose
@@ -31,11 +32,26 @@ def _call(dgconv, mesh, f, g):
     return rc
 
 
-@pytest.mark.parametrize("dim,k,n", [(2, 4, 9), (3, 3, 3)])
-def test_noalloc_matches_transfer_T_twice(lib, dim, k, n):
+def _mesh(lib, shape, dim, k):
     from paper_1508_04245_gb300 import workloads as W
-    verts, elems = W.square_mesh(n, 0.1, 4) if dim == 2 else W.cube_mesh(n, 0.05, 4)
-    mesh = lib.Mesh(dim, k, verts, elems)
+    if shape == "simplex":
+        verts, elems = W.square_mesh(9, 0.1, 4) if dim == 2 else W.cube_mesh(3, 0.05, 4)
+        return lib.Mesh(dim, k, verts, elems)
+    if shape == "quad":
+        return lib.Mesh(2, k, *W.parallelogram_mesh(6, 4), shape="quad")
+    if shape == "hex":
+        return lib.Mesh(3, k, *W.parallelepiped_mesh(3, 4), shape="hex")
+    verts, elems, nodes = W.curved_square_mesh(8, 0.1, 4)
+    return lib.Mesh(2, k, verts, elems, shape="curved", edge_nodes=nodes)
+
+
+# every element shape: triangles, tetrahedra, parallelograms (4 facets),
+# parallelepipeds (6 faces) and curved triangles (a second kernel rewrites the
+# scratch of the curved elements)
+@pytest.mark.parametrize("shape,dim,k", [("simplex", 2, 4), ("simplex", 3, 3), ("quad", 2, 3), ("hex", 3, 2),
+                                         ("curved", 2, 3)])
+def test_noalloc_matches_transfer_T_twice(lib, shape, dim, k):
+    mesh = _mesh(lib, shape, dim, k)
     rng = np.random.default_rng(31)
     for call in range(2):
         f = torch.tensor(rng.standard_normal((mesh.n_elem, dim, mesh.N)), dtype=torch.float64, device="cuda")
@@ -44,7 +60,7 @@ def test_noalloc_matches_transfer_T_twice(lib, dim, k, n):
         assert _call(lib, mesh, f, got) == 0, lib.last_error()
         torch.cuda.synchronize()
         err = float((got - ref).abs().max() / ref.abs().max())
-        assert err < 1e-12, (call, err)
+        assert err < 1e-12, (shape, call, err)
 
 
 def test_noalloc_rejects_meshes_beyond_its_scratch(lib):
