@@ -158,22 +158,24 @@ def rk_substeps(op: ConvectionOracle, v, ds: float, nsteps: int, scheme: int) ->
     return v
 
 
-def transfer(mesh, k, u_hdiv) -> np.ndarray:
-    """w = I u: w_{c,i} = (1/|det J|) int_T u_c psi_i dx   (Sec. 2.4, L2 problem)."""
+def transfer(mesh, k, u_hdiv, sel=None) -> np.ndarray:
+    """w = I u: w_{c,i} = (1/|det J|) int_T u_c psi_i dx   (Sec. 2.4, L2 problem);
+    ``sel`` restricts the output to a subset of elements."""
     d = mesh.dim
     xq, wq = simplex_rule(d, 2 * k)
-    E = mesh.n_elem
+    sel = np.arange(mesh.n_elem) if sel is None else np.asarray(sel, dtype=np.int64)
     psi = B.dubiner_values(d, k, xq)                                     # [Q, N]
-    u = np.stack([H.evaluate(mesh, k, u_hdiv, np.full(xq.shape[0], e), xq) for e in range(E)]) \
-        if E <= 64 else _eval_all(mesh, k, u_hdiv, xq)                    # [E, Q, d]
+    u = np.stack([H.evaluate(mesh, k, u_hdiv, np.full(xq.shape[0], e), xq) for e in sel]) \
+        if sel.size <= 64 else _eval_all(mesh, k, u_hdiv, xq, sel)        # [S, Q, d]
     return np.einsum("q,eqc,qi->eci", wq, u, psi)
 
 
-def _eval_all(mesh, k, u_hdiv, xq):
-    coef = H.ref_coeffs(mesh, k, u_hdiv)                                  # [E, d, N]
+def _eval_all(mesh, k, u_hdiv, xq, sel=None):
+    sel = np.arange(mesh.n_elem) if sel is None else sel
+    coef = H.ref_coeffs(mesh, k, u_hdiv, sel=sel)                         # [S, d, N]
     psi = B.dubiner_values(mesh.dim, k, xq)
     uref = np.einsum("eci,qi->eqc", coef, psi)
-    return np.einsum("eab,eqb->eqa", mesh.J, uref) / mesh.detJ[:, None, None]
+    return np.einsum("eab,eqb->eqa", mesh.J[sel], uref) / mesh.detJ[sel][:, None, None]
 
 
 def transfer_T(mesh, k, f_dg) -> np.ndarray:
@@ -247,10 +249,11 @@ def assemble(op: ConvectionOracle) -> np.ndarray:
     return A
 
 
-def max_wind_speed(mesh, k, u_hdiv) -> float:
-    """max |u(x_q)| over the volume quadrature points (degree 3k-1 rule)."""
+def max_wind_speed(mesh, k, u_hdiv, sel=None) -> float:
+    """max |u(x_q)| over the volume quadrature points (degree 3k-1 rule), over the
+    elements ``sel`` (default all)."""
     xq, _ = simplex_rule(mesh.dim, 3 * k - 1)
-    return float(np.linalg.norm(_eval_all(mesh, k, u_hdiv, xq), axis=2).max())
+    return float(np.linalg.norm(_eval_all(mesh, k, u_hdiv, xq, sel), axis=2).max())
 
 
 def cfl_ds(mesh, k, u_hdiv, cfl: float) -> float:

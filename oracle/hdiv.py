@@ -76,7 +76,7 @@ def evaluate(mesh, k, u_hdiv, e, xi) -> np.ndarray:
     return np.einsum("mab,mb->ma", mesh.J[e], uref) / mesh.detJ[e][:, None]
 
 
-def dofs_of_field(mesh, k, field_e, degree=None) -> np.ndarray:
+def dofs_of_field(mesh, k, field_e, degree=None, elems=None) -> np.ndarray:
     """BDM DOFs of a field given per element.
 
     ``field_e(e [S], xi [Q, d]) -> u [S, Q, d]`` returns the physical field at
@@ -84,6 +84,10 @@ def dofs_of_field(mesh, k, field_e, degree=None) -> np.ndarray:
     from the facet's owner element:
     int_F u . n_F q_m dS = |F| (d-1)! sum_q w_q (u . n_F)(x_q) q_m(s_q).
     Interior moments: int_T^ u^ . t_m dxi with u^ = det J J^{-1} u.
+
+    ``elems`` restricts the work to the facets owned by those elements and to
+    their interiors (the other entries stay zero); the restrictions to a
+    partition of the elements add up to the full vector.
     """
     d = mesh.dim
     n_fm, n_int, n_w, n_hdiv = layout(mesh, k)
@@ -92,11 +96,15 @@ def dofs_of_field(mesh, k, field_e, degree=None) -> np.ndarray:
     s, ws = simplex_rule(d - 1, degree)
     qm = B.dubiner_values(d - 1, k, s)                          # [Qf, n_fm]
     G = mesh.n_facets
+    E = mesh.n_elem
     e_own = mesh.facet_owner[:, 0]
     f_own = mesh.facet_owner[:, 1]
     fact = math.factorial(d - 1)
+    es = np.arange(E) if elems is None else np.unique(np.asarray(elems, dtype=np.int64))
+    mine = np.zeros(E, dtype=bool)
+    mine[es] = True
     for f in range(d + 1):
-        gs = np.nonzero(f_own == f)[0]
+        gs = np.nonzero((f_own == f) & mine[e_own])[0]
         if gs.size == 0:
             continue
         xi_f = B.facet_param_to_ref(d, f, s)                    # [Qf, d]
@@ -108,21 +116,20 @@ def dofs_of_field(mesh, k, field_e, degree=None) -> np.ndarray:
         xq, wq = simplex_rule(d, degree)
         fields = B.nedelec_interior_fields(d, k)
         T = np.stack([np.stack([P.evaluate(t[c], xq) for c in range(d)], axis=1) for t in fields])  # [n_int, Q, d]
-        E = mesh.n_elem
-        u = field_e(np.arange(E), xq)                           # [E, Q, d]
-        uref = mesh.detJ[:, None, None] * np.einsum("eab,eqb->eqa", mesh.Jinv, u)
+        u = field_e(es, xq)                                     # [S, Q, d]
+        uref = mesh.detJ[es, None, None] * np.einsum("eab,eqb->eqa", mesh.Jinv[es], u)
         mom = np.einsum("eqa,mqa,q->em", uref, T, wq)
-        out[G * n_fm:] = mom.ravel()
+        out[G * n_fm + (es[:, None] * n_int + np.arange(n_int)[None, :]).ravel()] = mom.ravel()
     return out
 
 
-def dofs_of_function(mesh, k, func, degree=None) -> np.ndarray:
-    """BDM DOFs of an analytic field func(x [M, d]) -> [M, d]."""
+def dofs_of_function(mesh, k, func, degree=None, elems=None) -> np.ndarray:
+    """BDM DOFs of an analytic field func(x [M, d]) -> [M, d] (``elems`` as in ``dofs_of_field``)."""
     def field_e(e, xi):
         S, Q = e.shape[0], xi.shape[0]
         x = mesh.to_physical(np.repeat(e, Q), np.tile(xi, (S, 1)))
         return func(x).reshape(S, Q, mesh.dim)
-    return dofs_of_field(mesh, k, field_e, degree)
+    return dofs_of_field(mesh, k, field_e, degree, elems=elems)
 
 
 def lagrange_nodes_ref(dim: int, order: int) -> np.ndarray:
@@ -160,14 +167,16 @@ def LDpow(x, e):
     return np.longdouble(x) ** e
 
 
-def wind_from_potential(mesh, k, potential) -> np.ndarray:
+def wind_from_potential(mesh, k, potential, elems=None) -> np.ndarray:
     """Exactly divergence-free wind in W_h as the curl of an interpolated potential.
 
     Reading A13: interpolate the stream function psi (2D) or each component of
     the vector potential A (3D) by continuous P^{k+1} Lagrange elements
     (element-wise equispaced nodes, which coincide on shared facets), take the
     curl element by element (a [P^k]^d field with continuous normal component
-    and zero divergence) and return its BDM_k DOFs.
+    and zero divergence) and return its BDM_k DOFs.  ``elems`` restricts the
+    DOFs computed as in ``dofs_of_field`` (the potential is then interpolated
+    on those elements only).
     """
     d = mesh.dim
     order = k + 1
@@ -175,22 +184,26 @@ def wind_from_potential(mesh, k, potential) -> np.ndarray:
     L = _lagrange_polys(d, order)
     dL = [[P.deriv(p, a) for a in range(d)] for p in L]
     E = mesh.n_elem
-    ee = np.repeat(np.arange(E), nodes.shape[0])
-    X = mesh.to_physical(ee, np.tile(nodes, (E, 1)))
+    es = np.arange(E) if elems is None else np.unique(np.asarray(elems, dtype=np.int64))
+    loc = np.full(E, -1, dtype=np.int64)
+    loc[es] = np.arange(es.size)
+    S = es.size
+    ee = np.repeat(es, nodes.shape[0])
+    X = mesh.to_physical(ee, np.tile(nodes, (S, 1)))
     if d == 2:
-        vals = potential(X[:, 0], X[:, 1]).reshape(E, -1)           # [E, n_lag]
+        vals = potential(X[:, 0], X[:, 1]).reshape(S, -1)           # [S, n_lag]
     else:
-        vals = potential(X[:, 0], X[:, 1], X[:, 2]).reshape(3, E, -1).transpose(1, 2, 0)  # [E, n_lag, 3]
+        vals = potential(X[:, 0], X[:, 1], X[:, 2]).reshape(3, S, -1).transpose(1, 2, 0)  # [S, n_lag, 3]
 
     def field_e(e, xi):
         # reference gradients of the Lagrange functions at xi -> [Q, n_lag, d]
         gl = np.stack([np.stack([P.evaluate(dL[n][a], xi) for a in range(d)], axis=1) for n in range(len(L))], axis=1)
         gphys = np.einsum("sba,qnb->sqna", mesh.Jinv[e], gl)       # J^{-T} grad^ -> [S, Q, n_lag, d]
         if d == 2:
-            gpsi = np.einsum("sn,sqna->sqa", vals[e], gphys)
+            gpsi = np.einsum("sn,sqna->sqa", vals[loc[e]], gphys)
             return np.stack([gpsi[..., 1], -gpsi[..., 0]], axis=-1)
-        gA = np.einsum("snc,sqna->sqca", vals[e], gphys)            # dA_c/dx_a
+        gA = np.einsum("snc,sqna->sqca", vals[loc[e]], gphys)       # dA_c/dx_a
         return np.stack([gA[..., 2, 1] - gA[..., 1, 2], gA[..., 0, 2] - gA[..., 2, 0],
                          gA[..., 1, 0] - gA[..., 0, 1]], axis=-1)
 
-    return dofs_of_field(mesh, k, field_e)
+    return dofs_of_field(mesh, k, field_e, elems=elems)

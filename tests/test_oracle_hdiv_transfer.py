@@ -154,3 +154,30 @@ def test_mass_identity_MU_equals_IT_MV_I(dim, k):
     IT_MV_I = np.stack([dg.transfer_T(mesh, k, dg.mass(mesh, dg.transfer(mesh, k, np.eye(n)[h])))
                         for h in range(n)], axis=1)
     assert np.abs(IT_MV_I - MU).max() < 1e-12 * np.abs(MU).max()
+
+
+@pytest.mark.parametrize("dim,k", [(2, 3), (3, 2)])
+def test_dofs_restricted_to_an_element_partition_add_up(dim, k):
+    """The element-subset restriction of the DOF builders (used to split large
+    meshes over processes) computes each entry as the full call does: the
+    restrictions to a partition of the elements sum to the full vector (up to
+    the summation order numpy picks for a batch of another size)."""
+    mesh = OM.Mesh(*(W.square_mesh(5, 0.1, 2) if dim == 2 else W.cube_mesh(2, 0.05, 2)))
+    pot = W.stream_random(3) if dim == 2 else W.potential_random(3)
+    full = H.wind_from_potential(mesh, k, pot)
+    parts = np.array_split(np.random.default_rng(1).permutation(mesh.n_elem), 3)
+    tol = 4 * np.finfo(np.float64).eps
+    got = sum(H.wind_from_potential(mesh, k, pot, elems=p) for p in parts)
+    assert np.abs(got - full).max() <= tol * np.abs(full).max()
+    field = W.fourier_field(4, dim)
+    full_f = H.dofs_of_function(mesh, k, field)
+    got_f = sum(H.dofs_of_function(mesh, k, field, elems=p) for p in parts)
+    assert np.abs(got_f - full_f).max() <= tol * np.abs(full_f).max()
+
+
+def test_transfer_restricted_to_elements_matches_the_full_transfer():
+    mesh = OM.Mesh(*W.square_mesh(9, 0.1, 3))
+    u = np.random.default_rng(2).standard_normal(H.layout(mesh, 3)[3])
+    full = dg.transfer(mesh, 3, u)
+    for sel in (np.array([0, 5, mesh.n_elem - 1]), np.arange(70, 150)):
+        assert np.allclose(dg.transfer(mesh, 3, u, sel=sel), full[sel], rtol=0, atol=1e-14 * np.abs(full).max())
