@@ -141,6 +141,10 @@ struct dgc_mesh {
   // stage-table blobs
   DevBuf<double> tab64;
   DevBuf<float> tab32, tcblob, tcblob16, wcoef, trA, trB;   // tensor-core blobs: TF32x3, BF16x3
+  // tetrahedral tensor-core path: BF16 table chunks (the FP32 facet tables in tcblob)
+  // and the tile-blocked frozen facet flux
+  DevBuf<unsigned char> tc3chunks;
+  DevBuf<float> fw3;
   DevBuf<double> ts0;              // tile-blocked FP64 state of the tensor-core path
   DevBuf<float> tsf, d1, d2;       // its FP32 copy and the FP32 stage increments
   DevBuf<double> ts1, tsg;         // pseudo-time solve on that path: second state, right-hand side
@@ -232,6 +236,8 @@ struct dgc_mesh {
     tab32.release();
     tcblob.release();
     tcblob16.release();
+    tc3chunks.release();
+    fw3.release();
     wcoef.release();
     trA.release();
     trB.release();
@@ -346,8 +352,10 @@ bool mesh_tc(const dgc_mesh* m) {
 dgc_status check_prec(const dgc_mesh* m, dgc_prec prec) {
   if (prec == DGC_FP64 || prec == DGC_FP32) return DGC_OK;
   if (is_tc(prec)) {
+    if (mesh_tc(m) && m->s.D == 3 && prec == DGC_TF32X3)
+      return fail(DGC_ERR_UNSUPPORTED, "DGC_TF32X3 is available for triangles; tetrahedra take DGC_BF16X3");
     if (mesh_tc(m)) return DGC_OK;
-    return fail(DGC_ERR_UNSUPPORTED, "%s is available for affine triangles with k <= 4 (dim %d, k %d%s)",
+    return fail(DGC_ERR_UNSUPPORTED, "%s is available for affine simplices with k <= 4 (dim %d, k %d%s)",
                 prec == DGC_TF32X3 ? "DGC_TF32X3" : "DGC_BF16X3", m->s.D, m->s.K,
                 m->quad ? ", parallelograms" : (m->hex ? ", parallelepipeds" : (m->Ec ? ", curved elements" : "")));
   }
@@ -355,6 +363,29 @@ dgc_status check_prec(const dgc_mesh* m, dgc_prec prec) {
 }
 
 dgc_status ensure_tc_scratch(dgc_mesh* m) {
+  if (m->s.D == 3) {
+    cudaError_t perr = dgc::launch_stage_tc3(m->s.K, nullptr, nullptr);
+    if (perr != cudaSuccess)
+      return fail(DGC_ERR_CUDA, "tensor-core stage setup failed: %s", cudaGetErrorString(perr));
+    const size_t nt = dgc::tc3_rows_len(m->s.K, m->E), nr = dgc::tc3_tr_len(m->s.K, m->E);
+    const size_t nw = dgc::tc3_fw_len(m->s.K, m->E);
+    // rows the kernels never write (padding rows, elements past E) must read as zero
+    if (m->wcoef.n < nt) {
+      DGC_CUDA(m->wcoef.alloc(nt));
+      DGC_CUDA(cudaMemset(m->wcoef.ptr, 0, nt * sizeof(float)));
+    }
+    if (m->fw3.n < nw) {
+      DGC_CUDA(m->fw3.alloc(nw));
+      DGC_CUDA(cudaMemset(m->fw3.ptr, 0, nw * sizeof(float)));
+    }
+    DGC_CUDA(m->ts0.alloc(nt));
+    DGC_CUDA(m->tsf.alloc(nt));
+    DGC_CUDA(m->d1.alloc(nt));
+    DGC_CUDA(m->d2.alloc(nt));
+    DGC_CUDA(m->trA.alloc(nr));
+    DGC_CUDA(m->trB.alloc(nr));
+    return DGC_OK;
+  }
   for (int P = 0; P < 2; ++P) {
     cudaError_t perr = dgc::launch_stage_tc(m->s.D, m->s.K, P, nullptr, nullptr);
     if (perr != cudaSuccess)
@@ -394,7 +425,12 @@ dgc_status launch_stage_tc(dgc_mesh* m, dgc_prec prec, int mode, const float* di
   a.p_lo = (float)(p - (double)a.p_hi);
   a.q_hi = (float)q;
   a.q_lo = (float)(q - (double)a.q_hi);
-  cudaError_t err = dgc::launch_stage_tc(m->s.D, m->s.K, P, &a, st);
+  if (m->s.D == 3) {
+    a.blob = reinterpret_cast<const float*>(m->tc3chunks.ptr);
+    a.ftab = m->tcblob.ptr;
+    a.fw3 = m->fw3.ptr;
+  }
+  cudaError_t err = m->s.D == 3 ? dgc::launch_stage_tc3(m->s.K, &a, st) : dgc::launch_stage_tc(m->s.D, m->s.K, P, &a, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed: %s", cudaGetErrorString(err));
   return DGC_OK;
 }
@@ -429,13 +465,16 @@ dgc_status launch_rich_tc(dgc_mesh* m, dgc_prec prec, double tau, double ds, cud
 }
 
 dgc_status tc_transpose_in(dgc_mesh* m, const double* v, float* tr, cudaStream_t st) {
-  cudaError_t err = dgc::launch_tsoa_in(m->s.D, m->s.K, v, m->ts0.ptr, m->tsf.ptr, tr, m->tcblob.ptr, m->E, st);
+  cudaError_t err = m->s.D == 3
+                        ? dgc::launch_tc3_in(m->s.K, v, m->ts0.ptr, m->tsf.ptr, tr, m->tcblob.ptr, m->E, st)
+                        : dgc::launch_tsoa_in(m->s.D, m->s.K, v, m->ts0.ptr, m->tsf.ptr, tr, m->tcblob.ptr, m->E, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "layout transpose failed: %s", cudaGetErrorString(err));
   return DGC_OK;
 }
 
 dgc_status tc_transpose_out(dgc_mesh* m, const double* vt, double* v, cudaStream_t st) {
-  cudaError_t err = dgc::launch_tsoa_out(m->s.D, m->s.K, vt, v, m->E, st);
+  cudaError_t err = m->s.D == 3 ? dgc::launch_tc3_out(m->s.K, vt, v, m->E, st)
+                                : dgc::launch_tsoa_out(m->s.D, m->s.K, vt, v, m->E, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "layout transpose failed: %s", cudaGetErrorString(err));
   return DGC_OK;
 }
@@ -501,7 +540,9 @@ dgc_status stage(dgc_mesh* m, dgc_prec prec, const double* vin, const double* vn
 // frozen-wind data for the chosen precision
 dgc_status prepare_wind(dgc_mesh* m, dgc_prec prec, const double* wind, cudaStream_t st) {
   cudaError_t err;
-  if (is_tc(prec)) {
+  if (is_tc(prec) && m->s.D == 3) {
+    err = dgc::launch_wind_tc3(m->view(), wind, m->wcoef.ptr, m->fw3.ptr, st);
+  } else if (is_tc(prec)) {
     err = dgc::launch_wind_coeffs(m->view(), wind, m->wcoef.ptr, dgc::tc_nk(m->s.D, m->s.K), st);
   } else {
     const bool fp32 = prec == DGC_FP32;
@@ -612,8 +653,9 @@ dgc_status rich_build(dgc_mesh* m, const double* wind, const double* g, double* 
   if (!m->body_stream) DGC_CUDA(cudaStreamCreateWithFlags(&m->body_stream, cudaStreamNonBlocking));
   cudaStream_t cs = m->capture_stream, bs = m->body_stream;
   const long n = (long)m->E * m->s.D * m->s.N;
-  // tensor-core precisions: the iteration stays in the tile-blocked layout, fused into the stage kernel
-  const bool tc = is_tc(prec);
+  // tensor-core precisions on triangles: the iteration stays in the tile-blocked layout, fused into
+  // the stage kernel (tetrahedra take the separate kernels around the tensor-core operator)
+  const bool tc = is_tc(prec) && m->s.D == 2;
   const int ntiles = (m->E + 127) / 128;
   DGC_CUDA(begin_capture(cs));
   cudaGraph_t graph = nullptr;
@@ -790,7 +832,10 @@ dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int 
             up(m->tab32.upload(stage_blob<float>(t))) && up(m->status.alloc(1)) &&
             up(cudaMemset(m->status.ptr, 0, sizeof(int))) &&
             (!dgc::tc_supported(dim, k) ||
-             (up(m->tcblob.upload(dgc::tc_blob(dim, k, 0, t))) && up(m->tcblob16.upload(dgc::tc_blob(dim, k, 1, t)))));
+             (dim == 2 ? (up(m->tcblob.upload(dgc::tc_blob(dim, k, 0, t))) &&
+                          up(m->tcblob16.upload(dgc::tc_blob(dim, k, 1, t))))
+                       : (up(m->tcblob.upload(dgc::tc3_ftab(k, t))) &&
+                          up(m->tc3chunks.upload(dgc::tc3_chunks(k, t))))));
   if (!ok) {
     cudaError_t err = cudaGetLastError();
     m->release_all();
@@ -1226,7 +1271,7 @@ dgc_status dgc_richardson(dgc_mesh* mesh, const double* wind_hdiv, const double*
   DGC_CUDA(mesh->rop.alloc(n));
   DGC_CUDA(mesh->partials.alloc(std::max<size_t>((size_t)dgc::rich_blocks((long)n), ((size_t)mesh->E + 127) / 128)));
   DGC_CUDA(mesh->rstate.alloc(2));
-  if (is_tc(prec)) {
+  if (is_tc(prec) && mesh->s.D == 2) {
     const size_t nt = dgc::tc_tsoa_len(mesh->s.D, mesh->s.K, mesh->E);
     DGC_CUDA(mesh->ts1.alloc(nt));
     DGC_CUDA(mesh->tsg.alloc(nt));
@@ -1260,7 +1305,7 @@ dgc_status dgc_autotune(dgc_mesh* mesh, const double* wind_hdiv, dgc_prec prec, 
   if (!wind_hdiv) return fail(DGC_ERR_ARG, "wind_hdiv is NULL");
   if (reps < 1 || reps > 1000) return fail(DGC_ERR_ARG, "reps must lie in 1..1000 (got %d)", reps);
   if (block_out) *block_out = 0;
-  if (is_tc(prec)) return DGC_OK;   // the tensor-core kernel has one tile shape (128 x 288)
+  if (is_tc(prec)) return DGC_OK;   // the tensor-core kernels have one tile shape each
   if (mesh->quad || mesh->hex) return DGC_OK;   // the tensor-product kernels have one block shape (128)
   const bool fp32 = prec == DGC_FP32;
   const size_t n = (size_t)mesh->E * mesh->s.D * mesh->s.N;
@@ -1441,8 +1486,9 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
     if (nsteps[i] < 0) return fail(DGC_ERR_ARG, "instance %d: nsteps must be >= 0", i);
     for (int j = 0; j < i; ++j)
       if (meshes[j] == m) return fail(DGC_ERR_ARG, "instances %d and %d share a mesh handle (scratch)", j, i);
-    // the tensor-core path covers triangles k <= 4; other orders run their stages in FP32
-    pr[i] = (is_tc(prec) && !mesh_tc(m)) ? DGC_FP32 : prec;
+    // the tensor-core path covers affine simplices k <= 4 (tetrahedra in BF16x3 only);
+    // other instances run their stages in FP32
+    pr[i] = (is_tc(prec) && (!mesh_tc(m) || (m->s.D == 3 && prec == DGC_TF32X3))) ? DGC_FP32 : prec;
     if (dgc_status rc = ensure_prec_scratch(m, pr[i])) return rc;
     const size_t n = (size_t)m->E * m->s.D * m->s.N;
     DGC_CUDA(m->stage1.alloc(n));

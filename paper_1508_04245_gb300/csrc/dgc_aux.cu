@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "dgc_kernels.h"
+#include "dgc_tc3_layout.h"
 
 namespace dgc {
 namespace {
@@ -152,6 +153,38 @@ __global__ void wind_coeffs_kernel(DevMesh m, const double* __restrict__ u, floa
   float* wt = wc + (long)(e >> 7) * s.D * nk * 128 + (e & 127);
   for (int a = 0; a < s.D; ++a)
     for (int i = 0; i < nk; ++i) wt[(long)(a * nk + i) * 128] = i < s.N ? (float)(inv * uc[a * s.N + i]) : 0.f;
+}
+
+// tetrahedral tensor-core path: the wind on the vector Dubiner basis scaled by
+// 1/det J in the row layout (component c of element e in row tc3_row, tile of 40
+// elements, [tile][i][128]) and the frozen reference flux at the facet points,
+// (1/det J) w^f_q (u^ . -grad lambda_f), tile-blocked [tile][f][q][40]
+__global__ void wind_tc3_kernel(DevMesh m, const double* __restrict__ u, float* __restrict__ wc3,
+                                float* __restrict__ fw3) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const Sizes& s = m.s;
+  const int N = s.N;
+  double ut[MAXW], uc[MAXW];
+  gather_local(m, e, u, ut);
+  bdm_to_dubiner(m, ut, uc);
+  const double inv = 1.0 / m.detJ[e];
+  const int tile = e / 40, el = e % 40;
+  for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < N; ++i) wc3[((size_t)tile * N + i) * 128 + tc3_row(el, c)] = (float)(inv * uc[c * N + i]);
+  float* fb = fw3 + (size_t)tile * s.NF * s.QF * 40 + el;
+  for (int f = 0; f < s.NF; ++f)
+    for (int q = 0; q < s.QF; ++q) {
+      double acc = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double g = ref_dir(m, f, a);
+        if (g == 0.0) continue;
+        double ua = 0.0;
+        for (int i = 0; i < N; ++i) ua += m.Bf[(long)(f * s.QF + q) * N + i] * uc[a * N + i];
+        acc += g * ua;
+      }
+      fb[(size_t)(f * s.QF + q) * 40] = (float)(inv * m.wf[q] * acc);
+    }
 }
 
 // w_{c,i} = (1/det J) sum_a J[c][a] uc[a][i]   (= (1/|det J|) int_T u_c psi_i)
@@ -630,6 +663,12 @@ cudaError_t launch_wind_prep(const DevMesh& m, const double* u, void* Uw, void* 
     wind_prep_kernel<float><<<grid_for(m.E), BLOCK, 0, s>>>(m, u, (float*)Uw, (float*)Fw);
   else
     wind_prep_kernel<double><<<grid_for(m.E), BLOCK, 0, s>>>(m, u, (double*)Uw, (double*)Fw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wind_tc3(const DevMesh& m, const double* u, float* wc3, float* fw3, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  wind_tc3_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, u, wc3, fw3);
   return cudaGetLastError();
 }
 

@@ -70,8 +70,24 @@ cudaError_t launch_stage_hex(int K, bool fp32, const StageArgs* a, const signed 
 // kernel's constant-memory slot (synchronous; call before any stream capture)
 cudaError_t quad_tables_to_constant(int K, const std::vector<double>& tab);
 
-// tensor-core stage kernel (triangles, k <= 4); a == nullptr prepares the kernel
+// tensor-core stage kernels (triangles and tetrahedra, k <= 4); a == nullptr prepares the kernel
 bool tc_supported(int D, int K);
+// the three BF16 pieces (round to nearest even) of x: x = p0 + p1 + p2 to about 2^-24 |x|
+void bf16x3_pieces(double x, uint16_t* p);
+// tetrahedra: the BF16 table chunks (GEMM A basis, GEMM B gradients) as bytes,
+// the FP32 facet tables, the launch and the row-layout transposes
+std::vector<unsigned char> tc3_chunks(int K, const Tables& t);
+std::vector<float> tc3_ftab(int K, const Tables& t);
+cudaError_t launch_stage_tc3(int K, const StageTcArgs* a, cudaStream_t s);
+size_t tc3_rows_len(int K, int E);    // one state vector in the row layout
+size_t tc3_tr_len(int K, int E);      // its facet traces
+size_t tc3_fw_len(int K, int E);      // the tile-blocked facet flux
+cudaError_t launch_tc3_in(int K, const double* v, double* vt, float* vft, float* tr, const float* ftab, int E,
+                          cudaStream_t s);
+cudaError_t launch_tc3_out(int K, const double* vt, double* v, int E, cudaStream_t s);
+// wind rows [tile][i][128] (component c of element e in row tc3_row, scaled by
+// 1/det J) and the facet flux [tile][f][q][40] of the frozen wind
+cudaError_t launch_wind_tc3(const DevMesh& m, const double* u_hdiv, float* wc3, float* fw3, cudaStream_t s);
 int tc_nk(int D, int K);
 // P: 0 = TF32 head/tail (3 products), 1 = BF16 three pieces (6 products)
 std::vector<float> tc_blob(int D, int K, int P, const Tables& t);

@@ -150,6 +150,13 @@ cudaError_t tsoa_out_sel_t(const double* vt0, const double* vt1, const double* c
 
 }  // namespace
 
+void bf16x3_pieces(double x, uint16_t* p) {
+  p[0] = bf16_rn(x);
+  const double r = x - bf16_value(p[0]);
+  p[1] = bf16_rn(r);
+  p[2] = bf16_rn(r - bf16_value(p[1]));
+}
+
 cudaError_t launch_tsoa_in64(int D, int K, const double* v, double* vt, int E, cudaStream_t s) {
   if (D != 2) return cudaErrorInvalidValue;
   switch (K) {
@@ -205,7 +212,7 @@ cudaError_t launch_tsoa_out(int D, int K, const double* vt, double* v, int E, cu
   }
 }
 
-bool tc_supported(int D, int K) { return D == 2 && K >= 1 && K <= 4; }
+bool tc_supported(int D, int K) { return (D == 2 || D == 3) && K >= 1 && K <= 4; }
 
 int tc_nk(int D, int K) {
   if (D != 2) return 0;

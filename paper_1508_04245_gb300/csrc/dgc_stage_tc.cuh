@@ -85,6 +85,11 @@ struct StageTcArgs {
   const double* detJ;   // [E]
   double tau, ds;
   double* partials;     // [tiles]
+  // tetrahedra (stage_tc3_kernel): the frozen facet flux in tile blocks
+  // [tile][f][q][40] and the FP32 facet tables (Ef, Qt); blob then holds the
+  // BF16 table chunks and every state vector the row layout of TcLayout3D
+  const float* fw3;
+  const float* ftab;
 };
 
 namespace tcimpl {

@@ -1,0 +1,103 @@
+// Compile-time layout of the tensor-core stage kernel for tetrahedra (dim 3).
+//
+// GEMM rows are (element, velocity component) pairs: a tile holds 40
+// elements, rows 32 g + 3 s + c for element 10 g + s (g = 0..3, s = 0..9) and
+// component c; rows 32 g + 30 and 32 g + 31 are padding.  The three rows of an
+// element sit in one warp, so the wind components another row holds come by
+// warp shuffles.  Each row carries one field of the state (its component) and
+// one of the wind (the same component), so every tcgen05 operand is one field:
+//
+//   GEMM A (per chunk of 16 volume points, A from TMEM, B = basis table):
+//     X.w[r, q] = sum_j A_s[r, j] Bv[q, j]        state component c at xi_q
+//     X.u[r, q] = sum_j A_w[r, j] Bv[q, j]        wind component c / det J
+//   GEMM B (the volume test contraction, A = products from TMEM), per chunk:
+//     R_j[r, i] = sum_{d, q in chunk j} P[r, (d, q)] G[(d, q), i],  R = sum_j R_j,
+//     P[r, (d, q)] = u_d(xi_q) w_c(xi_q),  G[(d, q), i] = -w_q d_d psi^_i(xi_q)
+//
+// Every operand is split exactly into three BF16 pieces (kind::f16, six
+// products, FP32 accumulation).  The tables of a chunk (Bv and the three G
+// blocks, all pieces) are one contiguous blob bulk-copied into a ring of
+// shared-memory slots; the facet terms run on CUDA cores in FP32 from the
+// facet traces of the stage input and the frozen facet flux of the wind.
+#pragma once
+
+namespace dgc {
+
+template <int K>
+struct TcLayout3D {
+  static constexpr int pad(int n, int m) { return (n + m - 1) / m * m; }
+  static constexpr int D = 3;
+  static constexpr int NF = 4;
+  static constexpr int N = (K + 1) * (K + 2) * (K + 3) / 6;
+  static constexpr int NFM = (K + 1) * (K + 2) / 2;
+  static constexpr int NQ1V = (3 * K - 1) / 2 + 1;
+  static constexpr int QV = NQ1V * NQ1V * NQ1V;
+  static constexpr int NQ1F = (3 * K) / 2 + 1;
+  static constexpr int QF = NQ1F * NQ1F;
+  static constexpr int EPT = 40;                       // elements per tile
+  static constexpr int NK = pad(N, 16);                // K of GEMM A
+  static constexpr int NR = pad(N, 16);                // N of GEMM B
+  static constexpr int QC = 16;                        // volume points per chunk
+  static constexpr int NCH = (QV + QC - 1) / QC;       // chunks per tile
+
+  // TMEM columns (32-bit); a BF16 piece of a K = NK operand row takes NK / 2
+  static constexpr int NKC = NK / 2;
+  static constexpr int cAs = 0;                        // state operand, pieces h, m, l
+  static constexpr int cAw = 3 * NKC;                  // wind operand
+  static constexpr int cX = pad(6 * NKC, 16);          // two buffers: [w (16) | u (16)]
+  static constexpr int XCOLS = 32;
+  static constexpr int cP = cX + 2 * XCOLS;            // two buffers: [d][piece][8 columns]
+  static constexpr int PCOLS = 72;
+  // GEMM B accumulates each chunk into a fresh partial (two buffers): the tensor
+  // cores' FP32 accumulation truncates, so a single accumulator over all chunks
+  // would gather a bias of one unit in the last place per MMA; the partials are
+  // added on CUDA cores (round to nearest) and the tile's residual handed to
+  // the facet warps in cRf
+  static constexpr int cRp = cP + 2 * PCOLS;           // two chunk partials of NR columns
+  static constexpr int cRf = cRp + 2 * NR;             // the tile's residual
+  static constexpr int TMEM_USED = cRf + NR;
+  static constexpr int TMEM_COLS = 512;
+  static_assert(TMEM_USED <= TMEM_COLS, "tensor memory");
+
+  // chunk blob (bytes): [Bv pieces: 3 x (16 x NK)] [G: d x piece x (NR x 16)], BF16
+  static constexpr int szBA = 16 * NK * 2;             // one piece of the GEMM A table chunk
+  static constexpr int szBG = NR * 16 * 2;             // one piece of one G block
+  static constexpr int oBA = 0;
+  static constexpr int oBG = 3 * szBA;
+  static constexpr int CH_BYTES = oBG + 9 * szBG;
+  static constexpr unsigned SBO_A = (NK / 8) * 128;    // 8-row groups of the GEMM A table
+  static constexpr unsigned SBO_G = 256;               // 8-row groups of a G block (K = 16)
+  static constexpr bool RESIDENT = NCH <= 4;           // every chunk kept, else a ring
+  static constexpr int SLOTS = RESIDENT ? NCH : 4;
+
+  // FP32 tables of the facet terms: Ef [NF][NFM][NP4], Qt [QF][NFM4]
+  static constexpr int NP4 = pad(N, 4);
+  static constexpr int NFM4 = pad(NFM, 4);
+  static constexpr int oEf = 0;
+  static constexpr int oQt = NF * NFM * NP4;
+  static constexpr int FWT = pad(oQt + QF * NFM4, 4);  // floats
+
+  // frozen facet flux of a tile: [f][q][EPT] floats
+  static constexpr int FWS = NF * QF * EPT;
+
+  // shared memory (bytes)
+  static constexpr int oRing = 0;
+  static constexpr int oFwt = oRing + SLOTS * CH_BYTES;
+  static constexpr int oFws = oFwt + FWT * 4;          // two tile buffers
+  static constexpr int oPhi = oFws + 2 * FWS * 4;      // [f][m][128] facet projections
+  static constexpr int oXs = oPhi + NF * NFM * 128 * 4;  // [i][128] stage output (for its traces)
+  static constexpr int oBar = oXs + N * 128 * 4;
+  static constexpr int NBAR = 40;
+  static constexpr int SMEM_BYTES = oBar + NBAR * 8 + 64;
+};
+
+// tile-blocked row layouts of the tetrahedral tensor-core path
+__host__ __device__ __forceinline__ int tc3_row(int el, int c) { return (el / 10) * 32 + (el % 10) * 3 + c; }
+__host__ __device__ __forceinline__ size_t tc3_index(int tile, int i, int r, int N) {
+  return ((size_t)tile * N + i) * 128 + r;
+}
+__host__ __device__ __forceinline__ size_t tc3_tr_index(int tile, int f, int m, int r, int NFM) {
+  return (((size_t)tile * 4 + f) * NFM + m) * 128 + r;
+}
+
+}  // namespace dgc

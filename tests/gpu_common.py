@@ -25,9 +25,10 @@ def tol_hdiv_chain(dim, k, prec):
     return max(1e-12, 16 * np.finfo(np.float64).eps / 2 * cb)
 
 
-def tc_ok(dim, k):
-    """The tensor-core paths (tf32x3, bf16x3) cover triangles with k <= 4."""
-    return dim == 2 and k <= 4
+def tc_ok(dim, k, prec="bf16x3"):
+    """The tensor-core paths cover affine simplices with k <= 4: triangles in
+    tf32x3 and bf16x3, tetrahedra in bf16x3."""
+    return k <= 4 and (dim == 2 or prec == "bf16x3")
 
 
 def maxrel(got, ref) -> float:

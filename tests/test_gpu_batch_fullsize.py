@@ -16,7 +16,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_common import TOL, make_case, maxrel, oracle_ds, oracle_state
+from gpu_common import TOL, make_case, maxrel, oracle_ds, oracle_state, tc_ok
 from oracle import dg as ODG
 from oracle import hdiv as OH
 from oracle import mesh as OM
@@ -61,7 +61,7 @@ def test_batch_equals_single_instances(prec):
     singles = []
     for (m, w, v0), d, n in zip(cases, ds, nsteps):
         x = v0.clone()
-        m.rk_substeps(w, x, d, n, 3, prec if (prec == "fp64" or (m.dim == 2 and m.k <= 4)) else "fp32")
+        m.rk_substeps(w, x, d, n, 3, prec if (prec == "fp64" or tc_ok(m.dim, m.k, prec)) else "fp32")
         singles.append(host(x).copy())
     states = [v0.clone() for _, _, v0 in cases]
     dgconv.batch_rk_substeps([c[0] for c in cases], [c[1] for c in cases], states, ds, nsteps, 3, prec)

@@ -76,8 +76,8 @@ def test_transfer_T(cases, dim, k):
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("dim,k", ORDERS)
 def test_conv_apply(cases, dim, k, prec):
-    if prec in TC_PRECS and not tc_ok(dim, k):
-        pytest.skip("tensor-core path covers triangles with k <= 4")
+    if prec in TC_PRECS and not tc_ok(dim, k, prec):
+        pytest.skip("tensor-core paths: triangles k <= 4, tetrahedra k <= 4 in bf16x3")
     verts, elems, pot, om, wind, gm = cases(dim, k)
     w = oracle_state(om, k)
     ref = ODG.ConvectionOracle(om, k, wind).apply(w)
@@ -90,8 +90,8 @@ def test_conv_apply(cases, dim, k, prec):
 @pytest.mark.parametrize("dim,k,scheme", [(2, 1, 3), (2, 2, 2), (2, 3, 3), (2, 4, 3), (2, 6, 3), (3, 1, 2), (3, 3, 3),
                                           (3, 4, 3)])
 def test_rk_substeps(cases, dim, k, scheme, prec):
-    if prec in TC_PRECS and not tc_ok(dim, k):
-        pytest.skip("tensor-core path covers triangles with k <= 4")
+    if prec in TC_PRECS and not tc_ok(dim, k, prec):
+        pytest.skip("tensor-core paths: triangles k <= 4, tetrahedra k <= 4 in bf16x3")
     verts, elems, pot, om, wind, gm = cases(dim, k)
     v0 = oracle_state(om, k, seed=5)
     ds = oracle_ds(om, k, wind)
@@ -118,12 +118,16 @@ def test_rk_graph_replay_matches_fresh_launch(cases):
 
 
 def test_tc_unsupported_orders_are_rejected(cases):
+    """k = 5 has no tensor-core path in either dimension; tetrahedra take bf16x3 only."""
+    for dim, k in ((2, 5), (3, 5)):
+        verts, elems, pot, om, wind, gm = cases(dim, k)
+        w = cu(oracle_state(om, k))
+        for prec in TC_PRECS:
+            with pytest.raises(dgconv.DgcError):
+                gm.conv_apply(cu(wind), w, prec=prec)
     verts, elems, pot, om, wind, gm = cases(3, 2)
-    w = cu(oracle_state(om, 2))
     with pytest.raises(dgconv.DgcError):
-        gm.conv_apply(cu(wind), w, prec="tf32x3")
-    with pytest.raises(dgconv.DgcError):
-        gm.conv_apply(cu(wind), w, prec="bf16x3")
+        gm.conv_apply(cu(wind), cu(oracle_state(om, 2)), prec="tf32x3")
 
 
 def test_mass_and_geometry(cases):
