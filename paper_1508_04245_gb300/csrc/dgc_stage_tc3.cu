@@ -66,7 +66,7 @@ cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
     if (sms <= 0) sms = 1;
   }
   const int grid = tiles < sms ? tiles : sms;
-  stage_tc3_kernel<K><<<grid, 544, L::SMEM_BYTES, s>>>(*a);
+  stage_tc3_kernel<K><<<grid, 640, L::SMEM_BYTES, s>>>(*a);
   return cudaGetLastError();
 }
 
@@ -102,7 +102,7 @@ struct Lens {
     using L = TcLayout3D<K>;
     const size_t tiles = ((size_t)E + L::EPT - 1) / L::EPT;
     if (which == 0) return tiles * L::N * 128;
-    if (which == 1) return tiles * L::NF * L::NFM * 128;
+    if (which == 1) return tiles * L::NF * 128 * L::NFM4;
     return tiles * L::FWS;
   }
 };

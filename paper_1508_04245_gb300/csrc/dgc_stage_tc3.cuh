@@ -11,7 +11,7 @@
 //   reference flux (1/det J) w^f_q (u^ . -grad lambda_f), w^ the own trace where
 //   Fw >= 0 and the neighbour's otherwise (zero on inflow boundary facets).
 //
-// One persistent CTA per SM, 544 threads in three roles that work on
+// One persistent CTA per SM, 640 threads in four roles that work on
 // different tiles at the same time:
 //   volume warps 0-7 (two threads per GEMM row): write the tile's state and
 //     wind operands into TMEM, then per chunk of 16 volume points read the
@@ -24,8 +24,12 @@
 //     while its volume part runs, then the epilogue once GEMM B has finished:
 //     the increment, in the last stage of a substep the FP64 accumulation, and
 //     the facet traces of the stage output;
-//   warp 16: one thread issues every MMA and bulk copy (table chunks through
-//     a ring of shared-memory slots, the tile's facet flux block).
+//   warp 16: the bulk copies (table chunks through a ring of shared-memory
+//     slots, the tiles' facet flux blocks, L2 prefetch of the next tile);
+//   warps 17-19: one thread each issues the MMAs of GEMM A (even, odd chunks)
+//     and of GEMM B -- a single issuing thread sustains only about one
+//     tcgen05.mma per 50 cycles, so the independent chains of the two chunk
+//     parities of GEMM A are issued from separate warps.
 // Two TMEM buffers each for the GEMM A results, the GEMM B operands and the
 // GEMM B chunk partials (summed by the volume warps, round to nearest) let the
 // volume warps run a tile ahead of the facet warps.  Every
@@ -64,7 +68,7 @@ __device__ __forceinline__ void put3_tmem(uint32_t taddr, const float* x) {
 }  // namespace tc3impl
 
 template <int K>
-__global__ void __launch_bounds__(544, 1) stage_tc3_kernel(StageTcArgs a) {
+__global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
   using L = TcLayout3D<K>;
   constexpr int N = L::N, NFM = L::NFM, QF = L::QF, NK = L::NK, NKC = L::NKC, NR = L::NR, NCH = L::NCH;
   constexpr int NP4 = L::NP4, NFM4 = L::NFM4, EPT = L::EPT, SLOTS = L::SLOTS;
@@ -103,10 +107,10 @@ __global__ void __launch_bounds__(544, 1) stage_tc3_kernel(StageTcArgs a) {
   if (t == 0) {
     for (int i = 0; i < 4; ++i) {
       tc::mbar_init(bar_tab + i, 1);
-      tc::mbar_init(bar_tfree + i, 1);
+      tc::mbar_init(bar_tfree + i, 2);   // GEMM A and GEMM B of the slot's chunk
     }
     tc::mbar_init(bar_ops, 8);
-    tc::mbar_init(bar_afree, 1);
+    tc::mbar_init(bar_afree, NCH >= 2 ? 2 : 1);   // both GEMM A issuers, when both have chunks in a tile
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(bar_x + i, 1);
       tc::mbar_init(bar_xfree + i, 8);
@@ -118,7 +122,7 @@ __global__ void __launch_bounds__(544, 1) stage_tc3_kernel(StageTcArgs a) {
       tc::mbar_init(bar_fwsfree + i, 8);
     }
     tc::mbar_init(bar_ftab, 1);
-    tc::mbar_init(bar_fin, 1);
+    tc::mbar_init(bar_fin, 3);   // the three MMA-issuing threads
     *abort_flag = 0;
     *fw_stop = 0;
     tc::mbar_fence_init();
@@ -132,164 +136,161 @@ __global__ void __launch_bounds__(544, 1) stage_tc3_kernel(StageTcArgs a) {
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
 
-  if (warp == 16) {
-    // ============================ issuer ======================================
+  if (warp >= 16) {
+    // ============ warp 16: bulk copies; 17, 18: GEMM A; 19: GEMM B ===============
+    // (one tcgen05.mma issuing thread sustains one MMA per ~50 cycles, so the GEMM A
+    // MMAs of even and odd chunks, which use separate TMEM buffers, come from two
+    // warps; GEMM B has half as many MMAs)
     if (lane == 0) {
+      const int role = warp - 16;
       const unsigned char* chunks = reinterpret_cast<const unsigned char*>(a.blob);
       const uint32_t ring_s = tc::smem_u32(ring);
       const int total = nmy * NCH;   // chunk uses of this CTA
-      int ld = 0, lw = 0;            // table loads issued / waited (ring)
-      int fws_ld[2] = {0, 0};        // flux block loads issued per buffer
       bool ok = true;
       auto fail = [&]() {
         ok = false;
         *abort_flag = 1;
       };
-      auto load_chunk = [&](int Lx) {   // table chunk use Lx into its slot
-        const int s = L::RESIDENT ? Lx : Lx % SLOTS;
-        tc::mbar_arrive_expect_tx(bar_tab + s, L::CH_BYTES);
-        tc::bulk_g2s(ring + (size_t)s * L::CH_BYTES, chunks + (size_t)(Lx % NCH) * L::CH_BYTES, L::CH_BYTES,
-                     bar_tab + s);
+      auto slot = [&](int g) { return L::RESIDENT ? g % NCH : g % SLOTS; };
+      auto tab_ready = [&](int g) {   // the table chunk of use g has landed
+        return tc::mbar_wait(bar_tab + slot(g), L::RESIDENT ? 0u : (uint32_t)((g / SLOTS) & 1));
       };
-      auto load_fws = [&](int itl) {
-        const int b = itl & 1;
-        const int tile = blockIdx.x + itl * gridDim.x;
-        tc::mbar_arrive_expect_tx(bar_fws + b, L::FWS * 4);
-        tc::bulk_g2s(fws + b * L::FWS, a.fw3 + (size_t)tile * L::FWS, L::FWS * 4, bar_fws + b);
-        ++fws_ld[b];
-      };
-      auto prefetch_tile = [&](int itl) {   // a tile's streamed inputs toward L2
-        const int tile = blockIdx.x + itl * gridDim.x;
-        const uint32_t blk = (uint32_t)N * 128 * 4;
-        tc::bulk_prefetch_l2(vf_in + (size_t)tile * N * 128, blk);
-        tc::bulk_prefetch_l2(a.wcoef + (size_t)tile * N * 128, blk);
-        if (a.din) tc::bulk_prefetch_l2(a.din + (size_t)tile * N * 128, blk);
-        tc::bulk_prefetch_l2(tr_in + (size_t)tile * L::NF * NFM * 128, (uint32_t)L::NF * NFM * 128 * 4);
-        if (a.mode == 1) tc::bulk_prefetch_l2(a.v + (size_t)tile * N * 128, 2 * blk);
-      };
-      tc::mbar_arrive_expect_tx(bar_ftab, L::FWT * 4);
-      tc::bulk_g2s(const_cast<float*>(fwt), a.ftab, L::FWT * 4, bar_ftab);
-      if (nmy > 0) {
-        if (L::RESIDENT) {
-          for (int j = 0; j < NCH; ++j) load_chunk(j);
-          ld = NCH;
-        } else {
-          for (; ld < 2 && ld < total; ++ld) load_chunk(ld);
-        }
-        load_fws(0);
-        prefetch_tile(0);
-        if (nmy > 1) load_fws(1);
-      }
-      const uint32_t idA = tc::idesc_bf16(128, 16);
-      const uint32_t idB = tc::idesc_bf16(128, NR);
       // products of pieces (A piece, B piece), smallest first (see the triangle kernel)
       constexpr int PA[6] = {1, 2, 0, 1, 0, 0}, PB[6] = {1, 0, 2, 0, 1, 0};
-
-      auto gemm_b = [&](int gg) {   // the volume test contraction of chunk use gg, a fresh partial
-        const int jj = gg % NCH, b = gg & 1;
-        if (!tc::mbar_wait(bar_p + b, (gg >> 1) & 1)) return fail();
-        tc::fence_after_sync();
-        const int s = L::RESIDENT ? jj : gg % SLOTS;
-        const uint32_t sb = ring_s + (uint32_t)s * L::CH_BYTES + L::oBG;
-#pragma unroll
-        for (int pr = 0; pr < 6; ++pr)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const uint32_t at = tbase + L::cP + b * L::PCOLS + (d * 3 + PA[pr]) * 8;
-            const uint64_t bd = tc::smem_desc(sb + (uint32_t)(d * 3 + PB[pr]) * L::szBG, 128, L::SBO_G);
-            tc::mma_bf16_ts(tbase + L::cRp + b * NR, at, bd, idB, (pr | d) != 0);
-          }
-        tc::mma_commit(bar_pfree + b);
-        if (!L::RESIDENT) tc::mma_commit(bar_tfree + s);
-      };
-
-      for (int it = 0; it < nmy && ok; ++it) {
-        if (it >= 2) {   // the flux block of this tile into the buffer tile it - 2 used
-          if (!tc::mbar_wait(bar_fwsfree + (it & 1), ((it >> 1) - 1) & 1)) {
-            fail();
-            break;
-          }
-          load_fws(it);
+      if (role == 0) {
+        // ---- producer: table chunks through the ring, the tiles' facet flux blocks,
+        //      L2 prefetch of the next tile's streamed inputs ----------------------------
+        int ld = 0;                  // table loads issued
+        int fws_ld[2] = {0, 0};      // flux block loads issued per buffer
+        auto load_chunk = [&](int Lx) {
+          const int s2 = slot(Lx);
+          tc::mbar_arrive_expect_tx(bar_tab + s2, L::CH_BYTES);
+          tc::bulk_g2s(ring + (size_t)s2 * L::CH_BYTES, chunks + (size_t)(Lx % NCH) * L::CH_BYTES, L::CH_BYTES,
+                       bar_tab + s2);
+        };
+        auto load_fws = [&](int itl) {
+          const int b = itl & 1;
+          const int tile = blockIdx.x + itl * gridDim.x;
+          tc::mbar_arrive_expect_tx(bar_fws + b, L::FWS * 4);
+          tc::bulk_g2s(fws + b * L::FWS, a.fw3 + (size_t)tile * L::FWS, L::FWS * 4, bar_fws + b);
+          ++fws_ld[b];
+        };
+        auto prefetch_tile = [&](int itl) {
+          const int tile = blockIdx.x + itl * gridDim.x;
+          const uint32_t blk = (uint32_t)N * 128 * 4;
+          tc::bulk_prefetch_l2(vf_in + (size_t)tile * N * 128, blk);
+          tc::bulk_prefetch_l2(a.wcoef + (size_t)tile * N * 128, blk);
+          if (a.din) tc::bulk_prefetch_l2(a.din + (size_t)tile * N * 128, blk);
+          tc::bulk_prefetch_l2(tr_in + (size_t)tile * L::NF * 128 * NFM4, (uint32_t)L::NF * 128 * NFM4 * 4);
+          if (a.mode == 1) tc::bulk_prefetch_l2(a.v + (size_t)tile * N * 128, 2 * blk);
+        };
+        tc::mbar_arrive_expect_tx(bar_ftab, L::FWT * 4);
+        tc::bulk_g2s(const_cast<float*>(fwt), a.ftab, L::FWT * 4, bar_ftab);
+        if (nmy > 0) {
+          const int first = L::RESIDENT ? NCH : (total < SLOTS ? total : SLOTS);
+          for (; ld < first; ++ld) load_chunk(ld);
+          load_fws(0);
+          if (nmy > 1) load_fws(1);
+          prefetch_tile(0);
         }
-        if (it + 1 < nmy) prefetch_tile(it + 1);
-        if (!tc::mbar_wait(bar_ops, it & 1)) {
-          fail();
-          break;
-        }
-        tc::fence_after_sync();
-        for (int j = 0; j < NCH && ok; ++j) {
-          const int g = it * NCH + j, b = g & 1;
-          const int s = L::RESIDENT ? j : g % SLOTS;
-          if (L::RESIDENT) {
-            if (it == 0 && !tc::mbar_wait(bar_tab + s, 0)) {
+        for (int it = 0; it < nmy && ok; ++it) {
+          if (it >= 2) {   // the flux block of tile it into the buffer tile it - 2 has released
+            if (!tc::mbar_wait(bar_fwsfree + (it & 1), ((it >> 1) - 1) & 1)) {
               fail();
               break;
             }
-          } else {
-            if (!tc::mbar_wait(bar_tab + s, (g / SLOTS) & 1)) {
+            load_fws(it);
+          }
+          if (it + 1 < nmy) prefetch_tile(it + 1);
+          if (!L::RESIDENT) {   // the table chunks up to the end of tile it + 1, each into a freed slot
+            const int upto = (it + 2) * NCH < total ? (it + 2) * NCH : total;
+            for (; ld < upto && ok; ++ld) {
+              if (ld >= SLOTS && !tc::mbar_wait(bar_tfree + ld % SLOTS, ((ld / SLOTS) - 1) & 1)) {
+                fail();
+                break;
+              }
+              load_chunk(ld);
+            }
+          }
+        }
+        // drain: the copies still in flight land before the CTA exits
+        if (L::RESIDENT) {
+          if (nmy > 0)
+            for (int j = 0; j < NCH; ++j) tc::mbar_wait(bar_tab + j, 0);
+        } else {
+          for (int Lx = ld - SLOTS > 0 ? ld - SLOTS : 0; Lx < ld; ++Lx)
+            tc::mbar_wait(bar_tab + Lx % SLOTS, (Lx / SLOTS) & 1);
+        }
+        for (int b = 0; b < 2; ++b)
+          if (fws_ld[b]) tc::mbar_wait(bar_fws + b, (fws_ld[b] - 1) & 1);
+        tc::mbar_wait(bar_ftab, 0);
+      } else if (role <= 2) {
+        // ---- GEMM A of the chunk uses of parity p: state and wind at 16 volume points -----
+        const int p = role - 1;
+        const uint32_t idA = tc::idesc_bf16(128, 16);
+        int cur = -1;   // the tile whose operands this issuer has seen written
+        for (int g = p; g < total && ok; g += 2) {
+          const int it = g / NCH;
+          if (it != cur) {
+            if (!tc::mbar_wait(bar_ops, it & 1)) {
               fail();
               break;
             }
-            lw = g + 1;
+            cur = it;
           }
-          if (g >= 2 && !tc::mbar_wait(bar_xfree + b, ((g >> 1) - 1) & 1)) {
+          if (!tab_ready(g) || (g >= 2 && !tc::mbar_wait(bar_xfree + p, ((g >> 1) - 1) & 1))) {
             fail();
             break;
           }
           tc::fence_after_sync();
-          // ---- GEMM A: state and wind at the chunk's 16 volume points ----------------
-          const uint32_t sa = ring_s + (uint32_t)s * L::CH_BYTES + L::oBA;
+          const uint32_t sa = ring_s + (uint32_t)slot(g) * L::CH_BYTES + L::oBA;
 #pragma unroll 1
           for (int fld = 0; fld < 2; ++fld) {
-            const uint32_t dcol = tbase + L::cX + b * L::XCOLS + fld * 16;
+            const uint32_t dcol = tbase + L::cX + p * L::XCOLS + fld * 16;
             const uint32_t acol = tbase + (fld ? L::cAw : L::cAs);
-            uint32_t acc = 0;
+            const uint64_t bd0 = tc::smem_desc(sa, 128, L::SBO_A);
 #pragma unroll
             for (int pr = 0; pr < 6; ++pr)
 #pragma unroll
-              for (int ks = 0; ks < NK / 16; ++ks) {
-                const uint64_t bd = tc::smem_desc(sa + (uint32_t)PB[pr] * L::szBA + ks * 256, 128, L::SBO_A);
-                tc::mma_bf16_ts(dcol, acol + PA[pr] * NKC + ks * 8, bd, idA, acc);
-                acc = 1;
-              }
+              for (int ks = 0; ks < NK / 16; ++ks)   // the address field of a descriptor is address / 16
+                tc::mma_bf16_ts(dcol, acol + PA[pr] * NKC + ks * 8, bd0 + (uint64_t)((PB[pr] * L::szBA + ks * 256) >> 4),
+                                idA, (pr | ks) != 0);
           }
-          tc::mma_commit(bar_x + b);
-          if (j == NCH - 1) tc::mma_commit(bar_afree);
-          if (j >= 1) {
-            gemm_b(g - 1);
-            if (!ok) break;
-          }
-          // ---- ring: the chunk two uses ahead into the slot GEMM B(g - 2) has freed ------
-          if (!L::RESIDENT && ld < total && ld <= g + 2) {
-            const int s2 = ld % SLOTS;
-            if (ld >= SLOTS && !tc::mbar_wait(bar_tfree + s2, ((ld / SLOTS) - 1) & 1)) {
-              fail();
-              break;
-            }
-            load_chunk(ld);
-            ++ld;
-          }
+          tc::mma_commit(bar_x + p);
+          if (!L::RESIDENT) tc::mma_commit(bar_tfree + slot(g));
+          if (g + 2 >= (it + 1) * NCH) tc::mma_commit(bar_afree);   // this issuer's last chunk of the tile
         }
-        if (ok) gemm_b(it * NCH + NCH - 1);
-      }
-      // ---- drain: every MMA, then every copy still in flight ------------------------
-      tc::mma_commit(bar_fin);
-      tc::mbar_wait(bar_fin, 0);
-      if (L::RESIDENT) {
-        if (nmy > 0)
-          for (int j = 0; j < NCH; ++j) tc::mbar_wait(bar_tab + j, 0);
+        tc::mma_commit(bar_fin);
+        tc::mbar_wait(bar_fin, 0);
       } else {
-        for (int Lx = lw; Lx < ld; ++Lx) tc::mbar_wait(bar_tab + Lx % SLOTS, (Lx / SLOTS) & 1);
+        // ---- GEMM B of every chunk use: the test contraction into a fresh partial ------
+        const uint32_t idB = tc::idesc_bf16(128, NR);
+        for (int g = 0; g < total && ok; ++g) {
+          const int p = g & 1;
+          if (!tab_ready(g) || !tc::mbar_wait(bar_p + p, (g >> 1) & 1)) {
+            fail();
+            break;
+          }
+          tc::fence_after_sync();
+          const uint64_t bd0 = tc::smem_desc(ring_s + (uint32_t)slot(g) * L::CH_BYTES + L::oBG, 128, L::SBO_G);
+#pragma unroll
+          for (int pr = 0; pr < 6; ++pr)
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+              tc::mma_bf16_ts(tbase + L::cRp + p * NR, tbase + L::cP + p * L::PCOLS + (d * 3 + PA[pr]) * 8,
+                              bd0 + (uint64_t)(((d * 3 + PB[pr]) * L::szBG) >> 4), idB, (pr | d) != 0);
+          tc::mma_commit(bar_pfree + p);
+          if (!L::RESIDENT) tc::mma_commit(bar_tfree + slot(g));
+        }
+        tc::mma_commit(bar_fin);
+        tc::mbar_wait(bar_fin, 0);
       }
-      for (int b = 0; b < 2; ++b)
-        if (fws_ld[b]) tc::mbar_wait(bar_fws + b, (fws_ld[b] - 1) & 1);
-      tc::mbar_wait(bar_ftab, 0);
       if (!ok) atomicOr(a.status, 2);
     }
   } else if (warp < 8) {
     // ============================ volume warps ===================================
     const int r = t & 127, h = t >> 7;
-    const int rg = r >> 5, ln = r & 31, sl = ln / 3, c = ln % 3;
+    const int rg = r >> 5, ln = r & 31, sl = ln / 3;
     const uint32_t lb = tbase + ((uint32_t)(rg * 32) << 16);
     constexpr int NRH = NR / 2;                 // residual columns this thread sums
     const uint32_t rcol = (uint32_t)(h * NRH);
@@ -410,7 +411,8 @@ __global__ void __launch_bounds__(544, 1) stage_tc3_kernel(StageTcArgs a) {
     const uint32_t lb = tbase + ((uint32_t)(rg * 32) << 16);
     const float* Ef = fwt + L::oEf;   // [NF][NFM][NP4]
     const float* Qt = fwt + L::oQt;   // [QF][NFM4]
-    constexpr int NH = (N + 1) / 2;   // coefficients per thread in the epilogue
+    // coefficients of this thread in the epilogue: a 4-aligned half, [i0, i0 + NH)
+    constexpr int NH = ((N + 1) / 2 + 3) / 4 * 4;
     const int i0 = h * NH;
     bool ok = tc::mbar_wait(bar_ftab, 0);
     if (!ok) *abort_flag = 1;
@@ -425,126 +427,176 @@ __global__ void __launch_bounds__(544, 1) stage_tc3_kernel(StageTcArgs a) {
       bool w = *abort_flag == 0 && tc::mbar_wait(bar_fws + b, (it >> 1) & 1);
       if (!w) *abort_flag = 1;
       const float* fwb = fws + b * L::FWS;
-      // ---- upwind facet terms of facets 2h, 2h + 1 (CUDA cores, FP32) ----------------
-      float phi[2][NFM];
+      // ---- upwind facet terms of facets 2h, 2h + 1 (CUDA cores, FP32, packed pairs) ------
+      // own and neighbour traces of a facet as pairs of modes (NFM4 / 2 pairs each)
+      constexpr int NP2 = NFM4 / 2;
 #pragma unroll
       for (int ff = 0; ff < 2; ++ff) {
         const int f = 2 * h + ff;
-        float to[NFM], tn[NFM];
-        const int code = valid ? a.nbr[(size_t)e * 4 + f] : -1;
-        const int ne = code >> 2, fn = code & 3;
-        const int nrow = code >= 0 ? tc3_row(ne % EPT, c) : 0;
+        unsigned long long to2[NP2], tn2[NP2];
+        {
+          const int code = valid ? a.nbr[(size_t)e * 4 + f] : -1;
+          const ulonglong2* po = reinterpret_cast<const ulonglong2*>(tr_in + tc3_tr_index(tile, f, 0, r, NFM4));
+          const ulonglong2* pn = reinterpret_cast<const ulonglong2*>(
+              tr_in + tc3_tr_index(code >= 0 ? (code >> 2) / EPT : 0, code & 3, 0,
+                                   code >= 0 ? tc3_row((code >> 2) % EPT, c) : 0, NFM4));
 #pragma unroll
-        for (int m = 0; m < NFM; ++m) {
-          to[m] = valid ? tr_in[tc3_tr_index(tile, f, m, r, NFM)] : 0.f;
-          tn[m] = code >= 0 ? tr_in[tc3_tr_index(ne / EPT, fn, m, nrow, NFM)] : 0.f;
-          phi[ff][m] = 0.f;
+          for (int j = 0; j < NP2 / 2; ++j) {
+            const ulonglong2 x = valid ? po[j] : make_ulonglong2(0ull, 0ull);
+            const ulonglong2 y = code >= 0 ? pn[j] : make_ulonglong2(0ull, 0ull);
+            to2[2 * j] = x.x;
+            to2[2 * j + 1] = x.y;
+            tn2[2 * j] = y.x;
+            tn2[2 * j + 1] = y.y;
+          }
         }
-#pragma unroll 1
+        unsigned long long ph2[NP2];
+#pragma unroll
+        for (int j = 0; j < NP2; ++j) ph2[j] = 0ull;
+#pragma unroll 2
         for (int q = 0; q < QF; ++q) {
           const float fw = valid ? fwb[(f * QF + q) * EPT + el] : 0.f;
-          float qq[NFM4];
+          const ulonglong2* Qr = reinterpret_cast<const ulonglong2*>(Qt + q * NFM4);
+          unsigned long long qq2[NP2];
 #pragma unroll
-          for (int m4 = 0; m4 < NFM4; m4 += 4) {
-            const float4 y = *reinterpret_cast<const float4*>(Qt + q * NFM4 + m4);
-            qq[m4] = y.x;
-            qq[m4 + 1] = y.y;
-            qq[m4 + 2] = y.z;
-            qq[m4 + 3] = y.w;
+          for (int j = 0; j < NP2 / 2; ++j) {
+            const ulonglong2 y = Qr[j];
+            qq2[2 * j] = y.x;
+            qq2[2 * j + 1] = y.y;
           }
-          float o0 = 0.f, o1 = 0.f, n0 = 0.f, n1 = 0.f;
+          unsigned long long o2 = 0ull, n2 = 0ull;
 #pragma unroll
-          for (int m = 0; m < NFM; m += 2) {
-            o0 += qq[m] * to[m];
-            n0 += qq[m] * tn[m];
-            if (m + 1 < NFM) {
-              o1 += qq[m + 1] * to[m + 1];
-              n1 += qq[m + 1] * tn[m + 1];
-            }
+          for (int j = 0; j < NP2; ++j) {
+            o2 = tc::f2_fma(qq2[j], to2[j], o2);
+            n2 = tc::f2_fma(qq2[j], tn2[j], n2);
           }
-          const float val = fw * (fw >= 0.f ? o0 + o1 : n0 + n1);
+          float olo, ohi, nlo, nhi;
+          tc::f2_unpack(o2, olo, ohi);
+          tc::f2_unpack(n2, nlo, nhi);
+          const float val = fw * (fw >= 0.f ? olo + ohi : nlo + nhi);
+          const unsigned long long vv = tc::f2_pack(val, val);
 #pragma unroll
-          for (int m = 0; m < NFM; ++m) phi[ff][m] += qq[m] * val;
+          for (int j = 0; j < NP2; ++j) ph2[j] = tc::f2_fma(qq2[j], vv, ph2[j]);
+        }
+        // the projection into shared memory (free since the last barrier of the previous tile)
+#pragma unroll
+        for (int j = 0; j < NP2; ++j) {
+          float lo, hi;
+          tc::f2_unpack(ph2[j], lo, hi);
+          if (2 * j < NFM) phis[(f * NFM + 2 * j) * 128 + r] = lo;
+          if (2 * j + 1 < NFM) phis[(f * NFM + 2 * j + 1) * 128 + r] = hi;
         }
       }
       __syncwarp();
       if (lane == 0) tcimpl::mbar_arrive(bar_fwsfree + b);
-      // the projections into shared memory (free since the last barrier of the previous tile)
-#pragma unroll
-      for (int ff = 0; ff < 2; ++ff)
-#pragma unroll
-        for (int m = 0; m < NFM; ++m) phis[((2 * h + ff) * NFM + m) * 128 + r] = phi[ff][m];
-      // ---- the tile's residual from GEMM B -------------------------------------------
+      // ---- the tile's residual, this thread's coefficients --------------------------
       w = *abort_flag == 0 && tc::mbar_wait(bar_r, it & 1);
       if (!w) *abort_flag = 1;
       tc::fence_after_sync();
-      constexpr int NG = (NH + 7) / 8 + 1;   // 8-column groups covering [i0, i0 + NH)
-      float rr[NG * 8];
-      const int g0 = i0 / 8;
+      float ri[NH];
 #pragma unroll
-      for (int gq = 0; gq < NG; ++gq)
-        if ((g0 + gq) * 8 < NR) tc::tmem_ld8(lb + L::cRf + (g0 + gq) * 8, rr + 8 * gq);
+      for (int c4 = 0; c4 < NH; c4 += 4)
+        if (i0 + c4 < NR) tc::tmem_ld4(lb + L::cRf + i0 + c4, ri + c4);
       tc::tmem_wait_ld();
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tcimpl::mbar_arrive(bar_rfree);
       tc3impl::fw_sync();
       // ---- epilogue on coefficients i0 .. i0 + NH - 1 -------------------------------
-      float ri[NH];
+      {
+        unsigned long long r2[NH / 2];
 #pragma unroll
-      for (int ii = 0; ii < NH; ++ii) ri[ii] = rr[i0 - 8 * g0 + ii];
+        for (int j = 0; j < NH / 2; ++j) r2[j] = tc::f2_pack(ri[2 * j], ri[2 * j + 1]);
 #pragma unroll 1
-      for (int fm = 0; fm < L::NF * NFM; ++fm) {
-        const float p = phis[fm * 128 + r];
-        const float* Er = Ef + fm * NP4 + i0;
+        for (int fm = 0; fm < L::NF * NFM; ++fm) {
+          const float pv = phis[fm * 128 + r];
+          const unsigned long long pp = tc::f2_pack(pv, pv);
+          const ulonglong2* Er = reinterpret_cast<const ulonglong2*>(Ef + fm * NP4 + i0);
 #pragma unroll
-        for (int ii = 0; ii < NH; ++ii)
-          if (i0 + ii < N) ri[ii] += Er[ii] * p;
-      }
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) {
-        const int i = i0 + ii;
-        if (i >= N) break;
-        float x = 0.f;
-        if (valid) {
-          const size_t ix = tc3_index(tile, i, r, N);
-          const float ed = a.din ? a.din[ix] : 0.f;
-          const float inc = fmaf(a.p_hi, ed, fmaf(a.p_lo, ed, -fmaf(a.q_hi, ri[ii], a.q_lo * ri[ii])));
-          if (a.mode == 0) {
-            a.dout[ix] = inc;
-            x = vf_in[ix] + inc;
-          } else if (a.mode == 1) {
-            const double xv = a.v[ix] + tc::f32_to_f64(inc);   // FP64 state accumulation
-            a.v[ix] = xv;
-            x = tc::f64_to_f32_rn(xv);
-            a.vf_out[ix] = x;
-          } else {
-            a.v[ix] = tc::f32_to_f64(inc);
+          for (int j4 = 0; j4 < NH / 4; ++j4) {
+            if (i0 + 4 * j4 >= NP4) break;
+            const ulonglong2 y = Er[j4];
+            r2[2 * j4] = tc::f2_fma(y.x, pp, r2[2 * j4]);
+            r2[2 * j4 + 1] = tc::f2_fma(y.y, pp, r2[2 * j4 + 1]);
           }
         }
-        xs[i * 128 + r] = x;
+#pragma unroll
+        for (int j = 0; j < NH / 2; ++j) tc::f2_unpack(r2[j], ri[2 * j], ri[2 * j + 1]);
+      }
+      // in two halves: every global load of a half is issued before its stores, so
+      // the loads do not wait one after another behind possibly aliasing stores
+      constexpr int NQ = NH / 2;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        float ed[NQ], xb[NQ];
+        double xd[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int i = i0 + hh * NQ + q;
+          ed[q] = 0.f;
+          xb[q] = 0.f;
+          xd[q] = 0.0;
+          if (valid && i < N) {
+            const size_t ix = tc3_index(tile, i, r, N);
+            if (a.din) ed[q] = a.din[ix];
+            if (a.mode == 0) xb[q] = vf_in[ix];
+            if (a.mode == 1) xd[q] = a.v[ix];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int ii = hh * NQ + q, i = i0 + ii;
+          if (i >= N) break;
+          float x = 0.f;
+          if (valid) {
+            const size_t ix = tc3_index(tile, i, r, N);
+            const float inc = fmaf(a.p_hi, ed[q], fmaf(a.p_lo, ed[q], -fmaf(a.q_hi, ri[ii], a.q_lo * ri[ii])));
+            if (a.mode == 0) {
+              a.dout[ix] = inc;
+              x = xb[q] + inc;
+            } else if (a.mode == 1) {
+              const double xv = xd[q] + tc::f32_to_f64(inc);   // FP64 state accumulation
+              a.v[ix] = xv;
+              x = tc::f64_to_f32_rn(xv);
+              a.vf_out[ix] = x;
+            } else {
+              a.v[ix] = tc::f32_to_f64(inc);
+            }
+          }
+          xs[i * 128 + r] = x;
+        }
       }
       tc3impl::fw_sync();
       // ---- facet traces of the stage output, facets 2h, 2h + 1 -----------------------
       if (valid && a.mode != 2) {
-        float xo[NP4];
+        unsigned long long x2[NP4 / 2];
 #pragma unroll
-        for (int i = 0; i < NP4; ++i) xo[i] = i < N ? xs[i * 128 + r] : 0.f;
+        for (int j = 0; j < NP4 / 2; ++j)
+          x2[j] = tc::f2_pack(2 * j < N ? xs[2 * j * 128 + r] : 0.f, 2 * j + 1 < N ? xs[(2 * j + 1) * 128 + r] : 0.f);
 #pragma unroll
         for (int ff = 0; ff < 2; ++ff) {
           const int f = 2 * h + ff;
-#pragma unroll 1
-          for (int m = 0; m < NFM; ++m) {
-            const float* Er = Ef + (f * NFM + m) * NP4;
-            float s0 = 0.f, s1 = 0.f;
+          float tv[NFM4];
 #pragma unroll
-            for (int i4 = 0; i4 < NP4; i4 += 4) {
-              const float4 y = *reinterpret_cast<const float4*>(Er + i4);
-              s0 += y.x * xo[i4] + y.y * xo[i4 + 1];
-              s1 += y.z * xo[i4 + 2] + y.w * xo[i4 + 3];
+          for (int m = 0; m < NFM4; ++m) {
+            unsigned long long s2 = 0ull;
+            if (m < NFM) {
+              const ulonglong2* Er = reinterpret_cast<const ulonglong2*>(Ef + (f * NFM + m) * NP4);
+#pragma unroll
+              for (int j4 = 0; j4 < NP4 / 4; ++j4) {
+                const ulonglong2 y = Er[j4];
+                s2 = tc::f2_fma(y.x, x2[2 * j4], s2);
+                s2 = tc::f2_fma(y.y, x2[2 * j4 + 1], s2);
+              }
             }
-            a.trout[tc3_tr_index(tile, f, m, r, NFM)] = s0 + s1;
+            float lo, hi;
+            tc::f2_unpack(s2, lo, hi);
+            tv[m] = lo + hi;
           }
+          float4* dst = reinterpret_cast<float4*>(a.trout + tc3_tr_index(tile, f, 0, r, NFM4));
+#pragma unroll
+          for (int m4 = 0; m4 < NFM4 / 4; ++m4)
+            dst[m4] = make_float4(tv[4 * m4], tv[4 * m4 + 1], tv[4 * m4 + 2], tv[4 * m4 + 3]);
         }
       }
       tc3impl::fw_sync();   // phis and xs are reused by the next tile
@@ -578,12 +630,21 @@ __global__ void __launch_bounds__(128) tc3_in_kernel(const double* __restrict__ 
     vft[tc3_index(tile, i, r, N)] = x[i];
   }
   const float* Ef = ftab + L::oEf;
+  constexpr int NFM4 = L::NFM4;
 #pragma unroll 1
-  for (int fm = 0; fm < L::NF * NFM; ++fm) {
-    float s = 0.f;
+  for (int f = 0; f < L::NF; ++f) {
+    float tv[NFM4];
 #pragma unroll
-    for (int i = 0; i < N; ++i) s += Ef[fm * NP4 + i] * x[i];
-    tr[tc3_tr_index(tile, fm / NFM, fm % NFM, r, NFM)] = s;
+    for (int m = 0; m < NFM4; ++m) {
+      float s = 0.f;
+      if (m < NFM)
+#pragma unroll
+        for (int i = 0; i < N; ++i) s += Ef[(f * NFM + m) * NP4 + i] * x[i];
+      tv[m] = s;
+    }
+    float4* dst = reinterpret_cast<float4*>(tr + tc3_tr_index(tile, f, 0, r, NFM4));
+#pragma unroll
+    for (int m4 = 0; m4 < NFM4 / 4; ++m4) dst[m4] = make_float4(tv[4 * m4], tv[4 * m4 + 1], tv[4 * m4 + 2], tv[4 * m4 + 3]);
   }
 }
 

@@ -96,8 +96,10 @@ __host__ __device__ __forceinline__ int tc3_row(int el, int c) { return (el / 10
 __host__ __device__ __forceinline__ size_t tc3_index(int tile, int i, int r, int N) {
   return ((size_t)tile * N + i) * 128 + r;
 }
-__host__ __device__ __forceinline__ size_t tc3_tr_index(int tile, int f, int m, int r, int NFM) {
-  return (((size_t)tile * 4 + f) * NFM + m) * 128 + r;
+// facet traces [tile][f][row][NFM4]: the modes of one (row, facet) contiguous, so a
+// neighbour's trace is one short aligned run (two sectors at k = 4) read by vector loads
+__host__ __device__ __forceinline__ size_t tc3_tr_index(int tile, int f, int m, int r, int NFM4) {
+  return (((size_t)tile * 4 + f) * 128 + r) * NFM4 + m;
 }
 
 }  // namespace dgc
