@@ -56,10 +56,20 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-shapes", action="store_true",
                     help="skip the parallelogram and curved-triangle sections")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other simplex configurations (square16_k2, cube32_k3, cube48_k4)")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip the oracle runs (errors against the oracle and the cpu_baseline)")
     args = ap.parse_args()
-    if args.impl == "dgconv" and W.WORKLOADS[args.workload].shape != "simplex" and args.prec in TC_PRECS:
-        ap.error("the tensor-core precisions cover affine triangles; use --prec fp32 or fp64 on other shapes")
+    if args.impl == "dgconv" and args.prec in TC_PRECS and not tc_covers(W.WORKLOADS[args.workload], args.prec):
+        ap.error("the tensor-core precisions cover affine simplices with k <= 4 (tetrahedra in bf16x3 only); "
+                 "use --prec fp32 or fp64 here")
     return args
+
+
+def tc_covers(wl, prec) -> bool:
+    """Whether the tensor-core path of the library covers a workload at a precision."""
+    return wl.shape == "simplex" and wl.k <= 4 and (wl.dim == 2 or prec == "bf16x3")
 
 
 def dist_env():
@@ -252,6 +262,36 @@ def peaks():
             m = json.load(f)
         return m.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def bf16_peak():
+    """Dense bf16 tensor rate (TFLOP/s) for a kernel timed inside a long step: the
+    sustained measured figure, else the burst one, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            m = json.load(f)
+        for key in ("bf16_tflops_sustained", "bf16_tflops"):
+            if m.get(key):
+                return float(m[key]), f"measured ({key})"
+    return 1700.0, "fallback (sustained)"
+
+
+def measure_fp64_peak(torch):
+    """FP64 rate of this GPU (TFLOP/s), measured here: a cuBLAS DGEMM of 4096^3, best of 5."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = a @ b
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
 # ---------------------------------------------------------------------------
@@ -539,6 +579,156 @@ class OracleTimer:
         return all_core, stage_s, one_core
 
 
+# ---------------------------------------------------------------------------
+# the oracle on the whole mesh over the host cores: the reference result of a
+# workload's RK sequence and the cpu_baseline rate
+# ---------------------------------------------------------------------------
+def _shm_view(name, shape):
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=name)
+    return shm, np.ndarray(shape, dtype=np.float64, buffer=shm.buf)
+
+
+def _oracle_rk_worker(wl, p, lo, hi, nsteps, names, shapes, barrier, queue):
+    """Process p of the parallel oracle run: elements [lo, hi) of workload wl.
+
+    Every process builds the oracle's mesh; the wind, its peak speed and the
+    initial state are computed over the process's elements (the element
+    restrictions of the oracle's builders, in sub-blocks for memory) into
+    shared arrays; then each stage of every substep applies the oracle's
+    operator to the block (its ``sel``) between barriers, so the shared state
+    goes through the SSP-RK sequence of ``oracle.dg.rk_substeps``."""
+    from oracle import dg as ODG
+    from oracle import hdiv as OH
+    from oracle import mesh as OM
+    views = {key: _shm_view(nm, shapes[key]) for key, nm in names.items()}
+    A = {key: v[1] for key, v in views.items()}
+    verts, elems = wl.mesh()[:2]
+    om = OM.Mesh(verts, elems)
+    k, d = wl.k, wl.dim
+    block = np.arange(lo, hi)
+    subs = np.array_split(block, max(1, (hi - lo) // 2048))
+    t0 = time.perf_counter()
+    for sub in subs:                       # the wind's DOFs owned by this block
+        w = OH.wind_from_potential(om, k, wl.potential(), elems=sub)
+        nz = np.nonzero(w)[0]
+        A["wind"][nz] = w[nz]
+    barrier.wait()
+    wind = A["wind"].copy()
+    A["speed"][p] = ODG.max_wind_speed(om, k, wind, sel=block)
+    barrier.wait()
+    if wl.unit_peak_speed:
+        wind = wind / A["speed"].max()
+        barrier.wait()
+        A["speed"][p] = ODG.max_wind_speed(om, k, wind, sel=block)
+        barrier.wait()
+    ds = wl.cfl * float(om.shortest_edge().min()) / ((2 * k + 1) * A["speed"].max())   # reading A7
+    v, v1, v2 = A["v"], A["v1"], A["v2"]
+    if wl.state == "fourier":
+        field = W.fourier_field(wl.seed + 2000, d)
+        for sub in subs:
+            u = OH.dofs_of_function(om, k, lambda x: field(x), elems=sub)
+            nz = np.nonzero(u)[0]
+            A["un"][nz] = u[nz]
+        barrier.wait()
+        for sub in subs:
+            v[sub] = ODG.transfer(om, k, A["un"], sel=sub)
+    else:
+        v[block] = W.uniform_coeffs(wl.seed, om.n_elem, d, k)[block]
+    barrier.wait()
+    op = ODG.ConvectionOracle(om, k, wind, sel=block)
+    setup_s = time.perf_counter() - t0
+    L = lambda x: -op.apply(x)            # noqa: E731
+    stage_s = []
+
+    def stage(f):
+        t = time.perf_counter()
+        f()
+        stage_s.append(time.perf_counter() - t)
+        barrier.wait()
+    if wl.name == "square16_k2":           # this configuration also applies the operator once
+        A["apply"][block] = op.apply(v)
+        barrier.wait()
+    for _ in range(nsteps):
+        if wl.scheme == 2:
+            stage(lambda: v1.__setitem__(block, v[block] + ds * L(v)))
+            stage(lambda: v.__setitem__(block, 0.5 * v[block] + 0.5 * (v1[block] + ds * L(v1))))
+        else:
+            stage(lambda: v1.__setitem__(block, v[block] + ds * L(v)))
+            stage(lambda: v2.__setitem__(block, 0.75 * v[block] + 0.25 * (v1[block] + ds * L(v1))))
+            stage(lambda: v.__setitem__(block, v[block] / 3.0 + 2.0 / 3.0 * (v2[block] + ds * L(v2))))
+    queue.put((p, ds, setup_s, stage_s))
+    for shm, _ in views.values():
+        shm.close()
+
+
+def oracle_rk(wl, nsteps: int, procs: int | None = None):
+    """The oracle's RK sequence of workload wl (its wind, initial state and CFL
+    substep) on the whole mesh, split over the host cores.  Returns a dict with
+    the final state, the operator applied to the initial state (square16_k2),
+    the substep size, the stage times (slowest process) and the core count."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    from oracle import basis as OB
+    from oracle import mesh as OM
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    P = min(procs or cores, wl.n_elem)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"                             # inherited by the spawned processes
+    N = OB.dim_pk(wl.dim, wl.k)
+    verts, elems = wl.mesh()[:2]
+    n_hdiv = OM.Mesh(verts, elems).n_facets * OB.hdiv_counts(wl.dim, wl.k)[0] + \
+        wl.n_elem * OB.hdiv_counts(wl.dim, wl.k)[1]
+    shapes = {"wind": (n_hdiv,), "un": (n_hdiv,), "speed": (P,), "v": (wl.n_elem, wl.dim, N),
+              "v1": (wl.n_elem, wl.dim, N), "v2": (wl.n_elem, wl.dim, N), "apply": (wl.n_elem, wl.dim, N)}
+    shms = {key: shared_memory.SharedMemory(create=True, size=max(8, int(np.prod(sh)) * 8))
+            for key, sh in shapes.items()}
+    try:
+        for key, sh in shapes.items():
+            np.ndarray(sh, dtype=np.float64, buffer=shms[key].buf)[...] = 0.0
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        bar = ctx.Barrier(P)
+        edges = np.linspace(0, wl.n_elem, P + 1).astype(int)
+        names = {key: sm.name for key, sm in shms.items()}
+        ps = [ctx.Process(target=_oracle_rk_worker, args=(wl, p, int(edges[p]), int(edges[p + 1]), nsteps,
+                                                           names, shapes, bar, q)) for p in range(P)]
+        t0 = time.perf_counter()
+        for pr in ps:
+            pr.start()
+        res = [q.get() for _ in ps]
+        for pr in ps:
+            pr.join()
+        wall = time.perf_counter() - t0
+        out = {"v": np.ndarray(shapes["v"], dtype=np.float64, buffer=shms["v"].buf).copy(),
+               "apply": np.ndarray(shapes["apply"], dtype=np.float64, buffer=shms["apply"].buf).copy(),
+               "ds": res[0][1], "setup_s": max(r[2] for r in res), "cores": P, "wall_s": wall}
+        n_st = len(res[0][3])
+        out["stage_s"] = [max(r[3][i] for r in res) for i in range(n_st)]
+        return out
+    finally:
+        for sm in shms.values():
+            sm.close()
+            sm.unlink()
+
+
+def oracle_apply_sample(wl, w, sel):
+    """The oracle's operator on the elements sel of workload wl (its unscaled wind,
+    computed only where those elements need it) applied to the state w."""
+    from oracle import dg as ODG
+    from oracle import hdiv as OH
+    from oracle import mesh as OM
+    verts, elems = wl.mesh()[:2]
+    om = OM.Mesh(verts, elems)
+    nb = om.nbr[sel]
+    need = np.unique(np.concatenate([sel, nb[nb >= 0]]))   # owners of the selected elements' facets
+    wind = OH.wind_from_potential(om, wl.k, wl.potential(), elems=need)
+    return ODG.ConvectionOracle(om, wl.k, wind, sel=sel).apply(w)
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -561,6 +751,210 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+class OracleJobs(threading.Thread):
+    """The oracle runs of the benchmark, one after another on the host cores while
+    the GPU measurements proceed (spawned processes; none of them touches CUDA)."""
+
+    def __init__(self, jobs):
+        super().__init__(daemon=True)
+        self.jobs = jobs
+        self.results = {}
+
+    def run(self):
+        for key, fn in self.jobs:
+            t0 = time.perf_counter()
+            try:
+                self.results[key] = fn()
+            except Exception as ex:            # reported in the JSON line, never silent
+                self.results[key] = {"error": repr(ex)}
+            self.results[key]["job_s"] = time.perf_counter() - t0
+
+
+# the slice of the RK sequence the oracle runs on the full mesh, per configuration
+# (square256_k4 and square16_k2 in full; cube32_k3 the first 4 substeps of 50)
+ORACLE_SUBSTEPS = {"square16_k2": 10, "square256_k4": 100, "cube32_k3": 4}
+SAMPLE_ELEMS = 1024     # cube48_k4: one operator application on sampled elements
+
+
+def sample_elements(wl):
+    """Seeded element sample of a workload (first and last tile edges included)."""
+    sel = np.random.default_rng(wl.seed + 77).choice(wl.n_elem, size=SAMPLE_ELEMS, replace=False)
+    return np.unique(np.concatenate([sel, [0, 39, 40, wl.n_elem - 1]]))
+
+
+def oracle_jobs_for(names):
+    jobs = []
+    for name in names:
+        wl = W.WORKLOADS[name]
+        if name in ORACLE_SUBSTEPS:
+            jobs.append((name, lambda wl=wl: oracle_rk(wl, ORACLE_SUBSTEPS[wl.name])))
+        else:
+            def sample(wl=wl):
+                w = W.uniform_coeffs(wl.seed, wl.n_elem, wl.dim, wl.k)
+                sel = sample_elements(wl)
+                return {"apply": oracle_apply_sample(wl, w, sel), "sel": sel}
+            jobs.append((name, sample))
+    return jobs
+
+
+def stage_roofline(wl, stage_ms, hbm, hbm_src, bf16, bf16_src, prec, fp64_tflops=None):
+    """Roofline of one stage launch: the algorithmic bytes at the HBM rate, and the
+    algorithmic flops at the rate of the arithmetic that carries them (the split
+    BF16x3 contractions issue six tensor-core products per FP32 product; FP64 runs
+    on the FP64 pipe); the binding bound is the larger time."""
+    byts, flops, _ = stage_bytes_flops(wl)
+    t_hbm = byts * wl.n_elem / (hbm * 1e9)
+    out = {"kernel": ("stage_tc3_kernel" if wl.dim == 3 else "stage_tc_kernel") if prec in TC_PRECS
+           else "stage_kernel", "stage_ms": stage_ms,
+           "alg_bytes_per_elem_stage": byts, "alg_flops_per_elem_stage": flops,
+           "hbm_bound_ms": 1e3 * t_hbm, "achieved_gbs": byts * wl.n_elem / (stage_ms * 1e-3) / 1e9}
+    if prec in TC_PRECS:
+        t_t = 6.0 * flops * wl.n_elem / (bf16 * 1e12)
+        out["tensor_bound_ms"] = 1e3 * t_t
+        if t_t > t_hbm:
+            out.update(bound="tensor", achieved=6.0 * flops * wl.n_elem / (stage_ms * 1e-3) / 1e12, peak=bf16,
+                       unit="TFLOP/s", peak_source=bf16_src + ", 6 bf16 products per FP32 product")
+        else:
+            out.update(bound="hbm", achieved=out["achieved_gbs"], peak=hbm, unit="GB/s", peak_source=hbm_src)
+    elif prec == "fp64" and fp64_tflops:
+        out.update(bound="alu", achieved=flops * wl.n_elem / (stage_ms * 1e-3) / 1e12, peak=fp64_tflops,
+                   unit="TFLOP/s", peak_source="FP64 DGEMM measured in this run")
+    else:
+        out.update(bound="hbm", achieved=out["achieved_gbs"], peak=hbm, unit="GB/s", peak_source=hbm_src)
+    out["frac"] = out["achieved"] / out["peak"]
+    return out
+
+
+def measure_config(torch, dgconv, name, rank, world, flush, stream, fp64_tflops):
+    """One of the simplex configurations (square16_k2, cube32_k3, cube48_k4): the
+    configured RK sequence per precision (its step time, or for long FP64 runs the
+    step extrapolated from the stage time), the stage kernel against its roofline,
+    and the inputs of the comparison with the oracle (run afterwards)."""
+    wl = rank_workload(W.WORKLOADS[name], rank)
+    verts, elems = wl.mesh()[:2]
+    mesh = dgconv.Mesh(wl.dim, wl.k, verts, elems)
+    wind = mesh.wind_from_potential(torch.tensor(dgconv.potential_values(mesh, wl.potential()),
+                                                 dtype=torch.float64, device="cuda"))
+    wind_raw = wind.clone()
+    if wl.unit_peak_speed:
+        wind /= mesh.max_wind_speed(wind)
+    ds = mesh.cfl_ds(wind, wl.cfl)
+    v0 = torch.tensor(W.uniform_coeffs(wl.seed, wl.n_elem, wl.dim, wl.k), dtype=torch.float64, device="cuda")
+    byts, flops, N = stage_bytes_flops(wl)
+    stages = wl.scheme * wl.substeps
+    units = wl.n_elem * N * wl.dim * (stages + (1 if name == "square16_k2" else 0))
+    hbm, hbm_src = peaks()
+    bf16, bf16_src = bf16_peak()
+    v = mesh.dg_zeros()
+    out = {"workload": wl.name, "elements": wl.n_elem, "dim": wl.dim, "k": wl.k, "substeps": wl.substeps,
+           "scheme": f"SSP-RK{wl.scheme}", "unit": "DOF-stage updates/s", "by_prec": {}}
+
+    def step(p):
+        if name == "square16_k2":
+            mesh.conv_apply(wind, v0, out=v, prec=p)
+        v.copy_(v0)
+        mesh.rk_substeps(wind, v, ds, wl.substeps, wl.scheme, p)
+
+    def time_rk(n, p, reps=3):
+        best = 1e30
+        for _ in range(reps):
+            v.copy_(v0)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mesh.rk_substeps(wind, v, ds, n, wl.scheme, p)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+    for prec in ("bf16x3", "fp32", "fp64"):
+        if prec in TC_PRECS and not (wl.k <= 4):
+            continue
+        # two graph lengths whose difference is a few hundred milliseconds of stages
+        mesh.rk_substeps(wind, v, ds, 1, wl.scheme, prec)
+        est = time_rk(1, prec, reps=1) / wl.scheme
+        n_hi = max(2, min(wl.substeps // 2, int(300.0 / (wl.scheme * max(est, 1e-3)))))
+        n_lo = max(1, n_hi // 3)
+        mesh.rk_substeps(wind, v, ds, n_lo, wl.scheme, prec)          # graphs built outside the timing
+        mesh.rk_substeps(wind, v, ds, n_hi, wl.scheme, prec)
+        t_lo, t_hi = time_rk(n_lo, prec), time_rk(n_hi, prec)
+        stage_ms = max((t_hi - t_lo) / (wl.scheme * (n_hi - n_lo)), 1e-6)
+        rec = {"stage_ms": stage_ms}
+        if stage_ms * stages < 5000.0:                                # the whole configured step, timed
+            step(prec)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(2):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step(prec)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = max_over_ranks(min(ts), world, "cuda")
+            rec.update(ms_per_step=ms, value=job_throughput(units, world, ms))
+        else:
+            ms = stage_ms * stages
+            rec.update(ms_per_step_from_stage=ms, value=job_throughput(units, world, ms),
+                       value_note="step extrapolated from the stage time (the full FP64 run takes minutes)")
+        rec["roofline"] = stage_roofline(wl, stage_ms, hbm, hbm_src, bf16, bf16_src, prec, fp64_tflops)
+        mesh.check()
+        out["by_prec"][prec] = rec
+    out["_gpu"] = {"mesh": mesh, "wind": wind, "wind_raw": wind_raw, "v0": v0, "ds": ds}
+    return out
+
+
+def config_errors(torch, cfg, orc):
+    """The configuration's GPU results against the oracle's (reading A17, max-norm
+    relative): the oracle's RK slice from the same initial state with the oracle's
+    substep, or (cube48_k4) one operator application on sampled elements with the
+    unscaled wind; plus the whole configured run of each mixed precision against the
+    FP64 GPU run (short for cube48_k4, whose FP64 run takes minutes)."""
+    g = cfg.pop("_gpu")
+    mesh, wind, v0 = g["mesh"], g["wind"], g["v0"]
+    wl = W.WORKLOADS[cfg["workload"]]
+    errs = {}
+    if orc is None or "error" in orc:
+        errs["oracle"] = {"error": None if orc is None else orc["error"]}
+    elif "sel" in orc:
+        sel = orc["sel"]
+        ref = orc["apply"]
+        for prec in cfg["by_prec"]:
+            got = mesh.conv_apply(g["wind_raw"], v0, prec=prec).cpu().numpy()[sel]
+            errs[prec] = float(np.abs(got - ref).max() / np.abs(ref).max())
+        errs["oracle"] = {"what": f"conv_apply on {sel.size} sampled elements (unscaled wind)",
+                          "oracle_s": orc["job_s"]}
+    else:
+        ns = ORACLE_SUBSTEPS[wl.name]
+        for prec in cfg["by_prec"]:
+            x = v0.clone()
+            mesh.rk_substeps(wind if not wl.unit_peak_speed else wind, x, orc["ds"], ns, wl.scheme, prec)
+            got = x.cpu().numpy()
+            errs[prec] = float(np.abs(got - orc["v"]).max() / np.abs(orc["v"]).max())
+        if wl.name == "square16_k2":
+            for prec in cfg["by_prec"]:
+                got = mesh.conv_apply(wind, v0, prec=prec).cpu().numpy()
+                errs[f"conv_apply/{prec}"] = float(np.abs(got - orc["apply"]).max() / np.abs(orc["apply"]).max())
+        errs["oracle"] = {"what": f"{ns} of {wl.substeps} substeps on the full mesh from the same state, the "
+                                  f"oracle's substep {orc['ds']:.6g}", "cores": orc["cores"],
+                          "oracle_s": orc["job_s"]}
+    cfg["max_rel_err_vs_oracle"] = errs
+    # the whole configured run of the mixed precisions against FP64 on the GPU
+    ns = wl.substeps if wl.name != "cube48_k4" else 4
+    ref = v0.clone()
+    mesh.rk_substeps(wind, ref, g["ds"], ns, wl.scheme, "fp64")
+    vs = {}
+    for prec in cfg["by_prec"]:
+        if prec == "fp64":
+            continue
+        x = v0.clone()
+        mesh.rk_substeps(wind, x, g["ds"], ns, wl.scheme, prec)
+        vs[prec] = float((x - ref).abs().max() / ref.abs().max())
+    cfg["max_rel_err_vs_fp64_gpu"] = {"substeps": ns, **vs}
+    mesh.check()
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -570,6 +964,13 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    # the oracle runs on the host cores while the GPU is measured (rank 0 of a 1-GPU run)
+    use_oracle = rank == 0 and world == 1 and not args.no_oracle and args.workload == WORKLOAD
+    config_names = [] if (args.no_configs or args.workload != WORKLOAD) else ["square16_k2", "cube32_k3", "cube48_k4"]
+    oracle = None
+    if use_oracle:
+        oracle = OracleJobs(oracle_jobs_for([WORKLOAD] + config_names))
+        oracle.start()
     import torch
     from paper_1508_04245_gb300 import build, dgconv
     build.build()
@@ -658,7 +1059,8 @@ def main():
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
 
-    # error of the mixed path against the FP64 GPU path (itself pinned to the oracle)
+    # error of the mixed path against the FP64 GPU path (itself pinned to the oracle);
+    # the error against the oracle follows once its run has finished
     err = None
     if args.prec != "fp64":
         v64 = mesh.transfer(u_n)
@@ -675,13 +1077,13 @@ def main():
     value = job_throughput(units_per_step, world, ms)
     e2e_val = job_throughput(units_per_step, world, e2e_ms_max)
     hbm, hbm_src = peaks()
-    achieved = byts * wl.n_elem / (stage_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": ncu_traffic(wl, args.prec), "peak_source": hbm_src,
-            "kernel": ("stage_tc_kernel" if args.prec in TC_PRECS
-                       else {"quad": "stage_quad_kernel", "hex": "stage_hex_kernel"}.get(wl.shape, "stage_kernel")),
-            "stage_ms": stage_ms, "alg_bytes_per_elem_stage": byts, "alg_flops_per_elem_stage": flops,
-            "achieved_tflops": flops * wl.n_elem / (stage_ms * 1e-3) / 1e12}
+    bf16, bf16_src = bf16_peak()
+    roof = stage_roofline(wl, stage_ms, hbm, hbm_src, bf16, bf16_src, args.prec)
+    if args.prec not in TC_PRECS:
+        roof["kernel"] = {"quad": "stage_quad_kernel", "hex": "stage_hex_kernel"}.get(wl.shape, "stage_kernel")
+    roof["traffic"] = ncu_traffic(wl, args.prec)
+    roof["traffic_source"] = "committed ncu capture of this kernel source (None once the source changed)"
+    roof["achieved_tflops"] = flops * wl.n_elem / (stage_ms * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "DOF-stage updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -690,7 +1092,7 @@ def main():
         "config": {"workload": wl.name, "elements": wl.n_elem, "dim": wl.dim, "k": wl.k, "substeps": substeps,
                    "scheme": "SSP-RK3", "prec": args.prec, "l2": "flushed between timed steps",
                    "step": "a1 geometry, a2 I, 100x RK3 (a3-a7), M^V, a8 I^T"},
-        "max_rel_err_vs_fp64": err,
+        "max_rel_err_vs_fp64_gpu": err,
         "e2e": {"value": e2e_val, "unit": "DOF-stage updates/s", "h2d_bytes_per_step": 2 * mesh.n_hdiv * 8,
                 "d2h_bytes_per_step": mesh.n_hdiv * 8},
         "gpu_launches": launches_per_step * args.steps,
@@ -700,7 +1102,7 @@ def main():
         # the same step at the other contraction precisions (1 warm-up, 2 timed steps each)
         others = {}
         for prec in ("fp64", "fp32", "tf32x3", "bf16x3"):
-            if prec == args.prec or (prec in TC_PRECS and not (wl.dim == 2 and wl.k <= 4 and wl.shape == "simplex")):
+            if prec == args.prec or (prec in TC_PRECS and not tc_covers(wl, prec)):
                 continue
 
             def step_p(p=prec):
@@ -741,7 +1143,7 @@ def main():
     res_r = torch.zeros(rich_iters + 1, dtype=torch.float64, device="cuda")
     rich = {}
     for prec in ("fp64", "fp32", "tf32x3", "bf16x3"):
-        if prec in TC_PRECS and not (wl.dim == 2 and wl.k <= 4 and wl.shape == "simplex"):
+        if prec in TC_PRECS and not tc_covers(wl, prec):
             continue
         if wl.shape == "curved":        # the pseudo-time solve takes affine meshes
             break
@@ -772,9 +1174,47 @@ def main():
         line["parallelogram"] = measure_shape(torch, dgconv, "parallelogram256_k4", rank, world, flush, stream)
         line["curved"] = measure_shape(torch, dgconv, "curved256_k4", rank, world, flush, stream)
         line["parallelepiped"] = measure_shape(torch, dgconv, "parallelepiped32_k3", rank, world, flush, stream)
+    fp64_tflops = measure_fp64_peak(torch)
+    line["fp64_peak_tflops"] = {"value": fp64_tflops, "source": "cuBLAS DGEMM 4096^3 in this run"}
+    configs = {}
+    for name in config_names:
+        configs[name] = measure_config(torch, dgconv, name, rank, world, flush, stream, fp64_tflops)
     # clocks sampled from before the first timed step to the end of the GPU measurements
     line["clocks"] = clocks.stop()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl.shape != "curved":
+    if oracle is not None:
+        oracle.join()
+        orc = oracle.results.get(WORKLOAD)
+        if orc is None or "error" in orc:
+            line["max_rel_err_vs_oracle"] = {"error": None if orc is None else orc["error"]}
+        else:
+            # the configured RK sequence from the GPU's own I u^n with the oracle's substep
+            errs = {}
+            ns_o = ORACLE_SUBSTEPS[WORKLOAD]
+            for prec in ("fp64", "fp32", "tf32x3", "bf16x3"):
+                if prec in TC_PRECS and not (wl.k <= 4 and wl.shape == "simplex"):
+                    continue
+                x = mesh.transfer(u_n)
+                mesh.rk_substeps(wind, x, orc["ds"], ns_o, 3, prec)
+                got = x.cpu().numpy()
+                errs[prec] = float(np.abs(got - orc["v"]).max() / np.abs(orc["v"]).max())
+            errs["oracle"] = {"what": f"the oracle's {ns_o}-substep SSP-RK3 run of the full mesh from its own "
+                                      f"I u^n (substep {orc['ds']:.6g}), {orc['cores']} processes",
+                              "oracle_s": orc["job_s"]}
+            line["max_rel_err_vs_oracle"] = errs
+            units_stage = wl.n_elem * N * wl.dim
+            line["cpu_baseline"] = {
+                "value": units_stage / statistics.mean(orc["stage_s"]), "unit": "DOF-stage updates/s",
+                "cores": orc["cores"], "kind": "oracle",
+                "sample": f"the FP64 numpy oracle's {len(orc['stage_s'])} SSP-RK3 stages of the full "
+                          f"{wl.n_elem}-element mesh (the reference run of max_rel_err_vs_oracle), {orc['cores']} "
+                          f"processes on element blocks, one BLAS thread each, a barrier per stage; value = DOF "
+                          f"updates per stage over the mean stage time ({sum(orc['stage_s']):.1f} s of stages)"}
+    for name, cfg in configs.items():
+        config_errors(torch, cfg, None if oracle is None else oracle.results.get(name))
+    if configs:
+        line["configs"] = configs
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and "cpu_baseline" not in line \
+            and wl.shape != "curved":
         timer = OracleTimer(wl)
         rate, stage_s, one_core = timer.rates(warm=1, steps=2)
         line["cpu_baseline"] = {"value": rate, "unit": "DOF-stage updates/s", "cores": timer.cores,
