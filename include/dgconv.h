@@ -26,7 +26,10 @@
  *   the environment variable DGC_FAULT=alloc|capture|launch makes device
  *   allocations, graph captures or kernel launches fail on the host before the
  *   CUDA call is made; the call returns its DGC_ERR_* code and the handle stays
- *   usable.
+ *   usable.  DGC_FAULT=stall launches the tensor-core stage kernels with no
+ *   bulk copy issued and a short poll budget: their bounded waits run out with
+ *   nothing in flight, the results of that call are undefined, and dgc_check
+ *   then returns DGC_ERR_TIMEOUT; the handle stays usable.
  * - Status: 0 (DGC_OK) on success, a negative DGC_ERR_* code otherwise; the
  *   message is available from dgc_last_error().  Argument errors are detected
  *   on the host before anything is launched.

@@ -32,7 +32,9 @@ thread_local std::string g_last_error;
 // Host-side fault injection for tests of error propagation (no GPU is ever made
 // to fault): DGC_FAULT=alloc makes device allocations fail, =capture makes graph
 // captures fail to start, =launch makes kernel launches fail, each before the
-// CUDA call is made.
+// CUDA call is made; =stall launches the tensor-core stage kernels with no bulk
+// copy issued and a short poll budget, so their bounded waits run out with
+// nothing in flight and the timeout reaches the status word (dgc_check).
 bool injected(const char* what) {
   const char* f = std::getenv("DGC_FAULT");
   return f && std::strcmp(f, what) == 0;
@@ -91,9 +93,10 @@ struct GraphKey {
   double* v;
   double ds;
   int nsteps, scheme, prec;
+  bool stall;   // captured under DGC_FAULT=stall
   bool operator==(const GraphKey& o) const {
     return wind == o.wind && v == o.v && ds == o.ds && nsteps == o.nsteps && scheme == o.scheme &&
-           prec == o.prec;
+           prec == o.prec && stall == o.stall;
   }
 };
 
@@ -141,10 +144,12 @@ struct dgc_mesh {
   // stage-table blobs
   DevBuf<double> tab64;
   DevBuf<float> tab32, tcblob, tcblob16, wcoef, trA, trB;   // tensor-core blobs: TF32x3, BF16x3
-  // tetrahedral tensor-core path: BF16 table chunks (the FP32 facet tables in tcblob)
-  // and the tile-blocked frozen facet flux
+  // tetrahedral tensor-core path: BF16 table chunks (the FP32 facet tables in tcblob),
+  // the tile-blocked frozen facet flux and wind at the volume points, and the wind's
+  // FP64 coefficients they are evaluated from
   DevBuf<unsigned char> tc3chunks;
-  DevBuf<float> fw3;
+  DevBuf<float> fw3, wq3;
+  DevBuf<double> uc3;
   DevBuf<double> ts0;              // tile-blocked FP64 state of the tensor-core path
   DevBuf<float> tsf, d1, d2;       // its FP32 copy and the FP32 stage increments
   DevBuf<double> ts1, tsg;         // pseudo-time solve on that path: second state, right-hand side
@@ -238,6 +243,8 @@ struct dgc_mesh {
     tcblob16.release();
     tc3chunks.release();
     fw3.release();
+    wq3.release();
+    uc3.release();
     wcoef.release();
     trA.release();
     trB.release();
@@ -369,11 +376,10 @@ dgc_status ensure_tc_scratch(dgc_mesh* m) {
       return fail(DGC_ERR_CUDA, "tensor-core stage setup failed: %s", cudaGetErrorString(perr));
     const size_t nt = dgc::tc3_rows_len(m->s.K, m->E), nr = dgc::tc3_tr_len(m->s.K, m->E);
     const size_t nw = dgc::tc3_fw_len(m->s.K, m->E);
-    // rows the kernels never write (padding rows, elements past E) must read as zero
-    if (m->wcoef.n < nt) {
-      DGC_CUDA(m->wcoef.alloc(nt));
-      DGC_CUDA(cudaMemset(m->wcoef.ptr, 0, nt * sizeof(float)));
-    }
+    // the wind at the points is written in full (zero at padding points and elements)
+    DGC_CUDA(m->wq3.alloc((size_t)dgc::wind_pts_tc3_len(m->s.QV, m->E)));
+    DGC_CUDA(m->uc3.alloc(((size_t)m->E + 39) / 40 * 3 * m->s.N * 40));
+    // facet flux entries the kernel never writes (elements past E) must read as zero
     if (m->fw3.n < nw) {
       DGC_CUDA(m->fw3.alloc(nw));
       DGC_CUDA(cudaMemset(m->fw3.ptr, 0, nw * sizeof(float)));
@@ -425,10 +431,15 @@ dgc_status launch_stage_tc(dgc_mesh* m, dgc_prec prec, int mode, const float* di
   a.p_lo = (float)(p - (double)a.p_hi);
   a.q_hi = (float)q;
   a.q_lo = (float)(q - (double)a.q_hi);
+  if (injected("stall")) {
+    a.stall = 1;
+    a.poll = 1u << 12;
+  }
   if (m->s.D == 3) {
     a.blob = reinterpret_cast<const float*>(m->tc3chunks.ptr);
     a.ftab = m->tcblob.ptr;
     a.fw3 = m->fw3.ptr;
+    a.wq3 = m->wq3.ptr;
   }
   cudaError_t err = m->s.D == 3 ? dgc::launch_stage_tc3(m->s.K, &a, st) : dgc::launch_stage_tc(m->s.D, m->s.K, P, &a, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed: %s", cudaGetErrorString(err));
@@ -541,7 +552,7 @@ dgc_status stage(dgc_mesh* m, dgc_prec prec, const double* vin, const double* vn
 dgc_status prepare_wind(dgc_mesh* m, dgc_prec prec, const double* wind, cudaStream_t st) {
   cudaError_t err;
   if (is_tc(prec) && m->s.D == 3) {
-    err = dgc::launch_wind_tc3(m->view(), wind, m->wcoef.ptr, m->fw3.ptr, st);
+    err = dgc::launch_wind_tc3(m->view(), wind, m->uc3.ptr, m->wq3.ptr, m->fw3.ptr, st);
   } else if (is_tc(prec)) {
     err = dgc::launch_wind_coeffs(m->view(), wind, m->wcoef.ptr, dgc::tc_nk(m->s.D, m->s.K), st);
   } else {
@@ -1225,7 +1236,7 @@ dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg
   DGC_CUDA(mesh->stage1.alloc(n));
   DGC_CUDA(mesh->stage2.alloc(n));
   cudaStream_t st = as_stream(stream);
-  GraphKey key{wind_hdiv, v_dg, ds, nsteps, (int)scheme, (int)prec};
+  GraphKey key{wind_hdiv, v_dg, ds, nsteps, (int)scheme, (int)prec, injected("stall")};
   if (!(mesh->graph && mesh->graph_key == key)) {
     if (mesh->graph) cudaGraphExecDestroy(mesh->graph);
     mesh->graph = nullptr;
@@ -1433,7 +1444,8 @@ dgc_status dgc_oifs_rhs(dgc_mesh* mesh, const double* u_hdiv, const double* wind
   std::memcpy(&b_dt, &dt_prev, 8);
   std::vector<uint64_t> key = {(uint64_t)(uintptr_t)u_hdiv, (uint64_t)(uintptr_t)wind_hdiv,
                                (uint64_t)(uintptr_t)wind_prev_hdiv, (uint64_t)(uintptr_t)out_hdiv, b_ds,
-                               wind_prev_hdiv ? b_dt : 0u, (uint64_t)nsteps, (uint64_t)scheme, (uint64_t)prec};
+                               wind_prev_hdiv ? b_dt : 0u, (uint64_t)nsteps, (uint64_t)scheme, (uint64_t)prec,
+                               (uint64_t)injected("stall")};
   if (!(mesh->oifs_graph && mesh->oifs_key == key)) {
     if (mesh->oifs_graph) cudaGraphExecDestroy(mesh->oifs_graph);
     mesh->oifs_graph = nullptr;
@@ -1498,6 +1510,7 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
     key.insert(key.end(), {(uint64_t)(uintptr_t)m, (uint64_t)(uintptr_t)winds[i], (uint64_t)(uintptr_t)states[i],
                            dsbits, (uint64_t)nsteps[i]});
   }
+  key.push_back((uint64_t)injected("stall"));
   std::lock_guard<std::mutex> lock(g_batch_mu);
   BatchGraph* hit = nullptr;
   for (BatchGraph& b : g_batch_cache)

@@ -155,11 +155,11 @@ __global__ void wind_coeffs_kernel(DevMesh m, const double* __restrict__ u, floa
     for (int i = 0; i < nk; ++i) wt[(long)(a * nk + i) * 128] = i < s.N ? (float)(inv * uc[a * s.N + i]) : 0.f;
 }
 
-// tetrahedral tensor-core path: the wind on the vector Dubiner basis scaled by
-// 1/det J in the row layout (component c of element e in row tc3_row, tile of 40
-// elements, [tile][i][128]) and the frozen reference flux at the facet points,
-// (1/det J) w^f_q (u^ . -grad lambda_f), tile-blocked [tile][f][q][40]
-__global__ void wind_tc3_kernel(DevMesh m, const double* __restrict__ u, float* __restrict__ wc3,
+// tetrahedral tensor-core path, step 1: the wind on the vector Dubiner basis scaled
+// by 1/det J, FP64, tile-blocked [tile][d][i][40] (tile of 40 elements), and the
+// frozen reference flux at the facet points, (1/det J) w^f_q (u^ . -grad lambda_f),
+// tile-blocked [tile][f][q][40]
+__global__ void wind_tc3_kernel(DevMesh m, const double* __restrict__ u, double* __restrict__ uc3,
                                 float* __restrict__ fw3) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m.E) return;
@@ -171,7 +171,7 @@ __global__ void wind_tc3_kernel(DevMesh m, const double* __restrict__ u, float* 
   const double inv = 1.0 / m.detJ[e];
   const int tile = e / 40, el = e % 40;
   for (int c = 0; c < 3; ++c)
-    for (int i = 0; i < N; ++i) wc3[((size_t)tile * N + i) * 128 + tc3_row(el, c)] = (float)(inv * uc[c * N + i]);
+    for (int i = 0; i < N; ++i) uc3[(((size_t)tile * 3 + c) * N + i) * 40 + el] = inv * uc[c * N + i];
   float* fb = fw3 + (size_t)tile * s.NF * s.QF * 40 + el;
   for (int f = 0; f < s.NF; ++f)
     for (int q = 0; q < s.QF; ++q) {
@@ -185,6 +185,30 @@ __global__ void wind_tc3_kernel(DevMesh m, const double* __restrict__ u, float* 
       }
       fb[(size_t)(f * s.QF + q) * 40] = (float)(inv * m.wf[q] * acc);
     }
+}
+
+// step 2: the wind at the volume points, u_d(xi_q) = sum_i psi^_i(xi_q) uc3[d][i],
+// in FP64, rounded once, in chunks of 16 points [tile][chunk][d][16][40]; padding
+// points and elements past E are zero
+__global__ void wind_pts_tc3_kernel(DevMesh m, const double* __restrict__ uc3, float* __restrict__ wq3,
+                                    long total) {
+  const long o = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= total) return;
+  const Sizes& s = m.s;
+  const int N = s.N, nch = (s.QV + 15) / 16;
+  const int el = (int)(o % 40);
+  const int qq = (int)((o / 40) % 16);
+  const int d = (int)((o / 640) % 3);
+  const long tj = o / 1920;
+  const long tile = tj / nch;
+  const int q = (int)(tj % nch) * 16 + qq;
+  double acc = 0.0;
+  if (q < s.QV && tile * 40 + el < m.E) {
+    const double* uc = uc3 + ((size_t)tile * 3 + d) * N * 40 + el;
+    const double* B = m.Bv + (size_t)q * N;
+    for (int i = 0; i < N; ++i) acc += B[i] * uc[(size_t)i * 40];
+  }
+  wq3[o] = (float)acc;
 }
 
 // w_{c,i} = (1/det J) sum_a J[c][a] uc[a][i]   (= (1/|det J|) int_T u_c psi_i)
@@ -666,9 +690,11 @@ cudaError_t launch_wind_prep(const DevMesh& m, const double* u, void* Uw, void* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_wind_tc3(const DevMesh& m, const double* u, float* wc3, float* fw3, cudaStream_t s) {
+cudaError_t launch_wind_tc3(const DevMesh& m, const double* u, double* uc3, float* wq3, float* fw3, cudaStream_t s) {
   if (m.E == 0) return cudaSuccess;
-  wind_tc3_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, u, wc3, fw3);
+  wind_tc3_kernel<<<grid_for(m.E), BLOCK, 0, s>>>(m, u, uc3, fw3);
+  const long total = wind_pts_tc3_len(m.s.QV, m.E);
+  wind_pts_tc3_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(m, uc3, wq3, total);
   return cudaGetLastError();
 }
 

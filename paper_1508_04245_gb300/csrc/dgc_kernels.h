@@ -87,7 +87,10 @@ cudaError_t launch_tc3_in(int K, const double* v, double* vt, float* vft, float*
 cudaError_t launch_tc3_out(int K, const double* vt, double* v, int E, cudaStream_t s);
 // wind rows [tile][i][128] (component c of element e in row tc3_row, scaled by
 // 1/det J) and the facet flux [tile][f][q][40] of the frozen wind
-cudaError_t launch_wind_tc3(const DevMesh& m, const double* u_hdiv, float* wc3, float* fw3, cudaStream_t s);
+// tetrahedral tensor-core path: the wind coefficients (FP64 scratch uc3, tiles x 3 x N x 40),
+// the wind at the volume points (wq3, wind_pts_tc3_len floats) and the facet flux (fw3)
+cudaError_t launch_wind_tc3(const DevMesh& m, const double* u_hdiv, double* uc3, float* wq3, float* fw3, cudaStream_t s);
+inline long wind_pts_tc3_len(int QV, long E) { return (E + 39) / 40 * ((QV + 15) / 16) * 1920L; }
 int tc_nk(int D, int K);
 // P: 0 = TF32 head/tail (3 products), 1 = BF16 three pieces (6 products)
 std::vector<float> tc_blob(int D, int K, int P, const Tables& t);

@@ -86,10 +86,17 @@ struct StageTcArgs {
   double tau, ds;
   double* partials;     // [tiles]
   // tetrahedra (stage_tc3_kernel): the frozen facet flux in tile blocks
-  // [tile][f][q][40] and the FP32 facet tables (Ef, Qt); blob then holds the
-  // BF16 table chunks and every state vector the row layout of TcLayout3D
+  // [tile][f][q][40], the FP32 facet tables (Ef, Qt) and the wind at the volume
+  // points; blob then holds the BF16 table chunks, wcoef is unused and every
+  // state vector has the row layout of TcLayout3D
   const float* fw3;
   const float* ftab;
+  const float* wq3;     // the wind at the volume points, [tile][chunk][d][16][40]
+  // bounded waits: polls of an mbarrier before a wait gives up (0 = 2^26); stall != 0
+  // (a test hook) issues no bulk copy at all, so every wait runs out with nothing in
+  // flight and the kernel reports the timeout in bit 1 of the status word
+  uint32_t poll;
+  int stall;
 };
 
 namespace tcimpl {
@@ -197,6 +204,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   uint64_t* bar_ep = bars + 4;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const uint32_t poll = a.poll ? a.poll : (1u << 26);   // polls per bounded wait
   double* red = reinterpret_cast<double*>(bars + 6);   // per-warp sums of mode 3 (8)
 
   // threads 0..255: (element row r of the tile, velocity component c); warps
@@ -260,7 +268,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     tc::mbar_fence_init();
   }
   __syncthreads();
-  if (t == issuer_t) {
+  if (t == issuer_t && !a.stall) {
     tc::mbar_arrive_expect_tx(bar_tab, L::BLOB * 4);
     tc::bulk_g2s(blob, a.blob, L::BLOB * 4, bar_tab);
     load_wind(blockIdx.x);
@@ -277,7 +285,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   const uint32_t lane_base = tbase + ((uint32_t)((warp & 3) * 32) << 16);
-  if (!tc::mbar_wait(bar_tab, 0)) *abort_flag = 1;
+  if (!tc::mbar_wait(bar_tab, 0, poll)) *abort_flag = 1;
   const float* G = blob + L::oG;     // [QV][2][NP4]
   const float* Ef = blob + L::oEf;   // [NF][NFM][NP4]
   const float* Qt = blob + L::oQt;   // [QF][NFM4]
@@ -292,7 +300,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
 
     // ---- stage input v^n + din (staged by bulk copy) -> state operand of component c
     if (producer) {
-    if (*abort_flag == 0 && !tc::mbar_wait(bar_st, it & 1)) *abort_flag = 1;
+    if (*abort_flag == 0 && !tc::mbar_wait(bar_st, it & 1, poll)) *abort_flag = 1;
     float w[NK];
 #pragma unroll
     for (int i = 0; i < NK; ++i) {
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     __syncthreads();   // the staged state has been read: its space takes the wind operands
     if (producer) {
     // ---- wind operand of dimension d = c from the staged coefficients --------------
-    if (*abort_flag == 0 && !tc::mbar_wait(bar_w, it & 1)) *abort_flag = 1;
+    if (*abort_flag == 0 && !tc::mbar_wait(bar_w, it & 1, poll)) *abort_flag = 1;
     float x[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) x[k] = valid ? wst[(c * NK + k) * 128 + r] : 0.f;   // conflict-free
@@ -360,7 +368,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
         tn[f][m] = code >= 0 ? tr_in[tr_index(ne, c, fn, m, NFM)] : 0.f;
       }
     }
-    if (producer && run && *abort_flag == 0 && !tc::mbar_wait(bar_A, it & 1)) *abort_flag = 1;
+    if (producer && run && *abort_flag == 0 && !tc::mbar_wait(bar_A, it & 1, poll)) *abort_flag = 1;
     tc::fence_after_sync();
     __syncthreads();
     const bool run2 = *abort_flag == 0;
@@ -481,7 +489,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
 #pragma unroll
     for (int i = 0; i < N; ++i)
       ex[i] = (producer && valid && a.mode == 1) ? v_state[tsoa_index(e, c, i, N)] : 0.0;
-    if (producer && run2 && (epi_vf || epi_din) && *abort_flag == 0 && !tc::mbar_wait(bar_ep, it & 1))
+    if (producer && run2 && (epi_vf || epi_din) && *abort_flag == 0 && !tc::mbar_wait(bar_ep, it & 1, poll))
       *abort_flag = 1;
     tc::fence_before_sync();
     __syncthreads();
@@ -551,9 +559,9 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   }
   // bulk copies still in flight (only after a timeout) land before the CTA exits
   if (t == issuer_t) {
-    if (st_issued) tc::mbar_wait(bar_st, (st_issued - 1) & 1);
-    if (ep_issued) tc::mbar_wait(bar_ep, (ep_issued - 1) & 1);
-    if (w_issued) tc::mbar_wait(bar_w, (w_issued - 1) & 1);
+    if (st_issued) tc::mbar_wait(bar_st, (st_issued - 1) & 1, poll);
+    if (ep_issued) tc::mbar_wait(bar_ep, (ep_issued - 1) & 1, poll);
+    if (w_issued) tc::mbar_wait(bar_w, (w_issued - 1) & 1, poll);
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -15,26 +15,53 @@ std::vector<unsigned char> chunks_t(const Tables& t) {
   using L = TcLayout3D<K>;
   constexpr int N = L::N, QV = L::QV;
   std::vector<unsigned char> b((size_t)L::NCH * L::CH_BYTES, 0);
-  auto put = [&](size_t piece0, size_t piece_bytes, size_t off, double x) {
-    uint16_t p[3];
-    bf16x3_pieces(x, p);
-    for (int k = 0; k < 3; ++k) std::memcpy(b.data() + piece0 + k * piece_bytes + off, &p[k], 2);
+  // head pieces on the grid of a table column, 2^(f - 8) for the largest magnitude
+  // 2^f x [0.5, 1) in the column (integers of at most 256 units, exact in BF16),
+  // the remainder (exact in FP64) in two BF16 pieces, so head x head products with
+  // the grid-aligned operand rows sum exactly in FP32
+  auto grid_of = [](double mx) {
+    int ex = 0;
+    std::frexp(mx, &ex);
+    return mx > 0.0 ? std::ldexp(1.0, ex - 8) : 1.0;
+  };
+  auto put_grid = [&](size_t piece0, size_t piece_bytes, size_t off, double x, double g) {
+    const double hd = std::nearbyint(x / g) * g;
+    uint16_t ph[3], pr[3];
+    bf16x3_pieces(hd, ph);
+    bf16x3_pieces(x - hd, pr);
+    const uint16_t pc[3] = {ph[0], pr[0], pr[1]};
+    for (int k = 0; k < 3; ++k) std::memcpy(b.data() + piece0 + k * piece_bytes + off, &pc[k], 2);
   };
   for (int j = 0; j < L::NCH; ++j) {
     const size_t base = (size_t)j * L::CH_BYTES;
     for (int n = 0; n < L::QC; ++n) {
       const int q = j * L::QC + n;
       if (q >= QV) break;   // padding points: zero rows and columns
-      // GEMM A table: row n (point), K index k (basis function), K-major core matrices
+      // GEMM A table: row n (point), K index k (basis function), K-major core matrices;
+      // its column of the product is the point, the grid the point's
+      double mx = 0.0;
+      for (int k = 0; k < N; ++k) mx = std::max(mx, std::fabs(t.Bv[(size_t)q * N + k]));
+      const double g = grid_of(mx);
       for (int k = 0; k < N; ++k)
-        put(base + L::oBA, L::szBA, (size_t)((n & 7) * 16 + (n >> 3) * L::SBO_A + (k & 7) * 2 + (k >> 3) * 128),
-            t.Bv[(size_t)q * N + k]);
-      // GEMM B tables, one per direction d: row i (basis function), K index n (point)
+        put_grid(base + L::oBA, L::szBA, (size_t)((n & 7) * 16 + (n >> 3) * L::SBO_A + (k & 7) * 2 + (k >> 3) * 128),
+                 t.Bv[(size_t)q * N + k], g);
+    }
+    // GEMM B tables, one per direction d: row i (basis function), K index n (point);
+    // the column of the product is the basis function, its grid taken over the chunk's
+    // 3 x 16 entries
+    auto G = [&](int n, int i, int d) {
+      const int q = j * L::QC + n;
+      return q < QV ? -t.wv[q] * t.Gv[((size_t)q * N + i) * 3 + d] : 0.0;
+    };
+    for (int i = 0; i < N; ++i) {
+      double mx = 0.0;
       for (int d = 0; d < 3; ++d)
-        for (int i = 0; i < N; ++i)
-          put(base + L::oBG + (size_t)d * 3 * L::szBG, L::szBG,
-              (size_t)((i & 7) * 16 + (i >> 3) * L::SBO_G + (n & 7) * 2 + (n >> 3) * 128),
-              -t.wv[q] * t.Gv[((size_t)q * N + i) * 3 + d]);
+        for (int n = 0; n < L::QC; ++n) mx = std::max(mx, std::fabs(G(n, i, d)));
+      const double g = grid_of(mx);
+      for (int d = 0; d < 3; ++d)
+        for (int n = 0; n < L::QC; ++n)
+          put_grid(base + L::oBG + (size_t)d * 3 * L::szBG, L::szBG,
+                   (size_t)((i & 7) * 16 + (i >> 3) * L::SBO_G + (n & 7) * 2 + (n >> 3) * 128), G(n, i, d), g);
     }
   }
   return b;

@@ -13,25 +13,26 @@
 //
 // One persistent CTA per SM, 640 threads in four roles that work on
 // different tiles at the same time:
-//   volume warps 0-7 (two threads per GEMM row): write the tile's state and
-//     wind operands into TMEM, then per chunk of 16 volume points read the
-//     evaluated state and wind (GEMM A), exchange the wind components of an
-//     element by warp shuffles, and write the products u_d w_c, split into
-//     BF16 pieces, into TMEM as the A operand of GEMM B;
+//   volume warps 0-7 (two threads per GEMM row): write the tile's state
+//     operand into TMEM, then per chunk of 16 volume points read the evaluated
+//     state (GEMM A) and the wind there (a shared-memory ring), and write the
+//     products u_d w_c, split into BF16 pieces on the row's grid for the chunk
+//     (both threads of a row form all 48 products and take the same largest
+//     magnitude), into TMEM as the A operand of GEMM B;
 //   facet warps 8-15 (two threads per row, facets 2h, 2h + 1): the upwind
 //     facet terms of a tile on CUDA cores from the facet traces of the stage
 //     input (the own ones and the neighbour's, written by the previous stage)
 //     while its volume part runs, then the epilogue once GEMM B has finished:
 //     the increment, in the last stage of a substep the FP64 accumulation, and
 //     the facet traces of the stage output;
-//   warp 16: the bulk copies (table chunks through a ring of shared-memory
-//     slots, the tiles' facet flux blocks, L2 prefetch of the next tile);
+//   warp 16: the bulk copies (table chunks and the chunks' wind blocks through
+//     rings of shared-memory slots, the tiles' facet flux blocks, L2 prefetch
+//     of the next tile), issued as their slots free up;
 //   warps 17-19: one thread each issues the MMAs of GEMM A (even, odd chunks)
 //     and of GEMM B -- a single issuing thread sustains only about one
-//     tcgen05.mma per 50 cycles, so the independent chains of the two chunk
-//     parities of GEMM A are issued from separate warps.
+//     tcgen05.mma per 50 cycles, so independent chains come from separate warps.
 // Two TMEM buffers each for the GEMM A results, the GEMM B operands and the
-// GEMM B chunk partials (summed by the volume warps, round to nearest) let the
+// GEMM B head partials (summed by the volume warps, round to nearest) let the
 // volume warps run a tile ahead of the facet warps.  Every
 // mbarrier wait is bounded; a timeout sets bit 1 of the status word, every
 // role stops at its next check, in-flight copies and MMAs are drained and TMEM
@@ -51,14 +52,44 @@ namespace tc3impl {
 // named barrier of the 256 facet-warp threads
 __device__ __forceinline__ void fw_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// the three BF16 pieces of NK values into TMEM columns col, col + NKC, col + 2 NKC
+// the grid 2^(e - 8) of a group of values whose largest magnitude is mx = f 2^e
+// (f in [0.5, 1)): heads rint(x / g) g are then integers of at most 256 grid
+// units, exact in BF16 (g = 1 for an all-zero group)
+__device__ __forceinline__ void grid_of(float mx, float& g, float& gi) {
+  int ex = 0;
+  frexpf(mx, &ex);
+  ex = ex < -100 ? -100 : ex;
+  g = mx > 0.f ? ldexpf(1.f, ex - 8) : 1.f;
+  gi = mx > 0.f ? ldexpf(1.f, 8 - ex) : 1.f;
+}
+
+// two values split exactly into BF16 pieces: the head on the grid g, the remainder
+// (exact in FP32) rounded into a middle and a low piece; lower value in the low half
+__device__ __forceinline__ void split_grid(float a, float b, float g, float gi, uint32_t& hw, uint32_t& mw,
+                                           uint32_t& lw) {
+  const float ha = rintf(a * gi) * g, hb = rintf(b * gi) * g;
+  hw = tcimpl::bf16x2_rn(ha, hb);   // exact
+  const float ra = a - ha, rb = b - hb;   // exact
+  mw = tcimpl::bf16x2_rn(ra, rb);
+  lw = tcimpl::bf16x2_rn(ra - __uint_as_float(mw << 16), rb - __uint_as_float(mw & 0xFFFF0000u));
+}
+
+// the three BF16 pieces of NK values into TMEM columns col, col + NKC, col + 2 NKC,
+// heads on the grid of the largest |x|; of the groups of 8 values the caller
+// writes those of parity part (the two threads of a row share the work)
 template <int NK, int NKC>
-__device__ __forceinline__ void put3_tmem(uint32_t taddr, const float* x) {
+__device__ __forceinline__ void put3_tmem(uint32_t taddr, const float* x, int part) {
+  float mx = 0.f;
+#pragma unroll
+  for (int k = 0; k < NK; ++k) mx = fmaxf(mx, fabsf(x[k]));
+  float g, gi;
+  grid_of(mx, g, gi);
 #pragma unroll
   for (int k8 = 0; k8 < NK; k8 += 8) {
+    if (((k8 >> 3) & 1) != part) continue;
     uint32_t hw[4], mw[4], lw[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) tcimpl::split3_bf16x2(x[k8 + 2 * j], x[k8 + 2 * j + 1], hw[j], mw[j], lw[j]);
+    for (int j = 0; j < 4; ++j) split_grid(x[k8 + 2 * j], x[k8 + 2 * j + 1], g, gi, hw[j], mw[j], lw[j]);
     tc::tmem_st4(taddr + k8 / 2, hw[0], hw[1], hw[2], hw[3]);
     tc::tmem_st4(taddr + NKC + k8 / 2, mw[0], mw[1], mw[2], mw[3]);
     tc::tmem_st4(taddr + 2 * NKC + k8 / 2, lw[0], lw[1], lw[2], lw[3]);
@@ -78,6 +109,7 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
   float* fws = reinterpret_cast<float*>(smb + L::oFws);
   float* phis = reinterpret_cast<float*>(smb + L::oPhi);
   float* xs = reinterpret_cast<float*>(smb + L::oXs);
+  float* wnd = reinterpret_cast<float*>(smb + L::oWnd);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smb + L::oBar);
   uint64_t* bar_tab = bars + 0;       // [4] table chunk landed
   uint64_t* bar_tfree = bars + 4;     // [4] table slot free (GEMM B of its chunk done)
@@ -96,6 +128,9 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 28);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 29);
   volatile int* fw_stop = reinterpret_cast<volatile int*>(bars + 30);
+  uint64_t* bar_wnd = bars + 31;      // [4] wind block of a chunk landed
+  uint64_t* bar_wfree = bars + 35;    // [4] wind slot consumed (8 volume warps)
+  const uint32_t poll = a.poll ? a.poll : (1u << 26);   // polls per bounded wait
 
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
@@ -120,6 +155,10 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
       tc::mbar_init(bar_rfree + i, 8);
       tc::mbar_init(bar_fws + i, 1);
       tc::mbar_init(bar_fwsfree + i, 8);
+    }
+    for (int i = 0; i < L::WSLOTS; ++i) {
+      tc::mbar_init(bar_wnd + i, 1);
+      tc::mbar_init(bar_wfree + i, 8);
     }
     tc::mbar_init(bar_ftab, 1);
     tc::mbar_init(bar_fin, 3);   // the three MMA-issuing threads
@@ -153,161 +192,194 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
       };
       auto slot = [&](int g) { return L::RESIDENT ? g % NCH : g % SLOTS; };
       auto tab_ready = [&](int g) {   // the table chunk of use g has landed
-        return tc::mbar_wait(bar_tab + slot(g), L::RESIDENT ? 0u : (uint32_t)((g / SLOTS) & 1));
+        return tc::mbar_wait(bar_tab + slot(g), L::RESIDENT ? 0u : (uint32_t)((g / SLOTS) & 1), poll);
       };
       // products of pieces (A piece, B piece), smallest first (see the triangle kernel)
       constexpr int PA[6] = {1, 2, 0, 1, 0, 0}, PB[6] = {1, 0, 2, 0, 1, 0};
       if (role == 0) {
-        // ---- producer: table chunks through the ring, the tiles' facet flux blocks,
-        //      L2 prefetch of the next tile's streamed inputs ----------------------------
-        int ld = 0;                  // table loads issued
-        int fws_ld[2] = {0, 0};      // flux block loads issued per buffer
+        // ---- producer: table chunks and wind blocks through their rings, the tiles'
+        //      facet flux blocks, L2 prefetch of a tile's streamed inputs; each copy is
+        //      issued as soon as its slot is free (polled, so that no full ring holds
+        //      up the others) --------------------------------------------------------
+        int ld = 0;      // table loads issued
+        int wl = 0;      // wind loads issued
+        int fl = 0;      // flux block loads issued (tiles)
         auto load_chunk = [&](int Lx) {
           const int s2 = slot(Lx);
           tc::mbar_arrive_expect_tx(bar_tab + s2, L::CH_BYTES);
           tc::bulk_g2s(ring + (size_t)s2 * L::CH_BYTES, chunks + (size_t)(Lx % NCH) * L::CH_BYTES, L::CH_BYTES,
                        bar_tab + s2);
         };
+        auto load_wind = [&](int g) {
+          const int s2 = g % L::WSLOTS;
+          const int tile = blockIdx.x + (g / NCH) * gridDim.x;
+          tc::mbar_arrive_expect_tx(bar_wnd + s2, L::WCH * 4);
+          tc::bulk_g2s(wnd + (size_t)s2 * L::WCH, a.wq3 + ((size_t)tile * NCH + g % NCH) * L::WCH, L::WCH * 4,
+                       bar_wnd + s2);
+        };
         auto load_fws = [&](int itl) {
           const int b = itl & 1;
           const int tile = blockIdx.x + itl * gridDim.x;
           tc::mbar_arrive_expect_tx(bar_fws + b, L::FWS * 4);
           tc::bulk_g2s(fws + b * L::FWS, a.fw3 + (size_t)tile * L::FWS, L::FWS * 4, bar_fws + b);
-          ++fws_ld[b];
         };
         auto prefetch_tile = [&](int itl) {
           const int tile = blockIdx.x + itl * gridDim.x;
           const uint32_t blk = (uint32_t)N * 128 * 4;
           tc::bulk_prefetch_l2(vf_in + (size_t)tile * N * 128, blk);
-          tc::bulk_prefetch_l2(a.wcoef + (size_t)tile * N * 128, blk);
           if (a.din) tc::bulk_prefetch_l2(a.din + (size_t)tile * N * 128, blk);
           tc::bulk_prefetch_l2(tr_in + (size_t)tile * L::NF * 128 * NFM4, (uint32_t)L::NF * 128 * NFM4 * 4);
           if (a.mode == 1) tc::bulk_prefetch_l2(a.v + (size_t)tile * N * 128, 2 * blk);
         };
-        tc::mbar_arrive_expect_tx(bar_ftab, L::FWT * 4);
-        tc::bulk_g2s(const_cast<float*>(fwt), a.ftab, L::FWT * 4, bar_ftab);
-        if (nmy > 0) {
+        const int nmy_ld = a.stall ? 0 : nmy;   // the stall hook issues no copy at all
+        if (!a.stall) {
+          tc::mbar_arrive_expect_tx(bar_ftab, L::FWT * 4);
+          tc::bulk_g2s(const_cast<float*>(fwt), a.ftab, L::FWT * 4, bar_ftab);
+        }
+        if (nmy_ld > 0) {
           const int first = L::RESIDENT ? NCH : (total < SLOTS ? total : SLOTS);
           for (; ld < first; ++ld) load_chunk(ld);
-          load_fws(0);
-          if (nmy > 1) load_fws(1);
-          prefetch_tile(0);
         }
-        for (int it = 0; it < nmy && ok; ++it) {
-          if (it >= 2) {   // the flux block of tile it into the buffer tile it - 2 has released
-            if (!tc::mbar_wait(bar_fwsfree + (it & 1), ((it >> 1) - 1) & 1)) {
-              fail();
-              break;
-            }
-            load_fws(it);
+        const int total_ld = nmy_ld * NCH;
+        const int ldn = L::RESIDENT ? ld : total_ld;   // table loads in all
+        uint32_t idle = 0;
+        while (ok && (fl < nmy_ld || wl < total_ld || ld < ldn)) {
+          bool moved = false;
+          // the flux block of tile fl into the buffer tile fl - 2 has released
+          if (fl < nmy_ld && (fl < 2 || tc::mbar_try_wait(bar_fwsfree + (fl & 1), ((fl >> 1) - 1) & 1))) {
+            load_fws(fl);
+            prefetch_tile(fl);
+            ++fl;
+            moved = true;
           }
-          if (it + 1 < nmy) prefetch_tile(it + 1);
-          if (!L::RESIDENT) {   // the table chunks up to the end of tile it + 1, each into a freed slot
-            const int upto = (it + 2) * NCH < total ? (it + 2) * NCH : total;
-            for (; ld < upto && ok; ++ld) {
-              if (ld >= SLOTS && !tc::mbar_wait(bar_tfree + ld % SLOTS, ((ld / SLOTS) - 1) & 1)) {
-                fail();
-                break;
-              }
-              load_chunk(ld);
-            }
+          // the wind block of chunk use wl into the slot use wl - WSLOTS has released
+          if (wl < total_ld &&
+              (wl < L::WSLOTS || tc::mbar_try_wait(bar_wfree + wl % L::WSLOTS, ((wl / L::WSLOTS) - 1) & 1))) {
+            load_wind(wl);
+            ++wl;
+            moved = true;
+          }
+          // the table chunk of use ld into the slot use ld - SLOTS has released
+          if (ld < ldn && tc::mbar_try_wait(bar_tfree + ld % SLOTS, ((ld / SLOTS) - 1) & 1)) {
+            load_chunk(ld);
+            ++ld;
+            moved = true;
+          }
+          if (moved) {
+            idle = 0;
+          } else if (++idle > poll || *abort_flag) {
+            fail();
           }
         }
         // drain: the copies still in flight land before the CTA exits
         if (L::RESIDENT) {
-          if (nmy > 0)
-            for (int j = 0; j < NCH; ++j) tc::mbar_wait(bar_tab + j, 0);
+          if (nmy_ld > 0)
+            for (int j = 0; j < NCH; ++j) tc::mbar_wait(bar_tab + j, 0, poll);
         } else {
           for (int Lx = ld - SLOTS > 0 ? ld - SLOTS : 0; Lx < ld; ++Lx)
-            tc::mbar_wait(bar_tab + Lx % SLOTS, (Lx / SLOTS) & 1);
+            tc::mbar_wait(bar_tab + Lx % SLOTS, (Lx / SLOTS) & 1, poll);
         }
-        for (int b = 0; b < 2; ++b)
-          if (fws_ld[b]) tc::mbar_wait(bar_fws + b, (fws_ld[b] - 1) & 1);
-        tc::mbar_wait(bar_ftab, 0);
+        for (int g = wl - L::WSLOTS > 0 ? wl - L::WSLOTS : 0; g < wl; ++g)
+          tc::mbar_wait(bar_wnd + g % L::WSLOTS, (g / L::WSLOTS) & 1, poll);
+        for (int itl = fl - 2 > 0 ? fl - 2 : 0; itl < fl; ++itl) tc::mbar_wait(bar_fws + (itl & 1), (itl >> 1) & 1, poll);
+        if (!a.stall) tc::mbar_wait(bar_ftab, 0, poll);
+        if (a.stall) fail();
       } else if (role <= 2) {
-        // ---- GEMM A of the chunk uses of parity p: state and wind at 16 volume points -----
+        // ---- GEMM A of the chunk uses of parity p: the state at 16 volume points --------
         const int p = role - 1;
         const uint32_t idA = tc::idesc_bf16(128, 16);
         int cur = -1;   // the tile whose operands this issuer has seen written
         for (int g = p; g < total && ok; g += 2) {
           const int it = g / NCH;
           if (it != cur) {
-            if (!tc::mbar_wait(bar_ops, it & 1)) {
+            if (!tc::mbar_wait(bar_ops, it & 1, poll)) {
               fail();
               break;
             }
             cur = it;
           }
-          if (!tab_ready(g) || (g >= 2 && !tc::mbar_wait(bar_xfree + p, ((g >> 1) - 1) & 1))) {
+          if (!tab_ready(g) || (g >= 2 && !tc::mbar_wait(bar_xfree + p, ((g >> 1) - 1) & 1, poll))) {
             fail();
             break;
           }
           tc::fence_after_sync();
           const uint32_t sa = ring_s + (uint32_t)slot(g) * L::CH_BYTES + L::oBA;
-#pragma unroll 1
-          for (int fld = 0; fld < 2; ++fld) {
-            const uint32_t dcol = tbase + L::cX + p * L::XCOLS + fld * 16;
-            const uint32_t acol = tbase + (fld ? L::cAw : L::cAs);
+          {
+            // [hh | corr]: the grid-aligned head x head sum (exact), then the five correction
+            // products smallest first
+            const uint32_t dcol = tbase + L::cX + p * L::XCOLS;
+            const uint32_t acol = tbase + L::cAs;
             const uint64_t bd0 = tc::smem_desc(sa, 128, L::SBO_A);
 #pragma unroll
-            for (int pr = 0; pr < 6; ++pr)
+            for (int ks = 0; ks < NK / 16; ++ks)   // the address field of a descriptor is address / 16
+              tc::mma_bf16_ts(dcol, acol + ks * 8, bd0 + (uint64_t)((ks * 256) >> 4), idA, ks != 0);
 #pragma unroll
-              for (int ks = 0; ks < NK / 16; ++ks)   // the address field of a descriptor is address / 16
-                tc::mma_bf16_ts(dcol, acol + PA[pr] * NKC + ks * 8, bd0 + (uint64_t)((PB[pr] * L::szBA + ks * 256) >> 4),
-                                idA, (pr | ks) != 0);
+            for (int pr = 0; pr < 5; ++pr)
+#pragma unroll
+              for (int ks = 0; ks < NK / 16; ++ks)
+                tc::mma_bf16_ts(dcol + 16, acol + PA[pr] * NKC + ks * 8,
+                                bd0 + (uint64_t)((PB[pr] * L::szBA + ks * 256) >> 4), idA, (pr | ks) != 0);
           }
           tc::mma_commit(bar_x + p);
           if (!L::RESIDENT) tc::mma_commit(bar_tfree + slot(g));
           if (g + 2 >= (it + 1) * NCH) tc::mma_commit(bar_afree);   // this issuer's last chunk of the tile
         }
         tc::mma_commit(bar_fin);
-        tc::mbar_wait(bar_fin, 0);
+        tc::mbar_wait(bar_fin, 0, poll);
       } else {
-        // ---- GEMM B of every chunk use: the test contraction into a fresh partial ------
+        // ---- GEMM B of every chunk use: the head x head sum (exact) into a fresh partial,
+        //      the correction products into the tile's correction accumulator ---------
         const uint32_t idB = tc::idesc_bf16(128, NR);
         for (int g = 0; g < total && ok; ++g) {
           const int p = g & 1;
-          if (!tab_ready(g) || !tc::mbar_wait(bar_p + p, (g >> 1) & 1)) {
+          if (!tab_ready(g) || !tc::mbar_wait(bar_p + p, (g >> 1) & 1, poll)) {
             fail();
             break;
           }
           tc::fence_after_sync();
           const uint64_t bd0 = tc::smem_desc(ring_s + (uint32_t)slot(g) * L::CH_BYTES + L::oBG, 128, L::SBO_G);
+          const uint32_t pa = tbase + L::cP + p * L::PCOLS;
 #pragma unroll
-          for (int pr = 0; pr < 6; ++pr)
+          for (int d = 0; d < 3; ++d)
+            tc::mma_bf16_ts(tbase + L::cRh + p * NR, pa + d * 24, bd0 + (uint64_t)((d * 3 * L::szBG) >> 4), idB,
+                            d != 0);
+          const bool first = g % NCH == 0;   // the tile's first chunk starts the correction sum
+#pragma unroll
+          for (int pr = 0; pr < 5; ++pr)
 #pragma unroll
             for (int d = 0; d < 3; ++d)
-              tc::mma_bf16_ts(tbase + L::cRp + p * NR, tbase + L::cP + p * L::PCOLS + (d * 3 + PA[pr]) * 8,
-                              bd0 + (uint64_t)(((d * 3 + PB[pr]) * L::szBG) >> 4), idB, (pr | d) != 0);
+              tc::mma_bf16_ts(tbase + L::cRc, pa + (d * 3 + PA[pr]) * 8,
+                              bd0 + (uint64_t)(((d * 3 + PB[pr]) * L::szBG) >> 4), idB, !first || (pr | d) != 0);
           tc::mma_commit(bar_pfree + p);
           if (!L::RESIDENT) tc::mma_commit(bar_tfree + slot(g));
         }
         tc::mma_commit(bar_fin);
-        tc::mbar_wait(bar_fin, 0);
+        tc::mbar_wait(bar_fin, 0, poll);
       }
       if (!ok) atomicOr(a.status, 2);
     }
   } else if (warp < 8) {
     // ============================ volume warps ===================================
     const int r = t & 127, h = t >> 7;
-    const int rg = r >> 5, ln = r & 31, sl = ln / 3;
+    const int rg = r >> 5, ln = r & 31;
+    const int elw = rg * 10 + (ln < 30 ? ln / 3 : 0);   // element whose wind the row reads
     const uint32_t lb = tbase + ((uint32_t)(rg * 32) << 16);
     constexpr int NRH = NR / 2;                 // residual columns this thread sums
     const uint32_t rcol = (uint32_t)(h * NRH);
     float racc[NRH];
     bool ok = true;
     auto wait_all = [&](uint64_t* bar, uint32_t parity) -> bool {   // warp-uniform bounded wait
-      const bool w = *abort_flag == 0 && tc::mbar_wait(bar, parity);
+      const bool w = *abort_flag == 0 && tc::mbar_wait(bar, parity, poll);
       if (__all_sync(0xffffffffu, w)) return true;
       *abort_flag = 1;
       ok = false;
       return false;
     };
-    auto collect = [&](int gg) {   // add the partial of chunk use gg (GEMM B(gg) has completed)
+    auto add_cols = [&](uint32_t col) {   // racc += TMEM columns col + rcol .. + NRH - 1 of the row
 #pragma unroll
       for (int c8 = 0; c8 < NRH; c8 += 8) {
         float v8[8];
-        tc::tmem_ld8(lb + L::cRp + (gg & 1) * NR + rcol + c8, v8);
+        tc::tmem_ld8(lb + col + rcol + c8, v8);
         tc::tmem_wait_ld();
 #pragma unroll
         for (int u = 0; u < 8; ++u) racc[c8 + u] += v8[u];
@@ -318,8 +390,9 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
         const int gg = itp * NCH + jj;
         if (!wait_all(bar_pfree + (gg & 1), (gg >> 1) & 1)) return;
         tc::fence_after_sync();
-        collect(gg);
+        add_cols(L::cRh + (gg & 1) * NR);
       }
+      add_cols(L::cRc);   // the tile's correction sum (complete with its last chunk)
       if (itp >= 1 && !wait_all(bar_rfree, (itp - 1) & 1)) return;
       tc::fence_after_sync();
 #pragma unroll
@@ -333,11 +406,11 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
     };
     for (int it = 0; it < nmy && ok; ++it) {
       const int tile = blockIdx.x + it * gridDim.x;
-      const int e = tile * EPT + rg * 10 + sl;
+      const int e = tile * EPT + rg * 10 + ln / 3;
       const bool valid = ln < 30 && e < a.E;
       if (it >= 1 && !wait_all(bar_afree, (it - 1) & 1)) break;
       tc::fence_after_sync();
-      // ---- the tile's operands: h = 0 the state component c, h = 1 the wind's ------
+      // ---- the tile's state operand (both threads of a row write half of its columns) ---
       {
         float x[NK];
 #pragma unroll
@@ -346,10 +419,10 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
 #pragma unroll
           for (int i = 0; i < N; ++i) {
             const size_t ix = tc3_index(tile, i, r, N);
-            x[i] = h == 0 ? vf_in[ix] + (a.din ? a.din[ix] : 0.f) : a.wcoef[ix];
+            x[i] = vf_in[ix] + (a.din ? a.din[ix] : 0.f);
           }
         }
-        tc3impl::put3_tmem<NK, NKC>(lb + (h ? L::cAw : L::cAs), x);
+        tc3impl::put3_tmem<NK, NKC>(lb + L::cAs, x, h);
       }
       tc::tmem_wait_st();
       tc::fence_before_sync();
@@ -362,34 +435,57 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
 #pragma unroll
       for (int i = 0; i < NRH; ++i) racc[i] = 0.f;
       for (int j = 0; j < NCH; ++j) {
-        const int g = it * NCH + j, b = g & 1;
+        const int g = it * NCH + j, b = g & 1, ws = g % L::WSLOTS;
         if (!wait_all(bar_x + b, (g >> 1) & 1)) break;
         tc::fence_after_sync();
-        // this thread's 8 points of the chunk: w_c and u_c there
-        float wq[8], uq[8];
-        tc::tmem_ld8(lb + L::cX + b * L::XCOLS + 8 * h, wq);
-        tc::tmem_ld8(lb + L::cX + b * L::XCOLS + 16 + 8 * h, uq);
-        tc::tmem_wait_ld();
+        // the state at the chunk's 16 points: this thread's 8 (wo) and the partner's (wx)
+        float wo[8], wx[8];
+        {
+          float ho[8], co[8], hx[8], cx[8];
+          const uint32_t xb = lb + L::cX + b * L::XCOLS;
+          tc::tmem_ld8(xb + 8 * h, ho);
+          tc::tmem_ld8(xb + 16 + 8 * h, co);
+          tc::tmem_ld8(xb + 8 * (1 - h), hx);
+          tc::tmem_ld8(xb + 16 + 8 * (1 - h), cx);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            wo[q] = ho[q] + co[q];
+            wx[q] = hx[q] + cx[q];
+          }
+        }
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) tcimpl::mbar_arrive(bar_xfree + b);
-        // the element's three wind components from its three rows (same warp)
+        if (!wait_all(bar_wnd + ws, (g / L::WSLOTS) & 1)) break;
+        // the products u_d w_c at this thread's points, and the largest |u_d w_c| of the
+        // row over all 48 of the chunk (both threads of the row form the same products)
         float pv[3][8];
+        float mx = 0.f;
+        {
+          const float* wb = wnd + ws * L::WCH + elw;
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
+          for (int d = 0; d < 3; ++d)
 #pragma unroll
-          for (int q = 0; q < 8; ++q) pv[d][q] = __shfl_sync(0xffffffffu, uq[q], 3 * sl + d) * wq[q];
+            for (int q = 0; q < 8; ++q) {
+              pv[d][q] = wb[(d * 16 + 8 * h + q) * EPT] * wo[q];
+              const float px = wb[(d * 16 + 8 * (1 - h) + q) * EPT] * wx[q];
+              mx = fmaxf(mx, fmaxf(fabsf(pv[d][q]), fabsf(px)));
+            }
+        }
         if (g >= 2) {   // GEMM B(g - 2) is done with P[b] and its partial
           if (!wait_all(bar_pfree + b, ((g - 2) >> 1) & 1)) break;
           tc::fence_after_sync();
-          if (j >= 2) collect(g - 2);
+          if (j >= 2) add_cols(L::cRh + b * NR);
         }
+        float gs, gi;
+        tc3impl::grid_of(mx, gs, gi);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           uint32_t hw[4], mw[4], lw[4];
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj)
-            tcimpl::split3_bf16x2(pv[d][2 * jj], pv[d][2 * jj + 1], hw[jj], mw[jj], lw[jj]);
+            tc3impl::split_grid(pv[d][2 * jj], pv[d][2 * jj + 1], gs, gi, hw[jj], mw[jj], lw[jj]);
           const uint32_t pc = lb + L::cP + b * L::PCOLS + d * 24 + 4 * h;
           tc::tmem_st4(pc, hw[0], hw[1], hw[2], hw[3]);
           tc::tmem_st4(pc + 8, mw[0], mw[1], mw[2], mw[3]);
@@ -398,7 +494,12 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
         tc::tmem_wait_st();
         tc::fence_before_sync();
         __syncwarp();
-        if (lane == 0) tcimpl::mbar_arrive(bar_p + b);
+        // every value read from the wind slot has been consumed into TMEM by now, so the
+        // next bulk copy into the slot cannot overtake a read still in flight
+        if (lane == 0) {
+          tcimpl::mbar_arrive(bar_p + b);
+          tcimpl::mbar_arrive(bar_wfree + ws);
+        }
       }
     }
     if (ok && nmy > 0) finish(nmy - 1);
@@ -414,7 +515,7 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
     // coefficients of this thread in the epilogue: a 4-aligned half, [i0, i0 + NH)
     constexpr int NH = ((N + 1) / 2 + 3) / 4 * 4;
     const int i0 = h * NH;
-    bool ok = tc::mbar_wait(bar_ftab, 0);
+    bool ok = tc::mbar_wait(bar_ftab, 0, poll);
     if (!ok) *abort_flag = 1;
     for (int it = 0; it < nmy; ++it) {
       if (ft == 0) *fw_stop = *abort_flag;
@@ -424,7 +525,7 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
       const int e = tile * EPT + el;
       const bool valid = ln < 30 && e < a.E;
       const int b = it & 1;
-      bool w = *abort_flag == 0 && tc::mbar_wait(bar_fws + b, (it >> 1) & 1);
+      bool w = *abort_flag == 0 && tc::mbar_wait(bar_fws + b, (it >> 1) & 1, poll);
       if (!w) *abort_flag = 1;
       const float* fwb = fws + b * L::FWS;
       // ---- upwind facet terms of facets 2h, 2h + 1 (CUDA cores, FP32, packed pairs) ------
@@ -490,7 +591,7 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
       __syncwarp();
       if (lane == 0) tcimpl::mbar_arrive(bar_fwsfree + b);
       // ---- the tile's residual, this thread's coefficients --------------------------
-      w = *abort_flag == 0 && tc::mbar_wait(bar_r, it & 1);
+      w = *abort_flag == 0 && tc::mbar_wait(bar_r, it & 1, poll);
       if (!w) *abort_flag = 1;
       tc::fence_after_sync();
       float ri[NH];

@@ -2,23 +2,34 @@
 //
 // GEMM rows are (element, velocity component) pairs: a tile holds 40
 // elements, rows 32 g + 3 s + c for element 10 g + s (g = 0..3, s = 0..9) and
-// component c; rows 32 g + 30 and 32 g + 31 are padding.  The three rows of an
-// element sit in one warp, so the wind components another row holds come by
-// warp shuffles.  Each row carries one field of the state (its component) and
-// one of the wind (the same component), so every tcgen05 operand is one field:
+// component c; rows 32 g + 30 and 32 g + 31 are padding.  Each row carries one
+// field of the state (its component):
 //
 //   GEMM A (per chunk of 16 volume points, A from TMEM, B = basis table):
-//     X.w[r, q] = sum_j A_s[r, j] Bv[q, j]        state component c at xi_q
-//     X.u[r, q] = sum_j A_w[r, j] Bv[q, j]        wind component c / det J
+//     X[r, q] = sum_j A_s[r, j] Bv[q, j]          state component c at xi_q
 //   GEMM B (the volume test contraction, A = products from TMEM), per chunk:
 //     R_j[r, i] = sum_{d, q in chunk j} P[r, (d, q)] G[(d, q), i],  R = sum_j R_j,
 //     P[r, (d, q)] = u_d(xi_q) w_c(xi_q),  G[(d, q), i] = -w_q d_d psi^_i(xi_q)
 //
+// The wind is frozen over a call, so its values at the volume points,
+// u_d(xi_q) = (1/det J) sum_i uc[d][i] psi^_i(xi_q), are evaluated once per
+// call in FP64 (rounded to FP32) and streamed per chunk, [tile][chunk][d][16][40].
+//
 // Every operand is split exactly into three BF16 pieces (kind::f16, six
-// products, FP32 accumulation).  The tables of a chunk (Bv and the three G
-// blocks, all pieces) are one contiguous blob bulk-copied into a ring of
-// shared-memory slots; the facet terms run on CUDA cores in FP32 from the
-// facet traces of the stage input and the frozen facet flux of the wind.
+// products, FP32 accumulation), with the head pieces on a grid: the head of
+// an operand row is a multiple of 2^(e - 7), e the exponent of the largest
+// value the row contributes to one accumulation (the state coefficients of
+// the row; the 48 products P of the row in the chunk), and the head of a table
+// column a multiple of 2^(f - 7) likewise (a point of the GEMM A table; a
+// basis function i over the chunk in G).  Every head x head product is then an
+// integer multiple of 2^(e + f - 14) of at most 2^16 units and their sum over
+// K <= 48 stays below 2^22 units: exact in FP32.  That sum accumulates on its
+// own, the five correction products (about 2^-8 of it) on theirs, and the two
+// are added on CUDA cores, so the truncating accumulation of the tensor cores
+// biases neither the evaluated state nor the residual.  The tables of a chunk
+// (Bv and the three G blocks, all pieces) are one contiguous blob bulk-copied
+// into a ring of shared-memory slots; the facet terms run on CUDA cores in FP32
+// from the facet traces of the stage input and the frozen facet flux.
 #pragma once
 
 namespace dgc {
@@ -43,18 +54,18 @@ struct TcLayout3D {
   // TMEM columns (32-bit); a BF16 piece of a K = NK operand row takes NK / 2
   static constexpr int NKC = NK / 2;
   static constexpr int cAs = 0;                        // state operand, pieces h, m, l
-  static constexpr int cAw = 3 * NKC;                  // wind operand
-  static constexpr int cX = pad(6 * NKC, 16);          // two buffers: [w (16) | u (16)]
+  // GEMM A results, two buffers of [hh | corr] (16 columns each): the head-piece
+  // products accumulate apart from the five correction products
+  static constexpr int cX = pad(3 * NKC, 16);
   static constexpr int XCOLS = 32;
-  static constexpr int cP = cX + 2 * XCOLS;            // two buffers: [d][piece][8 columns]
+  static constexpr int cP = cX + 2 * XCOLS;            // GEMM B operands, two buffers: [d][piece][8 columns]
   static constexpr int PCOLS = 72;
-  // GEMM B accumulates each chunk into a fresh partial (two buffers): the tensor
-  // cores' FP32 accumulation truncates, so a single accumulator over all chunks
-  // would gather a bias of one unit in the last place per MMA; the partials are
-  // added on CUDA cores (round to nearest) and the tile's residual handed to
-  // the facet warps in cRf
-  static constexpr int cRp = cP + 2 * PCOLS;           // two chunk partials of NR columns
-  static constexpr int cRf = cRp + 2 * NR;             // the tile's residual
+  // GEMM B: the head sums of a chunk into a fresh partial (two buffers), the
+  // correction products of all chunks of a tile into one accumulator, both added
+  // on CUDA cores; then the tile's summed residual handed to the facet warps
+  static constexpr int cRh = cP + 2 * PCOLS;
+  static constexpr int cRc = cRh + 2 * NR;
+  static constexpr int cRf = cRc + NR;
   static constexpr int TMEM_USED = cRf + NR;
   static constexpr int TMEM_COLS = 512;
   static_assert(TMEM_USED <= TMEM_COLS, "tensor memory");
@@ -79,6 +90,9 @@ struct TcLayout3D {
 
   // frozen facet flux of a tile: [f][q][EPT] floats
   static constexpr int FWS = NF * QF * EPT;
+  // the wind at the 16 points of a chunk: [d][q][EPT] floats, through a ring
+  static constexpr int WCH = 3 * QC * EPT;
+  static constexpr int WSLOTS = 4;
 
   // shared memory (bytes)
   static constexpr int oRing = 0;
@@ -86,9 +100,11 @@ struct TcLayout3D {
   static constexpr int oFws = oFwt + FWT * 4;          // two tile buffers
   static constexpr int oPhi = oFws + 2 * FWS * 4;      // [f][m][128] facet projections
   static constexpr int oXs = oPhi + NF * NFM * 128 * 4;  // [i][128] stage output (for its traces)
-  static constexpr int oBar = oXs + N * 128 * 4;
+  static constexpr int oWnd = oXs + N * 128 * 4;       // wind ring, WSLOTS x WCH floats
+  static constexpr int oBar = oWnd + WSLOTS * WCH * 4;
   static constexpr int NBAR = 40;
   static constexpr int SMEM_BYTES = oBar + NBAR * 8 + 64;
+  static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 };
 
 // tile-blocked row layouts of the tetrahedral tensor-core path

@@ -122,3 +122,40 @@ def test_injected_faults_return_errors_and_leave_the_handle_usable():
     torch.cuda.synchronize()
     assert torch.equal(v, w)
     assert np.isfinite(v.cpu().numpy()).all()
+
+
+def mesh_case(dim, k, n, seed=4):
+    verts, elems = W.square_mesh(n, 0.1, seed) if dim == 2 else W.cube_mesh(n, 0.05, seed)
+    gm = dgconv.Mesh(dim, k, verts, elems)
+    pot = W.stream_random(seed + 3) if dim == 2 else W.potential_random(seed + 3)
+    wind = gm.wind_from_potential(torch.tensor(dgconv.potential_values(gm, pot), dtype=torch.float64,
+                                               device="cuda"))
+    v0 = torch.tensor(W.uniform_coeffs(seed, gm.n_elem, dim, k), dtype=torch.float64, device="cuda")
+    return verts, elems, gm, wind, v0
+
+
+@pytest.mark.parametrize("dim,k,n,prec", [(2, 3, 12, "tf32x3"), (2, 4, 12, "bf16x3"), (3, 2, 3, "bf16x3"),
+                                          (3, 4, 3, "bf16x3")])
+def test_bounded_wait_timeout_is_reported_and_handle_recovers(dim, k, n, prec):
+    """DGC_FAULT=stall: the tensor-core stage kernel issues no bulk copy, so its
+    bounded mbarrier waits run out (nothing in flight); the timeout reaches the
+    status word, dgc_check reports DGC_ERR_TIMEOUT once, and the same handle then
+    reproduces a fresh handle's run bit for bit."""
+    verts, elems, gm, wind, v0 = mesh_case(dim, k, n)
+    ds = gm.cfl_ds(wind, 0.2)
+    ref_mesh = dgconv.Mesh(dim, k, verts, elems)
+    ref = v0.clone()
+    ref_mesh.rk_substeps(wind, ref, ds, 3, 3, prec)
+    ref_mesh.check()
+    v = v0.clone()
+    with fault("stall"):
+        gm.rk_substeps(wind, v, ds, 3, 3, prec)   # launches; the waits give up on the device
+    torch.cuda.synchronize()
+    with pytest.raises(dgconv.DgcError, match="status -4"):
+        gm.check()
+    gm.check()   # the word was cleared by the report
+    v = v0.clone()
+    gm.rk_substeps(wind, v, ds, 3, 3, prec)
+    gm.check()
+    torch.cuda.synchronize()
+    assert torch.equal(v, ref)
