@@ -139,8 +139,8 @@ def test_richardson_on_parallelograms(cases):
     v = cu(np.zeros_like(g))
     iters, res = gm.richardson(cu(wind), cu(g), v, tau, ds, 1e-3, 60, "fp64")
     assert int(host(iters)[0]) == it_ref
-    assert maxrel(host(v), ref) < 1e-11
-    assert maxrel(host(res)[:it_ref + 1], hist) < 1e-11
+    assert maxrel(host(v), ref) < 1e-12
+    assert maxrel(host(res)[:it_ref + 1], hist) < 1e-12
 
 
 def test_oifs_rhs_on_parallelograms(cases):
