@@ -26,7 +26,11 @@
  *   the environment variable DGC_FAULT=alloc|capture|launch makes device
  *   allocations, graph captures or kernel launches fail on the host before the
  *   CUDA call is made; the call returns its DGC_ERR_* code and the handle stays
- *   usable.  DGC_FAULT=stall launches the tensor-core stage kernels with no
+ *   usable.  In the checked build (libdgconv_checked.so, compiled with
+ *   DGC_CHECKED=1: every neighbour code, facet DOF id and facet side is
+ *   bounds-checked on the device), DGC_FAULT=gather offsets the facet DOF ids
+ *   of element 0 out of range, which the checks catch (DGC_ERR_BOUNDS from
+ *   dgc_check); the regular build ignores it.  DGC_FAULT=stall launches the tensor-core stage kernels with no
  *   bulk copy issued and a short poll budget: their bounded waits run out with
  *   nothing in flight, the results of that call are undefined, and dgc_check
  *   then returns DGC_ERR_TIMEOUT; the handle stays usable.
@@ -92,6 +96,7 @@ typedef int dgc_status;
 #define DGC_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up */
 #define DGC_ERR_NONFINITE (-5)    /* a NaN or Inf was produced */
 #define DGC_ERR_ALLOC (-6)        /* device or host allocation failed */
+#define DGC_ERR_BOUNDS (-7)       /* a gather index was out of range (checked build only) */
 
 /* Contraction precision of the convection stages; the state is FP64 in every
  * mode.
@@ -211,6 +216,18 @@ dgc_status dgc_transfer(dgc_mesh* mesh, const double* u_hdiv, double* w_dg, void
  * result is deterministic.  f_dg: device [n_dg]; g_hdiv: device [n_hdiv],
  * overwritten.  FP64. */
 dgc_status dgc_transfer_T(dgc_mesh* mesh, const double* f_dg, double* g_hdiv, void* stream);
+
+/* Diagnostics of a DG field v (device [n_dg]), the quantities of the conservation
+ * and stability statements of Sec. 2.3: out[c] = sum_T int_T v_c dx for each of
+ * the dim components (the mass, constant in time under a divergence-free wind
+ * with no inflow), out[dim] = sum_T int_T |v|^2 dx (the energy, non-increasing
+ * under the upwind flux) and out[dim + 1] = the number of non-finite
+ * coefficients.  out: device [dim + 2], written asynchronously on `stream`.  The
+ * sums run in a fixed two-pass tree order, so a result repeats bit for bit.  A
+ * non-finite coefficient also marks the handle's status word: dgc_check then
+ * returns DGC_ERR_NONFINITE (the check for a blown-up run after
+ * dgc_rk_substeps).  All element shapes; FP64. */
+dgc_status dgc_diagnostics(dgc_mesh* mesh, const double* v_dg, double* out, void* stream);
 
 /* out = M^V v (inverse = 0) or (M^V)^-1 v (inverse = 1); M^V_T = |det J_T| Id
  * (Sec. 2.3, diagonal mass of an orthonormal basis).  device [n_dg] each;
@@ -364,9 +381,12 @@ dgc_status dgc_state_load(const dgc_mesh* mesh, const void* blob, int64_t size, 
                           int64_t* step, void* stream);
 
 /* Device-side status of the handle: synchronizes `stream`, returns
- * DGC_ERR_TIMEOUT if a bounded wait inside a kernel gave up since the last
+ * DGC_ERR_BOUNDS if a gather index was out of range (only the checked build,
+ * libdgconv_checked.so, tests them; the message names the first such index),
+ * else DGC_ERR_TIMEOUT if a bounded wait inside a kernel gave up since the last
  * check, else DGC_ERR_NONFINITE if dgc_richardson met a non-finite residual
- * norm, else DGC_OK; a reported word is cleared. */
+ * norm or dgc_diagnostics a non-finite coefficient, else DGC_OK; a reported
+ * word is cleared. */
 dgc_status dgc_check(dgc_mesh* mesh, void* stream);
 
 /* Shortest element edge of the mesh (host value, from the upload). */

@@ -316,6 +316,16 @@ def cfl_ds(cm: CurvedMesh, k, u_hdiv, cfl: float) -> float:
     return cfl * float(cm.base.shortest_edge().min()) / ((2 * k + 1) * max_wind_speed(cm, k, u_hdiv))
 
 
+def integrals(cm: CurvedMesh, k, w):
+    """mass[c] = sum_T int_T w_c dx and energy = sum_T int_T |w|^2 dx on the curved
+    mesh (Sec. 2.3), the reference rule weighted by |det J(xi_q)| of the quadratic
+    map (exact: degree 2k + 2)."""
+    xq, wq = simplex_rule(2, 2 * k + 2)
+    vals = np.einsum("eci,qi->ecq", np.asarray(w), B.dubiner_values(2, k, xq))
+    dj = np.abs(cm.detJ(np.arange(cm.n_elem), xq))
+    return np.einsum("q,eq,ecq->c", wq, dj, vals), float(np.einsum("q,eq,ecq->", wq, dj, vals ** 2))
+
+
 def dg_energy(cm: CurvedMesh, k, v) -> float:
     """||v||^2_{L2} = sum_T v_c^T M_T v_c."""
     return float(np.einsum("eci,eij,ecj->", v, cm.mass(k), v))

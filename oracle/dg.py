@@ -208,6 +208,18 @@ def mass(mesh, v) -> np.ndarray:
     return np.abs(mesh.detJ)[:, None, None] * np.asarray(v)
 
 
+def integrals(mesh, k, w):
+    """Mass and energy of a DG field, the quantities of the conservation and
+    stability statements of Sec. 2.3: mass[c] = sum_T int_T w_c dx per component,
+    energy = sum_T int_T |w|^2 dx; by a reference rule exact for degree 2k, the
+    element integral being |det J| times the reference one (affine map)."""
+    d = mesh.dim
+    xq, wq = simplex_rule(d, 2 * k)
+    vals = np.einsum("eci,qi->ecq", np.asarray(w), B.dubiner_values(d, k, xq))
+    ad = np.abs(mesh.detJ)
+    return np.einsum("e,q,ecq->c", ad, wq, vals), float(np.einsum("e,q,ecq->", ad, wq, vals ** 2))
+
+
 def upwind_energy(mesh, k, u_hdiv, w) -> float:
     """1/2 sum_F int_F |u.n| [[w]]^2 + 1/2 int_{dOmega} |u.n| w^2, by facet quadrature.
 

@@ -481,6 +481,16 @@ def cfl_ds(mesh, k, u_hdiv, cfl: float) -> float:
     return cfl * float(mesh.shortest_edge().min()) / ((2 * k + 1) * max_wind_speed(mesh, k, u_hdiv))
 
 
+def integrals(mesh, k, w):
+    """mass[c] = sum_T int_T w_c dx and energy = sum_T int_T |w|^2 dx on
+    parallelograms (Sec. 2.3), Gauss rule on [0,1]^2 exact for degree 2k per
+    direction, times |det J|."""
+    xq, wq = square_rule(k + 1)
+    vals = np.einsum("eci,qi->ecq", np.asarray(w), vbasis(k, xq))
+    ad = np.abs(mesh.detJ)
+    return np.einsum("e,q,ecq->c", ad, wq, vals), float(np.einsum("e,q,ecq->", ad, wq, vals ** 2))
+
+
 def upwind_energy(mesh, k, u_hdiv, w) -> float:
     """1/2 sum_F int_F |u.n| [[w]]^2 + 1/2 int_{dOmega} |u.n| w^2 by facet
     quadrature, both traces found by affine inversion of physical points."""

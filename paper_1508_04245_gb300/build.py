@@ -1,9 +1,11 @@
-"""Build libdgconv.so in-tree for sm_103a (GB300).
+"""Build libdgconv.so in-tree for sm_103a (GB300), and its checked twin.
 
 The C++ table builder is compiled by g++, the CUDA sources by nvcc with
 ``-gencode arch=compute_103a,code=sm_103a``; translation units compile in
-parallel and are linked against the shared CUDA runtime.  Rebuilds only when
-a source is newer than the library.
+parallel and are linked against the shared CUDA runtime.  The same sources
+compiled with ``-DDGC_CHECKED=1`` give libdgconv_checked.so, whose kernels
+bounds-check every gather index (a test build; the binding loads it when
+DGC_LIBRARY=checked).  Rebuilds only when a source is newer than a library.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdgconv.so")
+LIB_CHECKED = os.path.join(PKG, "libdgconv_checked.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,10 +41,10 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def _compile(src: str, extra=()) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra=(), outdir: str = BUILD) -> str:
+    obj = os.path.join(outdir, os.path.basename(src) + ".o")
     if src.endswith(".cpp"):
-        cmd = ["g++", "-O2", "-fPIC", "-std=c++17", "-I", INCLUDE, "-c", src, "-o", obj]
+        cmd = ["g++", "-O2", "-fPIC", "-std=c++17", "-I", INCLUDE, *extra, "-c", src, "-o", obj]
     else:
         cmd = [_nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                "-I", INCLUDE, *extra, "-c", src, "-o", obj]
@@ -50,22 +54,41 @@ def _compile(src: str, extra=()) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
-        if all(os.path.getmtime(p) <= t for p in _deps()):
-            return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
-        objs = list(ex.map(_compile, _sources()))
-    tmp = LIB + ".tmp"
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
+        return True
+    t = os.path.getmtime(lib)
+    return any(os.path.getmtime(p) > t for p in _deps())
+
+
+def _link(objs, lib: str) -> None:
+    tmp = lib + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
-    if verbose:
-        print("built", LIB)
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Both libraries (the regular and the checked one); returns the regular one's path."""
+    jobs = []
+    if force or _stale(LIB):
+        os.makedirs(BUILD, exist_ok=True)
+        jobs += [(src, (), BUILD, LIB) for src in _sources()]
+    if force or _stale(LIB_CHECKED):
+        os.makedirs(BUILD_CHECKED, exist_ok=True)
+        jobs += [(src, ("-DDGC_CHECKED=1",), BUILD_CHECKED, LIB_CHECKED) for src in _sources()]
+    if not jobs:
+        return LIB
+    with cf.ThreadPoolExecutor(max_workers=max(2, min(16, os.cpu_count() or 2))) as ex:
+        objs = list(ex.map(lambda j: (j[3], _compile(j[0], j[1], j[2])), jobs))
+    for lib in (LIB, LIB_CHECKED):
+        mine = [o for l, o in objs if l == lib]
+        if mine:
+            _link(mine, lib)
+            if verbose:
+                print("built", lib)
     return LIB
 
 

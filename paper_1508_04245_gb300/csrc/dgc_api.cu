@@ -153,6 +153,7 @@ struct dgc_mesh {
   DevBuf<double> ts0;              // tile-blocked FP64 state of the tensor-core path
   DevBuf<float> tsf, d1, d2;       // its FP32 copy and the FP32 stage increments
   DevBuf<double> ts1, tsg;         // pseudo-time solve on that path: second state, right-hand side
+  DevBuf<double> diag_mv, diag_part;   // dgc_diagnostics: M v and the per-block partial sums
   DevBuf<float> tsf1;              // and the second state's FP32 copy
   DevBuf<int> status;
   // scratch
@@ -184,6 +185,10 @@ struct dgc_mesh {
     m.detJ = detJ.ptr;
     m.nbr = nbr.ptr;
     m.facet_id = facet_id.ptr;
+    m.status = status.ptr;
+#if DGC_CHECKED
+    m.inject_bad_facet = injected("gather") ? 1 : 0;
+#endif
     m.orient = orient.ptr;
     m.facet_sides = facet_sides.ptr;
     m.Bv = Bv.ptr;
@@ -244,6 +249,8 @@ struct dgc_mesh {
     tc3chunks.release();
     fw3.release();
     wq3.release();
+    diag_mv.release();
+    diag_part.release();
     uc3.release();
     wcoef.release();
     trA.release();
@@ -330,6 +337,7 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
   a.nbr = (m->quad || m->hex) ? m->qnbr.ptr : m->nbr.ptr;
   a.tab = fp32 ? (const void*)m->tab32.ptr : (const void*)m->tab64.ptr;
   a.E = m->E;
+  a.status = m->status.ptr;
   a.alpha = alpha;
   a.beta = beta;
   a.gamma = gamma;
@@ -840,8 +848,8 @@ dgc_status dgc_mesh_upload(int dim, int k, int n_vert, const double* verts, int 
             up(m->Lg_int.upload(t.Lg_int)) && up(m->Lg_fac.upload(t.Lg_fac)) && up(m->Tint.upload(t.Tint)) &&
             up(m->wd.upload(t.wd)) && up(m->wfd.upload(t.wfd)) && up(m->Qfd.upload(t.Qfd)) &&
             up(m->Bd.upload(t.Bd)) && up(m->tab64.upload(stage_blob<double>(t))) &&
-            up(m->tab32.upload(stage_blob<float>(t))) && up(m->status.alloc(1)) &&
-            up(cudaMemset(m->status.ptr, 0, sizeof(int))) &&
+            up(m->tab32.upload(stage_blob<float>(t))) && up(m->status.alloc(2)) &&
+            up(cudaMemset(m->status.ptr, 0, 2 * sizeof(int))) &&
             (!dgc::tc_supported(dim, k) ||
              (dim == 2 ? (up(m->tcblob.upload(dgc::tc_blob(dim, k, 0, t))) &&
                           up(m->tcblob16.upload(dgc::tc_blob(dim, k, 1, t))))
@@ -935,8 +943,8 @@ dgc_status dgc_mesh_upload_quad(int k, int n_vert, const double* verts, int n_el
             up(m->Lg_int.upload(t.Lg_int)) && up(m->Lg_fac.upload(t.Lg_fac)) && up(m->Tint.upload(t.Tint)) &&
             up(m->wd.upload(t.wd)) && up(m->wfd.upload(t.wfd)) && up(m->Qfd.upload(t.Qfd)) &&
             up(m->Bd.upload(t.Bd)) && up(m->tab64.upload(quad_stage_blob<double>(t))) &&
-            up(m->tab32.upload(quad_stage_blob<float>(t))) && up(m->status.alloc(1)) &&
-            up(cudaMemset(m->status.ptr, 0, sizeof(int))) &&
+            up(m->tab32.upload(quad_stage_blob<float>(t))) && up(m->status.alloc(2)) &&
+            up(cudaMemset(m->status.ptr, 0, 2 * sizeof(int))) &&
             up(dgc::quad_tables_to_constant(k, quad_stage_blob<double>(t)));
   if (!ok) {
     cudaError_t err = cudaGetLastError();
@@ -1032,8 +1040,8 @@ dgc_status dgc_mesh_upload_hex(int k, int n_vert, const double* verts, int n_ele
             up(m->Lg_int.upload(t.Lg_int)) && up(m->Lg_fac.upload(t.Lg_fac)) && up(m->Tint.upload(t.Tint)) &&
             up(m->wd.upload(t.wd)) && up(m->wfd.upload(t.wfd)) && up(m->Qfd.upload(t.Qfd)) &&
             up(m->Bd.upload(t.Bd)) && up(m->tab64.upload(quad_stage_blob<double>(t))) &&
-            up(m->tab32.upload(quad_stage_blob<float>(t))) && up(m->status.alloc(1)) &&
-            up(cudaMemset(m->status.ptr, 0, sizeof(int)));
+            up(m->tab32.upload(quad_stage_blob<float>(t))) && up(m->status.alloc(2)) &&
+            up(cudaMemset(m->status.ptr, 0, 2 * sizeof(int)));
   if (!ok) {
     cudaError_t err = cudaGetLastError();
     m->release_all();
@@ -1204,6 +1212,17 @@ dgc_status dgc_mass_apply(dgc_mesh* mesh, const double* v_dg, double* out_dg, in
   if (dgc_status rc = check_mesh(mesh)) return rc;
   if (!v_dg || !out_dg) return fail(DGC_ERR_ARG, "NULL vector");
   DGC_CUDA(dgc::launch_mass(mesh->view(), v_dg, out_dg, inverse != 0, as_stream(stream)));
+  return DGC_OK;
+}
+
+dgc_status dgc_diagnostics(dgc_mesh* mesh, const double* v_dg, double* out, void* stream) {
+  DGC_RANGE();
+  if (dgc_status rc = check_mesh(mesh)) return rc;
+  if (!v_dg || !out) return fail(DGC_ERR_ARG, "NULL vector");
+  DGC_CUDA(mesh->diag_mv.alloc((size_t)mesh->E * mesh->s.D * mesh->s.N));
+  DGC_CUDA(mesh->diag_part.alloc((size_t)std::max(dgc::diag_blocks(mesh->E), 1) * (mesh->s.D + 2)));
+  DGC_CUDA(dgc::launch_diagnostics(mesh->view(), v_dg, mesh->diag_mv.ptr, mesh->diag_part.ptr, out,
+                                   mesh->status.ptr, as_stream(stream)));
   return DGC_OK;
 }
 
@@ -1879,14 +1898,20 @@ dgc_status dgc_state_load(const dgc_mesh* mesh, const void* blob, int64_t size, 
 dgc_status dgc_check(dgc_mesh* mesh, void* stream) {
   if (dgc_status rc = check_mesh(mesh)) return rc;
   cudaStream_t st = as_stream(stream);
-  int word = 0;
-  DGC_CUDA(cudaMemcpyAsync(&word, mesh->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int word[2] = {0, 0};
+  DGC_CUDA(cudaMemcpyAsync(word, mesh->status.ptr, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   DGC_CUDA(cudaStreamSynchronize(st));
-  if (word) {
-    DGC_CUDA(cudaMemsetAsync(mesh->status.ptr, 0, sizeof(int), st));
+  if (word[0]) {
+    DGC_CUDA(cudaMemsetAsync(mesh->status.ptr, 0, 2 * sizeof(int), st));
     DGC_CUDA(cudaStreamSynchronize(st));
-    if (word & 2) return fail(DGC_ERR_TIMEOUT, "a bounded device-side wait gave up (status word 0x%x)", word);
-    return fail(DGC_ERR_NONFINITE, "non-finite residual norm in the pseudo-time iteration (status word 0x%x)", word);
+    if (word[0] & 8)
+      return fail(DGC_ERR_BOUNDS, "a gather index was out of range (checked build; first index %d, status word 0x%x)",
+                  word[1], word[0]);
+    if (word[0] & 2) return fail(DGC_ERR_TIMEOUT, "a bounded device-side wait gave up (status word 0x%x)", word[0]);
+    if (word[0] & 4)
+      return fail(DGC_ERR_NONFINITE, "dgc_diagnostics met a non-finite coefficient (status word 0x%x)", word[0]);
+    return fail(DGC_ERR_NONFINITE, "non-finite residual norm in the pseudo-time iteration (status word 0x%x)",
+                word[0]);
   }
   return DGC_OK;
 }

@@ -7,6 +7,8 @@
 // and per-thread scratch arrays sized for the largest supported order.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "dgc_kernels.h"
 #include "dgc_tc3_layout.h"
 
@@ -83,12 +85,13 @@ __device__ void gather_local(const DevMesh& m, int e, const double* __restrict__
   const Sizes& s = m.s;
   const double sg = m.detJ[e] > 0 ? 1.0 : -1.0;
   for (int f = 0; f < s.NF; ++f) {
-    const long g = m.facet_id[(long)e * s.NF + f];
+    const long g = m.facet_id[(long)e * s.NF + f] + (DGC_CHECKED && m.inject_bad_facet && e == 0 ? m.nF : 0);
     const double sf = sg * (double)m.orient[(long)e * s.NF + f];
+    const bool ok = gather_ok(g, m.nF, m.status);
     for (int j = 0; j < s.NFM; ++j) {
       int jg;
       const double fm = facet_mode(m, e, f, j, &jg);
-      ut[f * s.NFM + j] = sf * fm * u[g * s.NFM + jg];
+      ut[f * s.NFM + j] = ok ? sf * fm * u[g * s.NFM + jg] : 0.0;
     }
   }
   const long base = (long)m.nF * s.NFM + (long)e * s.NINT;
@@ -271,8 +274,14 @@ __global__ void facet_reduce_kernel(DevMesh m, const double* __restrict__ zbuf, 
   if (t >= (long)m.nF * NFM) return;
   const long fg = t / NFM;
   const int j = (int)(t % NFM);
-  const int s0 = m.facet_sides[2 * fg], s1 = m.facet_sides[2 * fg + 1];
   const int sh = NF > 4 ? 3 : 2, mk = (1 << sh) - 1;     // (e << sh) | f
+  int s0 = m.facet_sides[2 * fg], s1 = m.facet_sides[2 * fg + 1];
+  if (!gather_ok(s0 >> sh, m.E, m.status)) s0 = -1;
+  s1 = checked_code(s1, sh, m.E, m.status);
+  if (s0 < 0) {   // only in the checked build, after a recorded violation
+    g[t] = 0.0;
+    return;
+  }
   double v = zbuf[((long)(s0 >> sh) * NF + (s0 & mk)) * NFM + j];
   if (s1 >= 0) v += zbuf[((long)(s1 >> sh) * NF + (s1 & mk)) * NFM + j];
   g[t] = v;
@@ -367,6 +376,7 @@ __global__ void wind_from_potential_kernel(DevMesh m, const double* __restrict__
       for (int j = 0; j < s.NFM; ++j) acc[j] += m.wfd[q] * flux * m.Qfd[q * s.NFM + j];
     }
     const long g = m.facet_id[(long)e * s.NF + f];
+    if (!gather_ok(g, m.nF, m.status)) continue;
     for (int j = 0; j < s.NFM; ++j) {
       int jg;
       const double fm = facet_mode(m, e, f, j, &jg);
@@ -422,6 +432,7 @@ __global__ void hdiv_interpolate_kernel(DevMesh m, const double* __restrict__ va
       for (int j = 0; j < s.NFM; ++j) acc[j] += m.wfd[q] * flux * m.Qfd[q * s.NFM + j];
     }
     const long g = m.facet_id[(long)e * s.NF + f];
+    if (!gather_ok(g, m.nF, m.status)) continue;
     for (int j = 0; j < s.NFM; ++j) {
       int jg;
       const double fm = facet_mode(m, e, f, j, &jg);
@@ -718,6 +729,90 @@ cudaError_t launch_transfer_T(const DevMesh& m, const double* f, double* g, doub
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   facet_reduce_kernel<<<grid_for((long)m.nF * m.s.NFM), BLOCK, 0, s>>>(m, zbuf, g);
+  return cudaGetLastError();
+}
+
+// ---- diagnostics: mass per component and energy of a DG field, deterministic ----
+namespace {
+
+constexpr int DIAG_BLOCK = 256;
+
+// sum of the DIAG_BLOCK values x[t] of a block in a fixed tree order (t = 0 gets it)
+__device__ double block_tree_sum(double x, double* sh) {
+  const int t = threadIdx.x;
+  sh[t] = x;
+  __syncthreads();
+  for (int h = DIAG_BLOCK / 2; h > 0; h >>= 1) {
+    if (t < h) sh[t] += sh[t + h];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// pass 1: per element, int_T w_c = c0 (M_T v_c)_0 (psi^_0 is the constant 1 / c0,
+// c0^2 the reference measure) and int_T |w|^2 = sum_c v_c . (M_T v_c); one partial
+// [D + 2] per block (mass per component, energy, non-finite coefficient count)
+__global__ void diag_partial_kernel(DevMesh m, const double* __restrict__ v, const double* __restrict__ mv,
+                                    double c0, double* __restrict__ partials) {
+  __shared__ double sh[DIAG_BLOCK];
+  const long e = (long)blockIdx.x * DIAG_BLOCK + threadIdx.x;
+  const int D = m.s.D, N = m.s.N;
+  double mass[3] = {0.0, 0.0, 0.0}, energy = 0.0, bad = 0.0;
+  if (e < m.E) {
+    for (int c = 0; c < D; ++c) {
+      const double* x = v + (e * D + c) * N;
+      const double* y = mv + (e * D + c) * N;
+      mass[c] = c0 * y[0];
+      for (int i = 0; i < N; ++i) {
+        energy += x[i] * y[i];
+        bad += isfinite(x[i]) ? 0.0 : 1.0;
+      }
+    }
+  }
+  double* out = partials + (long)blockIdx.x * (D + 2);
+  for (int c = 0; c < D; ++c) {
+    const double s = block_tree_sum(mass[c], sh);
+    if (threadIdx.x == 0) out[c] = s;
+  }
+  const double se = block_tree_sum(energy, sh);
+  const double sb = block_tree_sum(bad, sh);
+  if (threadIdx.x == 0) {
+    out[D] = se;
+    out[D + 1] = sb;
+  }
+}
+
+// pass 2: one block sums the partials in a fixed order; a non-finite coefficient
+// sets bit 2 of the status word
+__global__ void diag_final_kernel(const double* __restrict__ partials, int nblocks, int D, double* out,
+                                  int* status) {
+  __shared__ double sh[DIAG_BLOCK];
+  for (int j = 0; j < D + 2; ++j) {
+    double x = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += DIAG_BLOCK) x += partials[(long)b * (D + 2) + j];
+    const double s = block_tree_sum(x, sh);
+    if (threadIdx.x == 0) {
+      out[j] = s;
+      if (j == D + 1 && s > 0.0) atomicOr(status, 4);
+    }
+  }
+}
+
+}  // namespace
+
+int diag_blocks(long E) { return (int)((E + DIAG_BLOCK - 1) / DIAG_BLOCK); }
+
+cudaError_t launch_diagnostics(const DevMesh& m, const double* v, double* mv, double* partials, double* out,
+                               int* status, cudaStream_t s) {
+  cudaError_t err = launch_mass(m, v, mv, false, s);
+  if (err != cudaSuccess) return err;
+  const int nb = diag_blocks(m.E);
+  // c0^2: the measure of the reference element (simplex 1/D!, square and cube 1)
+  const double c0 = (m.quad || m.hex) ? 1.0 : std::sqrt(m.s.D == 2 ? 0.5 : 1.0 / 6.0);
+  if (nb > 0) diag_partial_kernel<<<nb, DIAG_BLOCK, 0, s>>>(m, v, mv, c0, partials);
+  diag_final_kernel<<<1, DIAG_BLOCK, 0, s>>>(partials, nb, m.s.D, out, status);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 
 #include <vector>
 
+#include "dgc_checked.h"
 #include "dgc_internal.h"
 
 namespace dgc {
@@ -22,6 +23,8 @@ struct DevMesh {
   double* detJ;               // [E]
   const int* nbr;             // [E][NF]  (e' << 2) | f', or -1
   const int* facet_id;        // [E][NF]
+  int* status;                // [2] device status words (gather checks of the checked build)
+  int inject_bad_facet = 0;   // checked build only: DGC_FAULT=gather offsets element 0's facet ids
   const signed char* orient;  // [E][NF]  +1 owner / boundary, -1 otherwise
   const int* facet_sides;     // [nF][2]  (e << 2) | f, second entry -1 on the boundary
   // FP64 tables
@@ -118,6 +121,12 @@ cudaError_t launch_transfer(const DevMesh& m, const double* u_hdiv, double* w_dg
 cudaError_t launch_transfer_T(const DevMesh& m, const double* f_dg, double* g_hdiv, double* zbuf,
                               cudaStream_t s);
 cudaError_t launch_mass(const DevMesh& m, const double* v, double* out, bool inverse, cudaStream_t s);
+// mass per component and energy of a DG field (out [D + 2]: masses, energy, count of
+// non-finite coefficients), deterministic two-pass reduction; mv [E D N] and
+// partials [diag_blocks(E) (D + 2)] are scratch
+int diag_blocks(long E);
+cudaError_t launch_diagnostics(const DevMesh& m, const double* v, double* mv, double* partials, double* out,
+                               int* status, cudaStream_t s);
 cudaError_t launch_wind_from_potential(const DevMesh& m, const double* pot, double* u_hdiv, cudaStream_t s);
 // BDM DOFs of a physical field given at the DOF points: vals [E][NF*QFD + QD][D]
 cudaError_t launch_hdiv_interpolate(const DevMesh& m, const double* vals, double* u_hdiv, cudaStream_t s);

@@ -37,6 +37,7 @@ struct StageArgs {
   const void* Uw;      // [QV*D][E]
   const void* Fw;      // [NF*QF][E]
   const int* nbr;      // [E][NF]: (neighbour << 2) | neighbour's local facet, or -1
+  int* status = nullptr;   // [2] device status words (gather checks of the checked build)
   const void* tab;     // stage table blob (StageTab layout)
   int E;
   double alpha, beta, gamma;
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(256, 1) stage_kernel(StageArgs a) {
   // ---- facet terms ----------------------------------------------------------
 #pragma unroll 1
   for (int f = 0; f < NF; ++f) {
-    const int code = a.nbr[(long)e * NF + f];
+    const int code = checked_code(a.nbr[(long)e * NF + f], 2, a.E, a.status);
     const T* Eo = Ef + f * NFM * NP4;
     T to[CPT][NFM], tn[CPT][NFM], phi[CPT][NFM];
 #pragma unroll

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(32 * kHexWarps) stage_hex_kernel(StageArgs a, 
       const int ax = face_axis(f);
       const int ta = ax == 0 ? 1 : 0, tb = ax == 2 ? 1 : 2;     // tangential axes, increasing
       const T* Es = Eb + face_side(f) * n;
-      const int code = a.nbr[(long)e * 6 + f];
+      const int code = checked_code(a.nbr[(long)e * 6 + f], 3, a.E, a.status);
       __syncwarp();
       for (int j = tid; j < NFM; j += nt) {            // own modal trace, and the neighbour's
         const int al = j / n, be = j % n;

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(128) stage_quad_kernel(StageArgs a) {
       tn[j] = (T)0;
       ph[j] = (T)0;
     }
-    const int code = a.nbr[(long)e * 4 + f];
+    const int code = checked_code(a.nbr[(long)e * 4 + f], 3, a.E, a.status);
     if (code >= 0) {
       const int ne = code >> 3, fn = code & 3;
       const bool rev = (code & 4) != 0;

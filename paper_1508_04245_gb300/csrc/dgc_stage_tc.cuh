@@ -92,7 +92,7 @@ struct StageTcArgs {
   const float* fw3;
   const float* ftab;
   const float* wq3;     // the wind at the volume points, [tile][chunk][d][16][40]
-  // bounded waits: polls of an mbarrier before a wait gives up (0 = 2^26); stall != 0
+  // bounded waits: polls of an mbarrier before a wait gives up (0 = tc::kWaitPolls); stall != 0
   // (a test hook) issues no bulk copy at all, so every wait runs out with nothing in
   // flight and the kernel reports the timeout in bit 1 of the status word
   uint32_t poll;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
   uint64_t* bar_ep = bars + 4;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
-  const uint32_t poll = a.poll ? a.poll : (1u << 26);   // polls per bounded wait
+  const uint32_t poll = a.poll ? a.poll : tc::kWaitPolls;   // polls per bounded wait
   double* red = reinterpret_cast<double*>(bars + 6);   // per-warp sums of mode 3 (8)
 
   // threads 0..255: (element row r of the tile, velocity component c); warps
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
     float to[NF][NFM], tn[NF][NFM];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      const int code = (producer && valid) ? a.nbr[(size_t)e * NF + f] : -1;
+      const int code = (producer && valid) ? checked_code(a.nbr[(size_t)e * NF + f], 2, a.E, a.status) : -1;
       const int ne = code >> 2, fn = code & 3;
 #pragma unroll
       for (int m = 0; m < NFM; ++m) {

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
   volatile int* fw_stop = reinterpret_cast<volatile int*>(bars + 30);
   uint64_t* bar_wnd = bars + 31;      // [4] wind block of a chunk landed
   uint64_t* bar_wfree = bars + 35;    // [4] wind slot consumed (8 volume warps)
-  const uint32_t poll = a.poll ? a.poll : (1u << 26);   // polls per bounded wait
+  const uint32_t poll = a.poll ? a.poll : tc::kWaitPolls;   // polls per bounded wait
 
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
@@ -269,6 +269,8 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
             idle = 0;
           } else if (++idle > poll || *abort_flag) {
             fail();
+          } else {
+            __nanosleep(200);   // nothing to issue yet: leave the issue slots to the compute warps
           }
         }
         // drain: the copies still in flight land before the CTA exits
@@ -536,7 +538,7 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
         const int f = 2 * h + ff;
         unsigned long long to2[NP2], tn2[NP2];
         {
-          const int code = valid ? a.nbr[(size_t)e * 4 + f] : -1;
+          const int code = valid ? checked_code(a.nbr[(size_t)e * 4 + f], 2, a.E, a.status) : -1;
           const ulonglong2* po = reinterpret_cast<const ulonglong2*>(tr_in + tc3_tr_index(tile, f, 0, r, NFM4));
           const ulonglong2* pn = reinterpret_cast<const ulonglong2*>(
               tr_in + tc3_tr_index(code >= 0 ? (code >> 2) / EPT : 0, code & 3, 0,

@@ -164,10 +164,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait on the given phase parity; false when the iteration limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t max_iter = (1u << 26)) {
+// As mbar_try_wait, with the thread suspended until the phase completes or about
+// `ns` nanoseconds have passed: a waiting warp then takes no issue slots from the
+// warps that do the work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t phase, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+// default number of polls of a bounded wait: each poll suspends the thread for up
+// to a microsecond, so a wait gives up after about two seconds
+constexpr uint32_t kWaitPolls = 1u << 21;
+// Bounded wait on the given phase parity; false when the poll limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t max_iter = kWaitPolls) {
   for (uint32_t it = 0; it < max_iter; ++it)
-    if (mbar_try_wait(bar, phase)) return true;
+    if (mbar_try_wait_sleep(bar, phase, 1000u)) return true;
   return false;
 }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {

@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdgconv.so")
+# DGC_LIBRARY=checked selects the test build whose kernels bounds-check every gather
+LIB_PATH = os.path.join(_HERE, "libdgconv_checked.so" if os.environ.get("DGC_LIBRARY") == "checked"
+                        else "libdgconv.so")
 
 DGC_FP64, DGC_FP32, DGC_BF16X3, DGC_TF32X3 = 0, 1, 2, 3
 DGC_SSPRK2, DGC_SSPRK3 = 2, 3
@@ -38,6 +40,7 @@ SIGNATURES = {
     "dgc_transfer_T": [_vp, _vp, _vp, _vp],
     "dgc_transfer_T_noalloc": [_vp, _vp, _vp, _vp],
     "dgc_mass_apply": [_vp, _vp, _vp, ctypes.c_int, _vp],
+    "dgc_diagnostics": [_vp, _vp, _vp, _vp],
     "dgc_conv_apply": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp],
     "dgc_rk_substeps": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
     "dgc_richardson": [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -203,6 +206,14 @@ class Mesh:
         out = self.dg_zeros() if out is None else out
         check(lib().dgc_mass_apply(self._h, _ptr(v_dg, self.n_dg, "v_dg"), _ptr(out, self.n_dg, "out"),
                                    int(inverse), _stream(stream)))
+        return out
+
+    def diagnostics(self, v_dg, out=None, stream=None):
+        """[mass per component..., energy, non-finite count] of v_dg (device, float64)."""
+        import torch
+        out = torch.empty(self.dim + 2, dtype=torch.float64, device="cuda") if out is None else out
+        check(lib().dgc_diagnostics(self._h, _ptr(v_dg, self.n_dg, "v_dg"), _ptr(out, self.dim + 2, "out"),
+                                    _stream(stream)))
         return out
 
     def conv_apply(self, wind, w_dg, out=None, prec="fp64", stream=None):
