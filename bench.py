@@ -223,6 +223,7 @@ def stage_bytes_flops(wl):
 PROFILES = {
     ("square256_k4", "bf16x3"): ("stage_tc_kernel_square256_k4.md", "dgc_stage_tc.cuh"),
     ("square256_k4", "fp32"): ("stage_kernel_square256_k4_fp32.md", "dgc_stage.cuh"),
+    ("cube48_k4", "bf16x3"): ("stage_tc3_kernel_cube48_k4.md", "dgc_stage_tc3.cuh"),
     ("parallelogram256_k4", "fp32"): ("stage_quad_kernel_parallelogram256_k4.md", "dgc_stage_quad.cu"),
     ("parallelepiped32_k3", "fp32"): ("stage_hex_kernel_parallelepiped32_k3.md", "dgc_stage_hex.cu"),
 }
@@ -822,6 +823,9 @@ def stage_roofline(wl, stage_ms, hbm, hbm_src, bf16, bf16_src, prec, fp64_tflops
     else:
         out.update(bound="hbm", achieved=out["achieved_gbs"], peak=hbm, unit="GB/s", peak_source=hbm_src)
     out["frac"] = out["achieved"] / out["peak"]
+    out["traffic"] = ncu_traffic(wl, prec)
+    out["traffic_source"] = ("committed ncu capture of this kernel source, scaled to this workload's elements as its "
+                             "summary states (None once the source changed or without a capture)")
     return out
 
 
@@ -1032,11 +1036,12 @@ def main():
             ts.append(a.elapsed_time(b))
         return min(ts)
     n_lo = max(substeps // 2, 1)
+    n_hi = max(substeps, n_lo + 1)
     mesh.rk_substeps(wind, v, ds, n_lo, 3, args.prec)
     t_lo = time_rk(n_lo)
-    mesh.rk_substeps(wind, v, ds, substeps, 3, args.prec)
-    t_hi = time_rk(substeps)
-    stage_ms = (t_hi - t_lo) / (3 * (substeps - n_lo))
+    mesh.rk_substeps(wind, v, ds, n_hi, 3, args.prec)
+    t_hi = time_rk(n_hi)
+    stage_ms = (t_hi - t_lo) / (3 * (n_hi - n_lo))
 
     # end to end through the public calls with host buffers
     u_host = torch.empty(mesh.n_hdiv, dtype=torch.float64, pin_memory=True)

@@ -567,16 +567,23 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
             qq2[2 * j] = y.x;
             qq2[2 * j + 1] = y.y;
           }
-          unsigned long long o2 = 0ull, n2 = 0ull;
+          // two partial sums per trace: dependency chains of NP2 / 2 packed FMAs
+          unsigned long long oa = 0ull, ob = 0ull, na = 0ull, nb = 0ull;
 #pragma unroll
-          for (int j = 0; j < NP2; ++j) {
-            o2 = tc::f2_fma(qq2[j], to2[j], o2);
-            n2 = tc::f2_fma(qq2[j], tn2[j], n2);
+          for (int j = 0; j < NP2; j += 2) {
+            oa = tc::f2_fma(qq2[j], to2[j], oa);
+            na = tc::f2_fma(qq2[j], tn2[j], na);
+            if (j + 1 < NP2) {
+              ob = tc::f2_fma(qq2[j + 1], to2[j + 1], ob);
+              nb = tc::f2_fma(qq2[j + 1], tn2[j + 1], nb);
+            }
           }
-          float olo, ohi, nlo, nhi;
-          tc::f2_unpack(o2, olo, ohi);
-          tc::f2_unpack(n2, nlo, nhi);
-          const float val = fw * (fw >= 0.f ? olo + ohi : nlo + nhi);
+          float oal, oah, obl, obh, nal, nah, nbl, nbh;
+          tc::f2_unpack(oa, oal, oah);
+          tc::f2_unpack(ob, obl, obh);
+          tc::f2_unpack(na, nal, nah);
+          tc::f2_unpack(nb, nbl, nbh);
+          const float val = fw * (fw >= 0.f ? (oal + obl) + (oah + obh) : (nal + nbl) + (nah + nbh));
           const unsigned long long vv = tc::f2_pack(val, val);
 #pragma unroll
           for (int j = 0; j < NP2; ++j) ph2[j] = tc::f2_fma(qq2[j], vv, ph2[j]);

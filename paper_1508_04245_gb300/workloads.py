@@ -381,6 +381,9 @@ WORKLOADS = {
     "cube32_k3": Workload("cube32_k3", 3, 32, 3, 0.0, 3, "fixed", "uniform", 3, 50),
     "cube48_k4": Workload("cube48_k4", 3, 48, 4, 0.05, 4, "random", "uniform", 3, 200,
                           unit_peak_speed=True),
+    # the cube48_k4 recipe at 1/8 of its size (82944 tetrahedra): the case the kernel
+    # profiles are captured on, small enough for a full ncu capture
+    "cube24_k4": Workload("cube24_k4", 3, 24, 4, 0.05, 4, "random", "uniform", 3, 4, unit_peak_speed=True),
     # parallelograms: 256 x 256 cells of varying size and shear (3.3M DOFs at k = 4)
     "parallelogram256_k4": Workload("parallelogram256_k4", 2, 256, 4, 0.0, 6, "random", "fourier", 3, 100,
                                     shape="quad"),
