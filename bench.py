@@ -62,14 +62,14 @@ def parse():
                     help="skip the oracle runs (errors against the oracle and the cpu_baseline)")
     args = ap.parse_args()
     if args.impl == "dgconv" and args.prec in TC_PRECS and not tc_covers(W.WORKLOADS[args.workload], args.prec):
-        ap.error("the tensor-core precisions cover affine simplices with k <= 4 (tetrahedra in bf16x3 only); "
+        ap.error("the tensor-core precisions cover affine triangles with k <= 5 and tetrahedra with k <= 4 (bf16x3 only); "
                  "use --prec fp32 or fp64 here")
     return args
 
 
 def tc_covers(wl, prec) -> bool:
     """Whether the tensor-core path of the library covers a workload at a precision."""
-    return wl.shape == "simplex" and wl.k <= 4 and (wl.dim == 2 or prec == "bf16x3")
+    return wl.shape == "simplex" and (wl.k <= 5 if wl.dim == 2 else (wl.k <= 4 and prec == "bf16x3"))
 
 
 def dist_env():
@@ -358,7 +358,8 @@ def measure_batched(torch, dgconv, rank: int, world: int, flush, stream, mixed_p
     out_mixed = [s_.clone() for s_ in states]
     # the same graph restricted to the tensor-core orders and to the others
     sub_ms = {}
-    for name, keep in (("k<=4 (tensor cores)", lambda k: k <= 4), ("k>=5 (CUDA cores, fp32)", lambda k: k > 4)):
+    for name, keep in (("k<=4 (tensor cores, two CTAs per SM)", lambda k: k <= 4),
+                       ("k=5 (tensor cores, one CTA per SM)", lambda k: k == 5), ("k=6 (CUDA cores, fp32)", lambda k: k == 6)):
         idx = [i for i, wl in enumerate(insts) if keep(wl.k)]
         if idx:
             sub_ms[name] = timed(lambda idx=idx: dgconv.batch_rk_substeps(
@@ -376,7 +377,7 @@ def measure_batched(torch, dgconv, rank: int, world: int, flush, stream, mixed_p
     return {"instances": len(insts), "elements": sum(m.n_elem for m in meshes),
             "orders": sorted({wl.k for wl in insts}), "substeps": 50, "scheme": "SSP-RK3",
             "mixed": {"value": job_throughput(units, world, ms_mixed), "ms": ms_mixed,
-                      "prec": f"{mixed_prec} (k <= 4), fp32 (k = 5, 6)", "launch": "one cached multi-branch CUDA graph",
+                      "prec": f"{mixed_prec} (k <= 5), fp32 (k = 6)", "launch": "one cached multi-branch CUDA graph",
                       "roofline_frac": byts / (ms_mixed * 1e-3) / 1e9 / hbm},
             "fp64_per_instance": {"value": job_throughput(units, world, ms_fp64), "ms": ms_fp64,
                                   "launch": "one cached graph per instance, in sequence"},
@@ -872,7 +873,7 @@ def measure_config(torch, dgconv, name, rank, world, flush, stream, fp64_tflops)
             best = min(best, a.elapsed_time(b))
         return best
     for prec in ("bf16x3", "fp32", "fp64"):
-        if prec in TC_PRECS and not (wl.k <= 4):
+        if prec in TC_PRECS and not tc_covers(wl, prec):
             continue
         # two graph lengths whose difference is a few hundred milliseconds of stages
         mesh.rk_substeps(wind, v, ds, 1, wl.scheme, prec)
@@ -1196,7 +1197,7 @@ def main():
             errs = {}
             ns_o = ORACLE_SUBSTEPS[WORKLOAD]
             for prec in ("fp64", "fp32", "tf32x3", "bf16x3"):
-                if prec in TC_PRECS and not (wl.k <= 4 and wl.shape == "simplex"):
+                if prec in TC_PRECS and not tc_covers(wl, prec):
                     continue
                 x = mesh.transfer(u_n)
                 mesh.rk_substeps(wind, x, orc["ds"], ns_o, 3, prec)

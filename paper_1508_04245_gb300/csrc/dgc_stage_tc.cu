@@ -91,6 +91,8 @@ std::vector<float> blob_t(const Tables& t) {
 template <int K, int P>
 cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
   using L = TcLayout2D<K, P>;
+  static_assert(L::SMEM_BYTES <= 232448, "shared memory per block");
+  static_assert(L::TMEM_COLS * tc_ctas_per_sm(K) <= 512, "tensor memory per SM");
   if (!a) {
     cudaError_t e0 = cudaFuncSetAttribute(stage_tc_kernel<K, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           L::SMEM_BYTES);
@@ -101,7 +103,8 @@ cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
   auto kern = a->mode == 3 ? stage_tc_kernel<K, P, true> : stage_tc_kernel<K, P, false>;
   const int tiles = (a->E + 127) / 128;
   if (tiles == 0) return cudaSuccess;
-  // persistent: two resident CTAs per SM (shared memory and TMEM allow two)
+  // persistent: two resident CTAs per SM for k <= 4 (shared memory and TMEM allow
+  // two), one for k = 5 (more than half of either)
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -109,7 +112,8 @@ cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  const int grid = tiles < 2 * sms ? tiles : 2 * sms;
+  const int per_sm = tc_ctas_per_sm(K);
+  const int grid = tiles < per_sm * sms ? tiles : per_sm * sms;
   kern<<<grid, 288, L::SMEM_BYTES, s>>>(*a);
   return cudaGetLastError();
 }
@@ -164,6 +168,7 @@ cudaError_t launch_tsoa_in64(int D, int K, const double* v, double* vt, int E, c
     case 2: return tsoa_in64_t<2>(v, vt, E, s);
     case 3: return tsoa_in64_t<3>(v, vt, E, s);
     case 4: return tsoa_in64_t<4>(v, vt, E, s);
+    case 5: return tsoa_in64_t<5>(v, vt, E, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -176,6 +181,7 @@ cudaError_t launch_tsoa_out_sel(int D, int K, const double* vt0, const double* v
     case 2: return tsoa_out_sel_t<2>(vt0, vt1, ctrl, v, E, s);
     case 3: return tsoa_out_sel_t<3>(vt0, vt1, ctrl, v, E, s);
     case 4: return tsoa_out_sel_t<4>(vt0, vt1, ctrl, v, E, s);
+    case 5: return tsoa_out_sel_t<5>(vt0, vt1, ctrl, v, E, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -197,6 +203,7 @@ cudaError_t launch_tsoa_in(int D, int K, const double* v, double* vt, float* vft
     case 2: return tsoa_in_t<2>(v, vt, vft, tr, blob, E, s);
     case 3: return tsoa_in_t<3>(v, vt, vft, tr, blob, E, s);
     case 4: return tsoa_in_t<4>(v, vt, vft, tr, blob, E, s);
+    case 5: return tsoa_in_t<5>(v, vt, vft, tr, blob, E, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -208,11 +215,13 @@ cudaError_t launch_tsoa_out(int D, int K, const double* vt, double* v, int E, cu
     case 2: return tsoa_out_t<2>(vt, v, E, s);
     case 3: return tsoa_out_t<3>(vt, v, E, s);
     case 4: return tsoa_out_t<4>(vt, v, E, s);
+    case 5: return tsoa_out_t<5>(vt, v, E, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-bool tc_supported(int D, int K) { return (D == 2 || D == 3) && K >= 1 && K <= 4; }
+// k = 6 triangles would need 243 KB (BF16x3) or 232 KB (TF32x3) of shared memory per CTA
+bool tc_supported(int D, int K) { return K >= 1 && (D == 2 ? K <= 5 : (D == 3 && K <= 4)); }
 
 int tc_nk(int D, int K) {
   if (D != 2) return 0;
@@ -221,6 +230,7 @@ int tc_nk(int D, int K) {
     case 2: return TcLayout2D<2>::NK;
     case 3: return TcLayout2D<3>::NK;
     case 4: return TcLayout2D<4>::NK;
+    case 5: return TcLayout2D<5>::NK;
     default: return 0;
   }
 }
@@ -236,6 +246,8 @@ std::vector<float> tc_blob(int D, int K, int P, const Tables& t) {
     case 7: return blob_t<3, kBf16x3>(t);
     case 8: return blob_t<4, kTf32x3>(t);
     case 9: return blob_t<4, kBf16x3>(t);
+    case 10: return blob_t<5, kTf32x3>(t);
+    case 11: return blob_t<5, kBf16x3>(t);
     default: return {};
   }
 }
@@ -251,6 +263,8 @@ cudaError_t launch_stage_tc(int D, int K, int P, const StageTcArgs* a, cudaStrea
     case 7: return launch_t<3, kBf16x3>(a, s);
     case 8: return launch_t<4, kTf32x3>(a, s);
     case 9: return launch_t<4, kBf16x3>(a, s);
+    case 10: return launch_t<5, kTf32x3>(a, s);
+    case 11: return launch_t<5, kBf16x3>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -185,8 +185,12 @@ __device__ __forceinline__ void facet_traces(const float* Ef, const float* x, fl
 }
 
 // RICH: the variant for mode 3 (pseudo-time iteration); modes 0-2 compile without it
+// resident CTAs per SM: two for k <= 4, one for k = 5 (its shared memory and TMEM
+// exceed half of the SM's); the register budget follows
+constexpr int tc_ctas_per_sm(int K) { return K <= 4 ? 2 : 1; }
+
 template <int K, int P, bool RICH>
-__global__ void __launch_bounds__(288, 2) stage_tc_kernel(StageTcArgs a) {
+__global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageTcArgs a) {
   using L = TcLayout2D<K, P>;
   constexpr int N = L::N, QV = L::QV, QF = L::QF, NFM = L::NFM, NF = L::NF, NK = L::NK;
   constexpr int NP4 = L::NP4, NFM4 = L::NFM4;

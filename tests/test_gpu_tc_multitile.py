@@ -80,3 +80,34 @@ def test_triangles_rk_400_tiles():
         gm.rk_substeps(cu(wind), v, ds, 3, 3, prec)
         gm.check()
         assert maxrel(host(v), ref) < TOL[prec], prec
+
+
+def test_triangles_order5_400_tiles_one_cta_per_sm_sampled():
+    """k = 5: the triangle kernel runs one CTA per SM (its shared memory and TMEM
+    exceed half of the SM's), so 400 tiles put two or three tiles through every CTA."""
+    k = 5
+    verts, elems, pot, om, wind = make_case(2, k, 160, jitter=0.1, seed=9)
+    gm = dgconv.Mesh(2, k, verts, elems)
+    w = oracle_state(om, k, seed=4)
+    sel = np.random.default_rng(0).choice(om.n_elem, size=1500, replace=False)
+    sel = np.unique(np.concatenate([sel, [0, 127, 128, om.n_elem - 1]]))   # tile edges and the last element
+    ref = ODG.ConvectionOracle(om, k, wind, sel=sel).apply(w)
+    for prec in ("bf16x3", "tf32x3"):
+        got = host(gm.conv_apply(cu(wind), cu(w), prec=prec))[sel]
+        assert maxrel(got, ref) < TOL[prec], prec
+    gm.check()
+
+
+def test_triangles_order5_rk_169_tiles_one_cta_per_sm():
+    k = 5
+    verts, elems, pot, om, wind = make_case(2, k, 104, jitter=0.1, seed=9)
+    assert (om.n_elem + 127) // 128 == 169
+    gm = dgconv.Mesh(2, k, verts, elems)
+    v0 = oracle_state(om, k, seed=5)
+    ds = oracle_ds(om, k, wind)
+    ref = ODG.rk_substeps(ODG.ConvectionOracle(om, k, wind), v0, ds, 2, 3)
+    for prec in ("bf16x3", "tf32x3"):
+        v = cu(v0)
+        gm.rk_substeps(cu(wind), v, ds, 2, 3, prec)
+        assert maxrel(host(v), ref) < TOL[prec], prec
+    gm.check()
