@@ -102,7 +102,7 @@ typedef int dgc_status;
  * mode.
  *   DGC_FP64    FP64 on CUDA cores
  *   DGC_FP32    FP32 on CUDA cores
- *   DGC_BF16X3  triangles, k <= 5: the evaluation at the quadrature points on
+ *   DGC_BF16X3  triangles, k <= 6: the evaluation at the quadrature points on
  *               tcgen05 tensor cores, kind::f16, each operand split exactly into
  *               three BF16 pieces, six products, FP32 accumulation; the test
  *               contractions in FP32 on CUDA cores; FP32 stage increments,
@@ -114,7 +114,7 @@ typedef int dgc_status;
  *               each chunk of 16 quadrature points accumulated separately and the
  *               chunks added in FP32 on CUDA cores; the facet terms in FP32 on
  *               CUDA cores; FP32 increments, FP64 accumulation once per substep
- *   DGC_TF32X3  triangles, k <= 5: as DGC_BF16X3 with kind::tf32 and a
+ *   DGC_TF32X3  triangles, k <= 6: as DGC_BF16X3 with kind::tf32 and a
  *               two-piece TF32 split (about 22 significand bits per operand),
  *               three products
  * Other orders, other element shapes and DGC_TF32X3 on tetrahedra return

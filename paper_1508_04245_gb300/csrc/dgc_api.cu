@@ -359,7 +359,7 @@ dgc_status launch_stage(dgc_mesh* m, bool fp32, const double* vin, const double*
 // the tensor-core precisions (split operands on tcgen05)
 bool is_tc(dgc_prec prec) { return prec == DGC_TF32X3 || prec == DGC_BF16X3; }
 
-// the tensor-core stage kernels cover triangles with k <= 5 and tetrahedra with k <= 4
+// the tensor-core stage kernels cover triangles with k <= 6 and tetrahedra with k <= 4
 bool mesh_tc(const dgc_mesh* m) {
   return !m->quad && !m->hex && m->Ec == 0 && dgc::tc_supported(m->s.D, m->s.K);
 }
@@ -370,7 +370,7 @@ dgc_status check_prec(const dgc_mesh* m, dgc_prec prec) {
     if (mesh_tc(m) && m->s.D == 3 && prec == DGC_TF32X3)
       return fail(DGC_ERR_UNSUPPORTED, "DGC_TF32X3 is available for triangles; tetrahedra take DGC_BF16X3");
     if (mesh_tc(m)) return DGC_OK;
-    return fail(DGC_ERR_UNSUPPORTED, "%s is available for affine triangles with k <= 5 and tetrahedra with k <= 4 (dim %d, k %d%s)",
+    return fail(DGC_ERR_UNSUPPORTED, "%s is available for affine triangles with k <= 6 and tetrahedra with k <= 4 (dim %d, k %d%s)",
                 prec == DGC_TF32X3 ? "DGC_TF32X3" : "DGC_BF16X3", m->s.D, m->s.K,
                 m->quad ? ", parallelograms" : (m->hex ? ", parallelepipeds" : (m->Ec ? ", curved elements" : "")));
   }
@@ -1517,7 +1517,7 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
     if (nsteps[i] < 0) return fail(DGC_ERR_ARG, "instance %d: nsteps must be >= 0", i);
     for (int j = 0; j < i; ++j)
       if (meshes[j] == m) return fail(DGC_ERR_ARG, "instances %d and %d share a mesh handle (scratch)", j, i);
-    // the tensor-core path covers affine triangles k <= 5 and tetrahedra k <= 4 (BF16x3 only);
+    // the tensor-core path covers affine triangles k <= 6 and tetrahedra k <= 4 (BF16x3 only);
     // other instances run their stages in FP32
     pr[i] = (is_tc(prec) && (!mesh_tc(m) || (m->s.D == 3 && prec == DGC_TF32X3))) ? DGC_FP32 : prec;
     if (dgc_status rc = ensure_prec_scratch(m, pr[i])) return rc;

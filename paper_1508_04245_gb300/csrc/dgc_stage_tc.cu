@@ -104,7 +104,7 @@ cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
   const int tiles = (a->E + 127) / 128;
   if (tiles == 0) return cudaSuccess;
   // persistent: two resident CTAs per SM for k <= 4 (shared memory and TMEM allow
-  // two), one for k = 5 (more than half of either)
+  // two), one for k = 5, 6 (more than half of either)
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -169,6 +169,7 @@ cudaError_t launch_tsoa_in64(int D, int K, const double* v, double* vt, int E, c
     case 3: return tsoa_in64_t<3>(v, vt, E, s);
     case 4: return tsoa_in64_t<4>(v, vt, E, s);
     case 5: return tsoa_in64_t<5>(v, vt, E, s);
+    case 6: return tsoa_in64_t<6>(v, vt, E, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -182,6 +183,7 @@ cudaError_t launch_tsoa_out_sel(int D, int K, const double* vt0, const double* v
     case 3: return tsoa_out_sel_t<3>(vt0, vt1, ctrl, v, E, s);
     case 4: return tsoa_out_sel_t<4>(vt0, vt1, ctrl, v, E, s);
     case 5: return tsoa_out_sel_t<5>(vt0, vt1, ctrl, v, E, s);
+    case 6: return tsoa_out_sel_t<6>(vt0, vt1, ctrl, v, E, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -204,6 +206,7 @@ cudaError_t launch_tsoa_in(int D, int K, const double* v, double* vt, float* vft
     case 3: return tsoa_in_t<3>(v, vt, vft, tr, blob, E, s);
     case 4: return tsoa_in_t<4>(v, vt, vft, tr, blob, E, s);
     case 5: return tsoa_in_t<5>(v, vt, vft, tr, blob, E, s);
+    case 6: return tsoa_in_t<6>(v, vt, vft, tr, blob, E, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -216,12 +219,12 @@ cudaError_t launch_tsoa_out(int D, int K, const double* vt, double* v, int E, cu
     case 3: return tsoa_out_t<3>(vt, v, E, s);
     case 4: return tsoa_out_t<4>(vt, v, E, s);
     case 5: return tsoa_out_t<5>(vt, v, E, s);
+    case 6: return tsoa_out_t<6>(vt, v, E, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-// k = 6 triangles would need 243 KB (BF16x3) or 232 KB (TF32x3) of shared memory per CTA
-bool tc_supported(int D, int K) { return K >= 1 && (D == 2 ? K <= 5 : (D == 3 && K <= 4)); }
+bool tc_supported(int D, int K) { return K >= 1 && (D == 2 ? K <= 6 : (D == 3 && K <= 4)); }
 
 int tc_nk(int D, int K) {
   if (D != 2) return 0;
@@ -231,6 +234,7 @@ int tc_nk(int D, int K) {
     case 3: return TcLayout2D<3>::NK;
     case 4: return TcLayout2D<4>::NK;
     case 5: return TcLayout2D<5>::NK;
+    case 6: return TcLayout2D<6>::NK;
     default: return 0;
   }
 }
@@ -248,6 +252,8 @@ std::vector<float> tc_blob(int D, int K, int P, const Tables& t) {
     case 9: return blob_t<4, kBf16x3>(t);
     case 10: return blob_t<5, kTf32x3>(t);
     case 11: return blob_t<5, kBf16x3>(t);
+    case 12: return blob_t<6, kTf32x3>(t);
+    case 13: return blob_t<6, kBf16x3>(t);
     default: return {};
   }
 }
@@ -265,6 +271,8 @@ cudaError_t launch_stage_tc(int D, int K, int P, const StageTcArgs* a, cudaStrea
     case 9: return launch_t<4, kBf16x3>(a, s);
     case 10: return launch_t<5, kTf32x3>(a, s);
     case 11: return launch_t<5, kBf16x3>(a, s);
+    case 12: return launch_t<6, kTf32x3>(a, s);
+    case 13: return launch_t<6, kBf16x3>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

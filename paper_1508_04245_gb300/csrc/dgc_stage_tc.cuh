@@ -185,8 +185,8 @@ __device__ __forceinline__ void facet_traces(const float* Ef, const float* x, fl
 }
 
 // RICH: the variant for mode 3 (pseudo-time iteration); modes 0-2 compile without it
-// resident CTAs per SM: two for k <= 4, one for k = 5 (its shared memory and TMEM
-// exceed half of the SM's); the register budget follows
+// resident CTAs per SM: two for k <= 4, one for k = 5, 6 (their shared memory and
+// TMEM exceed half of the SM's); the register budget follows
 constexpr int tc_ctas_per_sm(int K) { return K <= 4 ? 2 : 1; }
 
 template <int K, int P, bool RICH>
@@ -273,8 +273,8 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
   }
   __syncthreads();
   if (t == issuer_t && !a.stall) {
-    tc::mbar_arrive_expect_tx(bar_tab, L::BLOB * 4);
-    tc::bulk_g2s(blob, a.blob, L::BLOB * 4, bar_tab);
+    tc::mbar_arrive_expect_tx(bar_tab, L::SBLOB * 4);
+    tc::bulk_g2s(blob, a.blob, L::SBLOB * 4, bar_tab);
     load_wind(blockIdx.x);
     load_state(stg, bar_st, blockIdx.x, true, epi_din);
     ++st_issued;
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
   const uint32_t tbase = *tslot;
   const uint32_t lane_base = tbase + ((uint32_t)((warp & 3) * 32) << 16);
   if (!tc::mbar_wait(bar_tab, 0, poll)) *abort_flag = 1;
-  const float* G = blob + L::oG;     // [QV][2][NP4]
+  const float* G = (L::G_GLOBAL ? a.blob : blob) + L::oG;     // [QV][2][NP4]
   const float* Ef = blob + L::oEf;   // [NF][NFM][NP4]
   const float* Qt = blob + L::oQt;   // [QF][NFM4]
   const uint32_t op_s = tc::smem_u32(op);

@@ -63,10 +63,14 @@ struct TcLayout2D {
   static constexpr int szEf = NF * NFM * NP4, szQt = QF * NFM4;
   static constexpr int oTAs = 0;
   static constexpr int oTAw = oTAs + PIECES * szTAs;
-  static constexpr int oG = oTAw + PIECES * szTAw;
-  static constexpr int oEf = oG + szG;
+  static constexpr int oEf = oTAw + PIECES * szTAw;
   static constexpr int oQt = oEf + szEf;
-  static constexpr int BLOB = oQt + szQt;
+  static constexpr int oG = oQt + szQt;
+  static constexpr int BLOB = oG + szG;
+  // the blob part copied into shared memory: all of it, except G for k >= 6, which
+  // the kernel then reads from global memory (through L1) to fit one CTA per SM
+  static constexpr bool G_GLOBAL = K >= 6;
+  static constexpr int SBLOB = G_GLOBAL ? oG : BLOB;
 
   // shared memory (floats): blob | wind staging | operand region
   static constexpr int WSTAGE = 128 * D * NK;          // wind coefficients of the tile
@@ -81,7 +85,7 @@ struct TcLayout2D {
   // start of the operand region takes this tile's state again for the epilogue.
   static constexpr bool STG_ALIAS = STG <= HALF_A;
   static_assert(STG <= OPREG, "the epilogue's state must fit in the GEMM A operands");
-  static constexpr int oWst = BLOB;
+  static constexpr int oWst = SBLOB;
   static constexpr int oOp = pad(oWst + WSTAGE, 32);   // 128-byte aligned
   static constexpr int oStg = STG_ALIAS ? oOp + HALF_A : oOp + OPREG;   // next tile's [vf | din]
   static constexpr int oEpi = oOp;                     // this tile's [vf | din] for the epilogue

@@ -26,9 +26,9 @@ def tol_hdiv_chain(dim, k, prec):
 
 
 def tc_ok(dim, k, prec="bf16x3"):
-    """The tensor-core paths cover affine triangles with k <= 5 in tf32x3 and
+    """The tensor-core paths cover affine triangles with k <= 6 in tf32x3 and
     bf16x3, and tetrahedra with k <= 4 in bf16x3."""
-    return k <= 5 if dim == 2 else (k <= 4 and prec == "bf16x3")
+    return k <= 6 if dim == 2 else (k <= 4 and prec == "bf16x3")
 
 
 def maxrel(got, ref) -> float:

@@ -45,7 +45,7 @@ CASES = [(2, 1, 5, 1), (2, 3, 4, 2), (2, 4, 4, 3), (2, 6, 2, 4), (3, 2, 2, 5)]
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_conv_apply_hdiv(dim, k, n, seed, prec):
     if prec in TC_PRECS and not tc_ok(dim, k, prec):
-        pytest.skip("tensor-core paths: triangles k <= 5, tetrahedra k <= 4 in bf16x3")
+        pytest.skip("tensor-core paths: triangles k <= 6, tetrahedra k <= 4 in bf16x3")
     verts, elems, om, wind, _, u = case(dim, k, n, seed)
     ref = ODG.conv_hdiv(ODG.ConvectionOracle(om, k, wind), u)
     gm = dgconv.Mesh(dim, k, verts, elems)
@@ -58,7 +58,7 @@ def test_conv_apply_hdiv(dim, k, n, seed, prec):
 @pytest.mark.parametrize("extrapolated", [False, True])
 def test_oifs_rhs(dim, k, n, seed, prec, extrapolated):
     if prec in TC_PRECS and not tc_ok(dim, k, prec):
-        pytest.skip("tensor-core paths: triangles k <= 5, tetrahedra k <= 4 in bf16x3")
+        pytest.skip("tensor-core paths: triangles k <= 6, tetrahedra k <= 4 in bf16x3")
     verts, elems, om, wind, wind2, u = case(dim, k, n, seed)
     ds = oracle_ds(om, k, wind)
     kw = dict(wind_prev=wind2, dt_prev=3 * ds) if extrapolated else {}

@@ -77,7 +77,7 @@ def test_transfer_T(cases, dim, k):
 @pytest.mark.parametrize("dim,k", ORDERS)
 def test_conv_apply(cases, dim, k, prec):
     if prec in TC_PRECS and not tc_ok(dim, k, prec):
-        pytest.skip("tensor-core paths: triangles k <= 5, tetrahedra k <= 4 in bf16x3")
+        pytest.skip("tensor-core paths: triangles k <= 6, tetrahedra k <= 4 in bf16x3")
     verts, elems, pot, om, wind, gm = cases(dim, k)
     w = oracle_state(om, k)
     ref = ODG.ConvectionOracle(om, k, wind).apply(w)
@@ -91,7 +91,7 @@ def test_conv_apply(cases, dim, k, prec):
                                           (3, 4, 3)])
 def test_rk_substeps(cases, dim, k, scheme, prec):
     if prec in TC_PRECS and not tc_ok(dim, k, prec):
-        pytest.skip("tensor-core paths: triangles k <= 5, tetrahedra k <= 4 in bf16x3")
+        pytest.skip("tensor-core paths: triangles k <= 6, tetrahedra k <= 4 in bf16x3")
     verts, elems, pot, om, wind, gm = cases(dim, k)
     v0 = oracle_state(om, k, seed=5)
     ds = oracle_ds(om, k, wind)
@@ -118,8 +118,8 @@ def test_rk_graph_replay_matches_fresh_launch(cases):
 
 
 def test_tc_unsupported_orders_are_rejected(cases):
-    """Triangles k = 6 and tetrahedra k = 5 have no tensor-core path; tetrahedra take bf16x3 only."""
-    for dim, k in ((2, 6), (3, 5)):
+    """Tetrahedra k = 5 have no tensor-core path; tetrahedra take bf16x3 only."""
+    for dim, k in ((3, 5),):
         verts, elems, pot, om, wind, gm = cases(dim, k)
         w = cu(oracle_state(om, k))
         for prec in TC_PRECS:

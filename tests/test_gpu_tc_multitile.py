@@ -82,10 +82,11 @@ def test_triangles_rk_400_tiles():
         assert maxrel(host(v), ref) < TOL[prec], prec
 
 
-def test_triangles_order5_400_tiles_one_cta_per_sm_sampled():
-    """k = 5: the triangle kernel runs one CTA per SM (its shared memory and TMEM
-    exceed half of the SM's), so 400 tiles put two or three tiles through every CTA."""
-    k = 5
+def test_triangles_order6_400_tiles_one_cta_per_sm_sampled():
+    """k = 6: the triangle kernel runs one CTA per SM (its shared memory and TMEM
+    exceed half of the SM's) and reads its gradient table from global memory, so
+    400 tiles put two or three tiles through every CTA."""
+    k = 6
     verts, elems, pot, om, wind = make_case(2, k, 160, jitter=0.1, seed=9)
     gm = dgconv.Mesh(2, k, verts, elems)
     w = oracle_state(om, k, seed=4)
