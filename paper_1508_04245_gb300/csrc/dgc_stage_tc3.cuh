@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
         unsigned long long ph2[NP2];
 #pragma unroll
         for (int j = 0; j < NP2; ++j) ph2[j] = 0ull;
-#pragma unroll 2
+#pragma unroll 4
         for (int q = 0; q < QF; ++q) {
           const float fw = valid ? fwb[(f * QF + q) * EPT + el] : 0.f;
           const ulonglong2* Qr = reinterpret_cast<const ulonglong2*>(Qt + q * NFM4);
@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(640, 1) stage_tc3_kernel(StageTcArgs a) {
         unsigned long long r2[NH / 2];
 #pragma unroll
         for (int j = 0; j < NH / 2; ++j) r2[j] = tc::f2_pack(ri[2 * j], ri[2 * j + 1]);
-#pragma unroll 1
+#pragma unroll 4   // loads of later iterations overlap the FMAs of earlier ones
         for (int fm = 0; fm < L::NF * NFM; ++fm) {
           const float pv = phis[fm * 128 + r];
           const unsigned long long pp = tc::f2_pack(pv, pv);
