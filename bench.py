@@ -583,6 +583,12 @@ class OracleTimer:
         one_core = self.units_per_stage * (hi - lo) / self.E / statistics.mean(one[2])
         return all_core, stage_s, one_core
 
+    def one_core_rate(self, warm: int = 1, steps: int = 1):
+        """DOF-stage updates/s of one block of E / cores elements timed alone (one core)."""
+        hi = max(1, self.E // self.cores)
+        one = self._run([(0, hi)], warm, steps)[0]
+        return self.units_per_stage * hi / self.E / statistics.mean(one[2])
+
 
 # ---------------------------------------------------------------------------
 # the oracle on the whole mesh over the host cores: the reference result of a
@@ -1217,7 +1223,10 @@ def main():
                 "sample": f"the FP64 numpy oracle's {len(orc['stage_s'])} SSP-RK3 stages of the full "
                           f"{wl.n_elem}-element mesh (the reference run of max_rel_err_vs_oracle), {orc['cores']} "
                           f"processes on element blocks, one BLAS thread each, a barrier per stage; value = DOF "
-                          f"updates per stage over the mean stage time ({sum(orc['stage_s']):.1f} s of stages)"}
+                          f"updates per stage over the mean stage time ({sum(orc['stage_s']):.1f} s of stages); "
+                          f"one_core_value: one block of E / cores elements timed alone"}
+            if not args.no_cpu_baseline:
+                line["cpu_baseline"]["one_core_value"] = OracleTimer(wl).one_core_rate()
     for name, cfg in configs.items():
         config_errors(torch, cfg, None if oracle is None else oracle.results.get(name))
     if configs:
