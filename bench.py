@@ -376,7 +376,11 @@ def measure_batched(torch, dgconv, rank: int, world: int, flush, stream, mixed_p
     return {"instances": len(insts), "elements": sum(m.n_elem for m in meshes),
             "orders": sorted({wl.k for wl in insts}), "substeps": 50, "scheme": "SSP-RK3",
             "mixed": {"value": job_throughput(units, world, ms_mixed), "ms": ms_mixed,
-                      "prec": f"{mixed_prec} (every order on the tensor cores)", "launch": "one cached multi-branch CUDA graph",
+                      "prec": f"{mixed_prec} (every order on the tensor cores)",
+                      "launch": "one cached CUDA graph; per order one persistent launch per RK stage over "
+                                "the element tiles of all instances of that order; k <= 4 (two CTAs per "
+                                "SM) first, then k = 5, 6 (one CTA per SM), the orders of a phase "
+                                "concurrently",
                       "roofline_frac": byts / (ms_mixed * 1e-3) / 1e9 / hbm},
             "fp64_per_instance": {"value": job_throughput(units, world, ms_fp64), "ms": ms_fp64,
                                   "launch": "one cached graph per instance, in sequence"},

@@ -261,7 +261,13 @@ dgc_status dgc_rk_substeps(dgc_mesh* mesh, const double* wind_hdiv, double* v_dg
  * scratch).  All instances are captured into one CUDA graph whose branches
  * run concurrently; the graph is cached (keyed by every argument) and
  * replayed by later identical calls, and dropped when one of its meshes is
- * freed.  meshes, winds, states, ds, nsteps: host arrays of n_inst entries.
+ * freed.  With DGC_TF32X3 or DGC_BF16X3 the affine-triangle instances of one
+ * order share their stage launches: each stage is one launch of the persistent
+ * kernel over the element tiles of all of them (those whose nsteps is not yet
+ * reached), so the results equal the single calls' bit for bit.  The first
+ * call uploads the per-instance stage arguments to device memory that the
+ * cached graph owns.  meshes, winds, states, ds, nsteps: host arrays of n_inst
+ * entries.
  * With DGC_TF32X3 or DGC_BF16X3, instances whose order the tensor-core path does not cover
  * (see dgc_prec) run their contractions in FP32 on CUDA cores. */
 dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const double* const* winds,

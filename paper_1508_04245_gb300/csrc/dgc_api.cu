@@ -110,6 +110,7 @@ struct BatchGraph {
   std::vector<uint64_t> key;
   std::vector<dgc_mesh*> meshes;
   cudaGraphExec_t exec = nullptr;
+  void* lists = nullptr;   // device stage argument lists and tile offsets of the merged groups
 };
 std::mutex g_batch_mu;
 std::vector<BatchGraph> g_batch_cache;
@@ -416,11 +417,10 @@ dgc_status ensure_tc_scratch(dgc_mesh* m) {
   return DGC_OK;
 }
 
-// one tensor-core stage in increment form (see dgc::StageTcArgs)
-dgc_status launch_stage_tc(dgc_mesh* m, dgc_prec prec, int mode, const float* din, const float* trin, float* dout,
-                           float* trout, double p, double q, double* v, cudaStream_t st) {
+// the arguments of one tensor-core stage in increment form (see dgc::StageTcArgs)
+dgc::StageTcArgs tc_args(dgc_mesh* m, dgc_prec prec, int mode, const float* din, const float* trin, float* dout,
+                         float* trout, double p, double q, double* v) {
   const int P = prec == DGC_BF16X3 ? 1 : 0;
-  if (injected("launch")) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed (injected)");
   dgc::StageTcArgs a{};   // every pointer a mode does not use is null
   a.vf = m->tsf.ptr;
   a.din = din;
@@ -449,9 +449,41 @@ dgc_status launch_stage_tc(dgc_mesh* m, dgc_prec prec, int mode, const float* di
     a.fw3 = m->fw3.ptr;
     a.wq3 = m->wq3.ptr;
   }
-  cudaError_t err = m->s.D == 3 ? dgc::launch_stage_tc3(m->s.K, &a, st) : dgc::launch_stage_tc(m->s.D, m->s.K, P, &a, st);
+  return a;
+}
+
+// stage j of an SSP-RK substep in increment form on the tensor-core path:
+//   RK3: d1 = ds L(v),  d2 = d1/4 + ds/4 L(v + d1),  v += 2/3 d2 + 2/3 ds L(v + d2)
+//   RK2: d1 = ds L(v),  v += d1/2 + ds/2 L(v + d1)
+// (identical to the Shu-Osher / Heun forms).  Each stage reads the facet traces of its
+// input from one buffer and writes those of its output to the other; RK3 has an odd
+// number of stages, so `parity` (the substep's number mod 2) says which buffer holds v's.
+dgc::StageTcArgs tc_rk_stage(dgc_mesh* m, dgc_prec prec, int scheme, int parity, int j, double ds) {
+  float* cur = parity ? m->trB.ptr : m->trA.ptr;
+  float* oth = parity ? m->trA.ptr : m->trB.ptr;
+  if (scheme == DGC_SSPRK2) {
+    if (j == 0) return tc_args(m, prec, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr);
+    return tc_args(m, prec, 1, m->d1.ptr, oth, nullptr, cur, 0.5, 0.5 * ds, m->ts0.ptr);
+  }
+  if (j == 0) return tc_args(m, prec, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr);
+  if (j == 1) return tc_args(m, prec, 0, m->d1.ptr, oth, m->d2.ptr, cur, 0.25, 0.25 * ds, nullptr);
+  return tc_args(m, prec, 1, m->d2.ptr, cur, nullptr, oth, 2.0 / 3.0, 2.0 / 3.0 * ds, m->ts0.ptr);
+}
+
+// launch one tensor-core stage (or, with a.list set, a batched stage over the triangle
+// meshes of one order, dim and precision given by d, k, prec)
+dgc_status launch_tc(int d, int k, dgc_prec prec, const dgc::StageTcArgs& a, cudaStream_t st) {
+  if (injected("launch")) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed (injected)");
+  cudaError_t err = d == 3 ? dgc::launch_stage_tc3(k, &a, st)
+                           : dgc::launch_stage_tc(d, k, prec == DGC_BF16X3 ? 1 : 0, &a, st);
   if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "tensor-core stage launch failed: %s", cudaGetErrorString(err));
   return DGC_OK;
+}
+
+// one tensor-core stage in increment form (see dgc::StageTcArgs)
+dgc_status launch_stage_tc(dgc_mesh* m, dgc_prec prec, int mode, const float* din, const float* trin, float* dout,
+                           float* trout, double p, double q, double* v, cudaStream_t st) {
+  return launch_tc(m->s.D, m->s.K, prec, tc_args(m, prec, mode, din, trin, dout, trout, p, q, v), st);
 }
 
 // one fused pseudo-time iteration on the tensor-core path (mode 3 of dgc::StageTcArgs)
@@ -523,29 +555,18 @@ dgc_status substep_wind(dgc_mesh* m, dgc_prec prec, const WindPlan& w, double ds
   return prepare_wind(m, prec, m->wmix.ptr, st);
 }
 
-// SSP-RK substeps on the tensor-core path, increment form: v^(i) = v^n + d_i,
-//   RK3: d1 = ds L(v),  d2 = d1/4 + ds/4 L(v + d1),  v += 2/3 d2 + 2/3 ds L(v + d2)
-//   RK2: d1 = ds L(v),  v += d1/2 + ds/2 L(v + d1)
-// (identical to the Shu-Osher / Heun forms); the state v is accumulated in FP64
-// once per substep, the increments are FP32.  ABI -> TSOA once, back at the end.
+// SSP-RK substeps on the tensor-core path, increment form (tc_rk_stage): v^(i) = v^n + d_i;
+// the state v is accumulated in FP64 once per substep, the increments are FP32.
+// ABI -> TSOA once, back at the end.
 dgc_status rk_sequence_tc(dgc_mesh* m, dgc_prec prec, double* v, double ds, int nsteps, int scheme,
                           const WindPlan& wp, cudaStream_t st) {
-  float *cur = m->trA.ptr, *oth = m->trB.ptr;
-  if (dgc_status rc = tc_transpose_in(m, v, cur, st)) return rc;
+  if (dgc_status rc = tc_transpose_in(m, v, m->trA.ptr, st)) return rc;
+  const int stages = scheme == DGC_SSPRK2 ? 2 : 3;
   for (int n = 0; n < nsteps; ++n) {
-    dgc_status rc;
-    if ((rc = substep_wind(m, prec, wp, ds, n, st))) return rc;
-    if (scheme == DGC_SSPRK2) {
-      if ((rc = launch_stage_tc(m, prec, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr, st))) return rc;
-      if ((rc = launch_stage_tc(m, prec, 1, m->d1.ptr, oth, nullptr, cur, 0.5, 0.5 * ds, m->ts0.ptr, st))) return rc;
-    } else {
-      if ((rc = launch_stage_tc(m, prec, 0, nullptr, cur, m->d1.ptr, oth, 0.0, ds, nullptr, st))) return rc;
-      if ((rc = launch_stage_tc(m, prec, 0, m->d1.ptr, oth, m->d2.ptr, cur, 0.25, 0.25 * ds, nullptr, st))) return rc;
-      if ((rc = launch_stage_tc(m, prec, 1, m->d2.ptr, cur, nullptr, oth, 2.0 / 3.0, 2.0 / 3.0 * ds, m->ts0.ptr,
-                                st)))
-        return rc;
-      std::swap(cur, oth);
-    }
+    if (dgc_status rc = substep_wind(m, prec, wp, ds, n, st)) return rc;
+    const int parity = scheme == DGC_SSPRK2 ? 0 : (n & 1);
+    for (int j = 0; j < stages; ++j)
+      if (dgc_status rc = launch_tc(m->s.D, m->s.K, prec, tc_rk_stage(m, prec, scheme, parity, j, ds), st)) return rc;
   }
   return tc_transpose_out(m, m->ts0.ptr, v, st);
 }
@@ -629,6 +650,7 @@ void drop_batch_graphs(const dgc_mesh* mesh) {
     BatchGraph& b = g_batch_cache[j];
     if (std::find(b.meshes.begin(), b.meshes.end(), mesh) != b.meshes.end()) {
       if (b.exec) cudaGraphExecDestroy(b.exec);
+      if (b.lists) cudaFree(b.lists);
       g_batch_cache.erase(g_batch_cache.begin() + j);
     } else {
       ++j;
@@ -1498,6 +1520,71 @@ dgc_status dgc_oifs_rhs(dgc_mesh* mesh, const double* u_hdiv, const double* wind
   return DGC_OK;
 }
 
+namespace {
+// The triangle instances of one order on the tensor-core path advance together: each
+// stage is one launch of the persistent kernel over the tiles of all of them
+// (dgc::StageTcArgs::list), so small meshes share the SMs instead of each leaving most
+// of them idle, and a substep takes one launch per stage instead of one per instance.
+struct MergedGroup {
+  int K = 0;
+  std::vector<int> inst;                  // instance numbers, nsteps descending
+  std::vector<dgc::StageTcArgs> lists;    // [parity][stage][instance], host copy
+  std::vector<int> off;                   // first tile of each instance, then the total
+  dgc::StageTcArgs* dlists = nullptr;     // device copies
+  int* doff = nullptr;
+};
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// the stage argument lists and tile offsets of a group (host side)
+void merged_plan(MergedGroup& g, dgc_mesh* const* meshes, const double* ds, int scheme, dgc_prec prec) {
+  const int n = (int)g.inst.size();
+  const int stages = scheme == DGC_SSPRK2 ? 2 : 3, parities = scheme == DGC_SSPRK2 ? 1 : 2;
+  g.lists.assign((size_t)parities * stages * n, dgc::StageTcArgs{});
+  g.off.assign(n + 1, 0);
+  for (int u = 0; u < n; ++u) {
+    dgc_mesh* m = meshes[g.inst[u]];
+    g.off[u + 1] = g.off[u] + (m->E + 127) / 128;
+    for (int par = 0; par < parities; ++par)
+      for (int j = 0; j < stages; ++j)
+        g.lists[((size_t)par * stages + j) * n + u] = tc_rk_stage(m, prec, scheme, par, j, ds[g.inst[u]]);
+  }
+}
+
+size_t merged_bytes(const MergedGroup& g) {
+  return round256(g.lists.size() * sizeof(dgc::StageTcArgs)) + round256(g.off.size() * sizeof(int));
+}
+
+// the launches of a group on one stream (captured): per instance the wind data and the
+// layout transpose in, the substeps, the transpose out
+dgc_status rk_sequence_merged(const MergedGroup& g, dgc_mesh* const* meshes, const double* const* winds,
+                              double* const* states, const int* nsteps, int scheme, dgc_prec prec, cudaStream_t st) {
+  const int n = (int)g.inst.size();
+  const int stages = scheme == DGC_SSPRK2 ? 2 : 3;
+  for (int i : g.inst) {
+    if (dgc_status rc = prepare_wind(meshes[i], prec, winds[i], st)) return rc;
+    if (dgc_status rc = tc_transpose_in(meshes[i], states[i], meshes[i]->trA.ptr, st)) return rc;
+  }
+  int active = n;
+  for (int step = 0; step < nsteps[g.inst[0]]; ++step) {
+    while (active > 0 && nsteps[g.inst[active - 1]] <= step) --active;   // the instances still stepping
+    const int parity = scheme == DGC_SSPRK2 ? 0 : (step & 1);
+    for (int j = 0; j < stages; ++j) {
+      const size_t l = ((size_t)parity * stages + j) * n;
+      dgc::StageTcArgs a = g.lists[l];   // mode, stage kind, tables and wait budget of every instance
+      a.list = g.dlists + l;
+      a.tile_off = g.doff;
+      a.n_list = active;
+      a.batch_tiles = g.off[active];
+      if (dgc_status rc = launch_tc(2, g.K, prec, a, st)) return rc;
+    }
+  }
+  for (int i : g.inst)
+    if (dgc_status rc = tc_transpose_out(meshes[i], meshes[i]->ts0.ptr, states[i], st)) return rc;
+  return DGC_OK;
+}
+}  // namespace
+
 dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const double* const* winds,
                                  double* const* states, const double* ds, const int* nsteps, dgc_scheme scheme,
                                  dgc_prec prec, void* stream) {
@@ -1538,6 +1625,48 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
     for (auto& st : g_batch_streams)
       if (!st) DGC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     cudaStream_t main_st = g_batch_streams[0];
+    // triangle instances on the tensor-core path: one merged group per order
+    std::vector<MergedGroup> groups;
+    std::vector<char> merged(n_inst, 0);
+    for (int i = 0; i < n_inst; ++i) {
+      dgc_mesh* m = meshes[i];
+      if (!is_tc(pr[i]) || m->s.D != 2 || nsteps[i] == 0 || m->E == 0) continue;
+      MergedGroup* g = nullptr;
+      for (MergedGroup& h : groups)
+        if (h.K == m->s.K) g = &h;
+      if (!g) {
+        groups.emplace_back();
+        g = &groups.back();
+        g->K = m->s.K;
+      }
+      g->inst.push_back(i);
+      merged[i] = 1;
+    }
+    size_t lbytes = 0;
+    for (MergedGroup& g : groups) {
+      std::stable_sort(g.inst.begin(), g.inst.end(), [&](int x, int y) { return nsteps[x] > nsteps[y]; });
+      merged_plan(g, meshes, ds, (int)scheme, prec);
+      lbytes += merged_bytes(g);
+    }
+    void* lists = nullptr;
+    if (lbytes) {
+      DGC_CUDA(cudaMalloc(&lists, lbytes));
+      char* p = static_cast<char*>(lists);
+      cudaError_t cerr = cudaSuccess;
+      for (MergedGroup& g : groups) {
+        g.dlists = reinterpret_cast<dgc::StageTcArgs*>(p);
+        g.doff = reinterpret_cast<int*>(p + round256(g.lists.size() * sizeof(dgc::StageTcArgs)));
+        if (cerr == cudaSuccess)
+          cerr = cudaMemcpy(g.dlists, g.lists.data(), g.lists.size() * sizeof(dgc::StageTcArgs), cudaMemcpyHostToDevice);
+        if (cerr == cudaSuccess)
+          cerr = cudaMemcpy(g.doff, g.off.data(), g.off.size() * sizeof(int), cudaMemcpyHostToDevice);
+        p += merged_bytes(g);
+      }
+      if (cerr != cudaSuccess) {
+        cudaFree(lists);
+        return fail(DGC_ERR_CUDA, "batch argument upload failed: %s", cudaGetErrorString(cerr));
+      }
+    }
     std::vector<cudaEvent_t> evs;
     auto new_event = [&](cudaEvent_t* e) {
       cudaError_t err = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
@@ -1547,30 +1676,52 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
     auto cleanup = [&]() {
       for (cudaEvent_t e : evs) cudaEventDestroy(e);
     };
+    // Two phases: first the work whose CTAs leave room for a second one on an SM (the
+    // triangle kernel for k <= 4, the CUDA-core kernels), then the work whose CTAs take a
+    // whole SM (triangles k = 5, 6, the tetrahedral kernel).  Within a phase the merged
+    // groups and the other instances run round robin on the branches (independent graph
+    // paths).  Mixed in one phase, the two kinds of CTA leave SMs half used: a CTA that
+    // needs a whole SM waits for an SM that a smaller one still half occupies.
+    auto whole_sm = [&](int i) { return is_tc(pr[i]) && (meshes[i]->s.D == 3 || meshes[i]->s.K >= 5); };
+    std::vector<std::vector<int>> phase(2);   // items: group g as g, instance i as -(i + 1)
+    for (size_t g = 0; g < groups.size(); ++g) phase[groups[g].K >= 5].push_back((int)g);
+    for (int i = 0; i < n_inst; ++i)
+      if (nsteps[i] > 0 && !merged[i]) phase[whole_sm(i)].push_back(-(i + 1));
+    if (phase[0].empty() && phase[1].empty()) return DGC_OK;   // no instance takes a substep
     DGC_CUDA(begin_capture(main_st));
-    cudaEvent_t fork;
-    cudaError_t err = new_event(&fork);
-    if (err == cudaSuccess) err = cudaEventRecord(fork, main_st);
+    cudaError_t err = cudaSuccess;
     dgc_status rc = DGC_OK;
-    const int branches = std::min(n_inst, kBatchBranches);
-    for (int b = 0; b < branches && err == cudaSuccess; ++b) err = cudaStreamWaitEvent(g_batch_streams[1 + b], fork, 0);
-    // instance i runs on branch i % branches; branches are independent graph paths
-    for (int i = 0; i < n_inst && err == cudaSuccess && rc == DGC_OK; ++i) {
-      if (nsteps[i] == 0) continue;
-      rc = rk_sequence(meshes[i], winds[i], states[i], ds[i], nsteps[i], (int)scheme, pr[i],
-                       g_batch_streams[1 + i % branches]);
-    }
-    for (int b = 0; b < branches && err == cudaSuccess; ++b) {
-      cudaEvent_t join;
-      err = new_event(&join);
-      if (err == cudaSuccess) err = cudaEventRecord(join, g_batch_streams[1 + b]);
-      if (err == cudaSuccess) err = cudaStreamWaitEvent(main_st, join, 0);
+    for (const std::vector<int>& items : phase) {
+      if (items.empty() || err != cudaSuccess || rc != DGC_OK) continue;
+      const int branches = std::min((int)items.size(), kBatchBranches);
+      cudaEvent_t fork;
+      err = new_event(&fork);
+      if (err == cudaSuccess) err = cudaEventRecord(fork, main_st);
+      for (int b = 0; b < branches && err == cudaSuccess; ++b)
+        err = cudaStreamWaitEvent(g_batch_streams[1 + b], fork, 0);
+      for (size_t u = 0; u < items.size() && err == cudaSuccess && rc == DGC_OK; ++u) {
+        cudaStream_t bs = g_batch_streams[1 + u % branches];
+        const int it = items[u];
+        if (it >= 0) {
+          rc = rk_sequence_merged(groups[it], meshes, winds, states, nsteps, (int)scheme, prec, bs);
+        } else {
+          const int i = -it - 1;
+          rc = rk_sequence(meshes[i], winds[i], states[i], ds[i], nsteps[i], (int)scheme, pr[i], bs);
+        }
+      }
+      for (int b = 0; b < branches && err == cudaSuccess; ++b) {
+        cudaEvent_t join;
+        err = new_event(&join);
+        if (err == cudaSuccess) err = cudaEventRecord(join, g_batch_streams[1 + b]);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(main_st, join, 0);
+      }
     }
     cudaGraph_t g = nullptr;
     cudaError_t err2 = cudaStreamEndCapture(main_st, &g);
     cleanup();
     if (rc != DGC_OK || err != cudaSuccess || err2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
+      if (lists) cudaFree(lists);
       if (rc != DGC_OK) return rc;
       return fail(DGC_ERR_CUDA, "batch graph capture failed: %s",
                   cudaGetErrorString(err != cudaSuccess ? err : err2));
@@ -1578,9 +1729,13 @@ dgc_status dgc_batch_rk_substeps(int n_inst, dgc_mesh* const* meshes, const doub
     BatchGraph bg;
     bg.key = key;
     bg.meshes.assign(meshes, meshes + n_inst);
+    bg.lists = lists;
     err = cudaGraphInstantiate(&bg.exec, g, 0);
     cudaGraphDestroy(g);
-    if (err != cudaSuccess) return fail(DGC_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(err));
+    if (err != cudaSuccess) {
+      if (lists) cudaFree(lists);
+      return fail(DGC_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(err));
+    }
     g_batch_cache.push_back(bg);
     hit = &g_batch_cache.back();
   }

@@ -96,12 +96,18 @@ cudaError_t launch_t(const StageTcArgs* a, cudaStream_t s) {
   if (!a) {
     cudaError_t e0 = cudaFuncSetAttribute(stage_tc_kernel<K, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           L::SMEM_BYTES);
+    if (e0 == cudaSuccess)
+      e0 = cudaFuncSetAttribute(stage_tc_kernel<K, P, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                L::SMEM_BYTES);
     if (e0 != cudaSuccess) return e0;
     return cudaFuncSetAttribute(stage_tc_kernel<K, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 L::SMEM_BYTES);
   }
-  auto kern = a->mode == 3 ? stage_tc_kernel<K, P, true> : stage_tc_kernel<K, P, false>;
-  const int tiles = (a->E + 127) / 128;
+  const bool batch = a->list != nullptr;
+  if (batch && a->mode == 3) return cudaErrorInvalidValue;
+  auto kern = a->mode == 3 ? stage_tc_kernel<K, P, true>
+                           : (batch ? stage_tc_kernel<K, P, false, true> : stage_tc_kernel<K, P, false>);
+  const int tiles = batch ? a->batch_tiles : (a->E + 127) / 128;
   if (tiles == 0) return cudaSuccess;
   // persistent: two resident CTAs per SM for k <= 4 (shared memory and TMEM allow
   // two), one for k = 5, 6 (more than half of either)

@@ -97,7 +97,28 @@ struct StageTcArgs {
   // flight and the kernel reports the timeout in bit 1 of the status word
   uint32_t poll;
   int stall;
+  // batched launch (triangles): one kernel over the tiles of several meshes of the same
+  // order and stage kind.  list[j] holds mesh j's arguments (their own list null),
+  // tile_off[j] the launch's number of mesh j's first tile (nondecreasing, tile_off[0] = 0),
+  // batch_tiles the launch's tile count (= tile_off[n_list]); in this struct mode, din's
+  // nullness, blob, poll and stall hold for every mesh, and the per-mesh fields are unused.
+  // null list: one mesh, described by this struct.
+  const StageTcArgs* list;
+  const int* tile_off;
+  int n_list;
+  int batch_tiles;
 };
+
+// the mesh of tile `tile` in a batched launch: the last j with tile_off[j] <= tile
+__device__ __forceinline__ int batch_instance(const int* tile_off, int n, int tile) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_off[mid] <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 namespace tcimpl {
 
@@ -189,8 +210,11 @@ __device__ __forceinline__ void facet_traces(const float* Ef, const float* x, fl
 // TMEM exceed half of the SM's); the register budget follows
 constexpr int tc_ctas_per_sm(int K) { return K <= 4 ? 2 : 1; }
 
-template <int K, int P, bool RICH>
+// BATCH: the tiles of the meshes in a.list (a batched launch); per tile, the mesh's own
+// buffers, size, neighbours, status word and stage coefficients
+template <int K, int P, bool RICH, bool BATCH = false>
 __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageTcArgs a) {
+  static_assert(!(RICH && BATCH), "the pseudo-time iteration runs on one mesh");
   using L = TcLayout2D<K, P>;
   constexpr int N = L::N, QV = L::QV, QF = L::QF, NFM = L::NFM, NF = L::NF, NK = L::NK;
   constexpr int NP4 = L::NP4, NFM4 = L::NFM4;
@@ -220,7 +244,7 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
   const int r = t & 127;
   const int c = (t >> 7) & 1;
   const int issuer_t = 256;
-  const int ntiles = (a.E + 127) / 128;
+  const int ntiles = BATCH ? a.batch_tiles : (a.E + 127) / 128;
   // input and output buffers (mode 3 picks its pair by the parity of the iteration count)
   const float* vf_in = a.vf;
   const float* tr_in = a.trin;
@@ -243,23 +267,37 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
   // issuer-side counts of bulk copies into the staging buffers (drained at exit)
   uint32_t w_issued = 0, st_issued = 0, ep_issued = 0;
   // the next tile's contiguous TR block into L2 ahead of use
-  auto prefetch_tile = [&](int tile) {
-    const uint32_t ntr = 128u * 2 * NF * NFM;  // values per tile in TR
-    tc::bulk_prefetch_l2(tr_in + (size_t)tile * ntr, ntr * 4);
+  // the sources of a tile's bulk copies: its mesh's buffers and its number within that mesh
+  struct TileSrc {
+    int lt;
+    const float *wcoef, *vf, *din, *tr;
   };
-  auto load_wind = [&](int tile) {        // a tile's wind coefficients into the staging buffer
+  auto tile_src = [&](int tile) {
+    TileSrc s{tile, a.wcoef, vf_in, a.din, tr_in};
+    if constexpr (BATCH) {
+      const int j = batch_instance(a.tile_off, a.n_list, tile);
+      const StageTcArgs& b = a.list[j];
+      s = TileSrc{tile - a.tile_off[j], b.wcoef, b.vf, b.din, b.trin};
+    }
+    return s;
+  };
+  auto prefetch_tile = [&](const TileSrc& s) {
+    const uint32_t ntr = 128u * 2 * NF * NFM;  // values per tile in TR
+    tc::bulk_prefetch_l2(s.tr + (size_t)s.lt * ntr, ntr * 4);
+  };
+  auto load_wind = [&](const TileSrc& s) {        // a tile's wind coefficients into the staging buffer
     const uint32_t bytes = (uint32_t)L::WSTAGE * 4;   // whole tile block ([c][k][128])
     tc::mbar_arrive_expect_tx(bar_w, bytes);
-    tc::bulk_g2s(wst, a.wcoef + (size_t)tile * L::WSTAGE, bytes, bar_w);
+    tc::bulk_g2s(wst, s.wcoef + (size_t)s.lt * L::WSTAGE, bytes, bar_w);
     ++w_issued;
   };
   // a tile's blocks of v^n (FP32 copy) and of the stage-input increment into dst
   // (TSOA vectors are allocated in whole tiles: complete, 16-byte aligned blocks)
   const uint32_t blk = (uint32_t)L::TSOA_TILE * 4;
-  auto load_state = [&](float* dst, uint64_t* bar, int tile, bool vf, bool din) {
+  auto load_state = [&](float* dst, uint64_t* bar, const TileSrc& s, bool vf, bool din) {
     tc::mbar_arrive_expect_tx(bar, (vf ? blk : 0u) + (din ? blk : 0u));
-    if (vf) tc::bulk_g2s(dst, vf_in + (size_t)tile * L::TSOA_TILE, blk, bar);
-    if (din) tc::bulk_g2s(dst + L::TSOA_TILE, a.din + (size_t)tile * L::TSOA_TILE, blk, bar);
+    if (vf) tc::bulk_g2s(dst, s.vf + (size_t)s.lt * L::TSOA_TILE, blk, bar);
+    if (din) tc::bulk_g2s(dst + L::TSOA_TILE, s.din + (size_t)s.lt * L::TSOA_TILE, blk, bar);
   };
 
   if (t == 0) {
@@ -275,10 +313,11 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
   if (t == issuer_t && !a.stall) {
     tc::mbar_arrive_expect_tx(bar_tab, L::SBLOB * 4);
     tc::bulk_g2s(blob, a.blob, L::SBLOB * 4, bar_tab);
-    load_wind(blockIdx.x);
-    load_state(stg, bar_st, blockIdx.x, true, epi_din);
+    const TileSrc s0 = tile_src(blockIdx.x);
+    load_wind(s0);
+    load_state(stg, bar_st, s0, true, epi_din);
     ++st_issued;
-    prefetch_tile(blockIdx.x);
+    prefetch_tile(s0);
   }
   if (warp == 0) {
     tc::tmem_alloc(tslot, L::TMEM_COLS);
@@ -298,8 +337,20 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
 
   int it = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int e = tile * 128 + r;
-    const bool valid = e < a.E;
+    // the tile's mesh (batched launches) and the tile's number lt within it
+    int lt = tile;
+    const StageTcArgs* ia = nullptr;
+    if constexpr (BATCH) {
+      const int j = batch_instance(a.tile_off, a.n_list, tile);
+      ia = a.list + j;
+      lt = tile - a.tile_off[j];
+    }
+    const int E = BATCH ? ia->E : a.E;
+    const int* nbr = BATCH ? ia->nbr : a.nbr;
+    int* status = BATCH ? ia->status : a.status;
+    const float* tr_t = BATCH ? ia->trin : tr_in;
+    const int e = lt * 128 + r;
+    const bool valid = e < E;
     const int next = tile + gridDim.x;
 
     // ---- stage input v^n + din (staged by bulk copy) -> state operand of component c
@@ -328,7 +379,7 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
     tc::fence_after_sync();
     const bool run = *abort_flag == 0;
     if (t == issuer_t && run) {
-      if (next < ntiles) load_wind(next);   // the staging buffer is free again
+      if (next < ntiles) load_wind(tile_src(next));   // the staging buffer is free again
       // ---- GEMM A ------------------------------------------------------------------
       // products of pieces (A piece, B piece), smallest first: the tensor-core FP32
       // accumulation rounds partly toward zero, so the small correction products
@@ -364,12 +415,12 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
     float to[NF][NFM], tn[NF][NFM];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      const int code = (producer && valid) ? checked_code(a.nbr[(size_t)e * NF + f], 2, a.E, a.status) : -1;
+      const int code = (producer && valid) ? checked_code(nbr[(size_t)e * NF + f], 2, E, status) : -1;
       const int ne = code >> 2, fn = code & 3;
 #pragma unroll
       for (int m = 0; m < NFM; ++m) {
-        to[f][m] = (producer && valid) ? tr_in[tr_index(e, c, f, m, NFM)] : 0.f;
-        tn[f][m] = code >= 0 ? tr_in[tr_index(ne, c, fn, m, NFM)] : 0.f;
+        to[f][m] = (producer && valid) ? tr_t[tr_index(e, c, f, m, NFM)] : 0.f;
+        tn[f][m] = code >= 0 ? tr_t[tr_index(ne, c, fn, m, NFM)] : 0.f;
       }
     }
     if (producer && run && *abort_flag == 0 && !tc::mbar_wait(bar_A, it & 1, poll)) *abort_flag = 1;
@@ -382,16 +433,18 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
       tc::fence_proxy_async_smem();
       // the FP64 state the epilogue accumulates into (mode 1), toward L2
       if (RICH || a.mode == 1)
-        tc::bulk_prefetch_l2(v_state + (size_t)tile * L::TSOA_TILE, (uint32_t)L::TSOA_TILE * 8);
+        tc::bulk_prefetch_l2((BATCH ? ia->v : v_state) + (size_t)lt * L::TSOA_TILE, (uint32_t)L::TSOA_TILE * 8);
       if constexpr (RICH) tc::bulk_prefetch_l2(a.g + (size_t)tile * L::TSOA_TILE, (uint32_t)L::TSOA_TILE * 8);
       if (epi_vf || epi_din) {
-        load_state(epi, bar_ep, tile, epi_vf, epi_din);
+        load_state(epi, bar_ep, TileSrc{lt, nullptr, BATCH ? ia->vf : vf_in, BATCH ? ia->din : a.din, nullptr},
+                   epi_vf, epi_din);
         ++ep_issued;
       }
       if (next < ntiles) {
-        load_state(stg, bar_st, next, true, epi_din);
+        const TileSrc sn = tile_src(next);
+        load_state(stg, bar_st, sn, true, epi_din);
         ++st_issued;
-        prefetch_tile(next);
+        prefetch_tile(sn);
       }
     }
 
@@ -492,7 +545,7 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
     double ex[N];
 #pragma unroll
     for (int i = 0; i < N; ++i)
-      ex[i] = (producer && valid && a.mode == 1) ? v_state[tsoa_index(e, c, i, N)] : 0.0;
+      ex[i] = (producer && valid && a.mode == 1) ? (BATCH ? ia->v : v_state)[tsoa_index(e, c, i, N)] : 0.0;
     if (producer && run2 && (epi_vf || epi_din) && *abort_flag == 0 && !tc::mbar_wait(bar_ep, it & 1, poll))
       *abort_flag = 1;
     tc::fence_before_sync();
@@ -500,11 +553,26 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
     tc::fence_after_sync();
     const bool fin = run2 && *abort_flag == 0;   // uniform after the barrier
     if (!fin) {
-      if (t == 0) atomicOr(a.status, 2);   // a bounded wait gave up: this CTA stops
+      // a bounded wait gave up: this CTA stops (in a batched launch its later tiles may
+      // belong to any of the meshes: each is told)
+      if (t == 0) {
+        if constexpr (BATCH) {
+          for (int j = 0; j < a.n_list; ++j) atomicOr(a.list[j].status, 2);
+        } else {
+          atomicOr(a.status, 2);
+        }
+      }
       break;
     }
     double racc = 0.0;   // mode 3: sum of rho^2 over this thread's coefficients
     if (producer && valid) {
+      double* vs_t = BATCH ? ia->v : v_state;
+      double* vo_t = BATCH ? ia->v : v_out;
+      float* vfo_t = BATCH ? ia->vf_out : vf_out;
+      float* tro_t = BATCH ? ia->trout : tr_out;
+      float* dout_t = BATCH ? ia->dout : a.dout;
+      const float p_hi = BATCH ? ia->p_hi : a.p_hi, p_lo = BATCH ? ia->p_lo : a.p_lo;
+      const float q_hi = BATCH ? ia->q_hi : a.q_hi, q_lo = BATCH ? ia->q_lo : a.q_lo;
       // inc = p din + q L, L = -r (r carries FP32 accuracy)
       float xo[NP4];
 #pragma unroll
@@ -514,26 +582,26 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
         const size_t ix = tsoa_index(e, c, i, N);
         const int si = (c * N + i) * 128 + r;
         const float ed = epi_din ? epi[L::TSOA_TILE + si] : 0.f;
-        const float inc = fmaf(a.p_hi, ed, fmaf(a.p_lo, ed, -fmaf(a.q_hi, rr[i], a.q_lo * rr[i])));
+        const float inc = fmaf(p_hi, ed, fmaf(p_lo, ed, -fmaf(q_hi, rr[i], q_lo * rr[i])));
         if (RICH) {
           // rho = g - v - tau r and the next iterate, in FP64
-          const double vx = v_state[ix];
+          const double vx = vs_t[ix];
           const double rho = (a.g[ix] - vx) - a.tau * tc::f32_to_f64(rr[i]);
           const double vn = vx + a.ds * rho;
-          v_out[ix] = vn;
+          vo_t[ix] = vn;
           xo[i] = tc::f64_to_f32_rn(vn);
-          vf_out[ix] = xo[i];
+          vfo_t[ix] = xo[i];
           racc += rho * rho;
         } else if (a.mode == 0) {
-          a.dout[ix] = inc;
+          dout_t[ix] = inc;
           xo[i] = epi[si] + inc;
         } else if (a.mode == 1) {
           const double x = ex[i] + tc::f32_to_f64(inc);   // FP64 state accumulation
-          v_out[ix] = x;
+          vo_t[ix] = x;
           xo[i] = tc::f64_to_f32_rn(x);
-          vf_out[ix] = xo[i];
+          vfo_t[ix] = xo[i];
         } else {
-          v_out[ix] = tc::f32_to_f64(inc);
+          vo_t[ix] = tc::f32_to_f64(inc);
         }
       }
       if (a.mode != 2) {
@@ -542,7 +610,7 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
 #pragma unroll
         for (int f = 0; f < NF; ++f)
 #pragma unroll
-          for (int m = 0; m < NFM; ++m) tr_out[tr_index(e, c, f, m, NFM)] = tr[f][m];
+          for (int m = 0; m < NFM; ++m) tro_t[tr_index(e, c, f, m, NFM)] = tr[f][m];
       }
       if constexpr (RICH) racc *= fabs(a.detJ[e]);
     }

@@ -76,6 +76,33 @@ def test_batch_equals_single_instances(prec):
         m.check()
 
 
+@pytest.mark.parametrize("scheme", [2, 3])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_merged_batch_launch_equals_single_instances(prec, scheme):
+    """Triangle instances of one order share each stage launch (a work list over all of
+    their tiles): several meshes per order of uneven size, more tiles than resident CTAs
+    (k = 2: 309 tiles on two CTAs per SM), meshes that stop stepping early (the launch
+    shrinks to the ones still stepping), one CTA per SM at k = 6; each result equals the
+    instance's own rk_substeps run bit for bit."""
+    specs = [(2, 2, 100, 21), (2, 2, 90, 22), (2, 2, 40, 23), (2, 4, 20, 24), (2, 4, 5, 25), (2, 4, 33, 26),
+             (2, 6, 9, 27), (2, 6, 4, 28)]
+    nsteps = [2, 3, 1, 3, 1, 2, 2, 1]
+    cases = [gpu_case(*s) for s in specs]
+    ds = [0.2 * m.min_edge() / ((2 * m.k + 1) * m.max_wind_speed(w)) for m, w, _ in cases]
+    singles = []
+    for (m, w, v0), d, n in zip(cases, ds, nsteps):
+        x = v0.clone()
+        m.rk_substeps(w, x, d, n, scheme, prec)
+        singles.append(host(x).copy())
+    for rep in range(2):   # capture, then replay of the cached graph
+        states = [v0.clone() for _, _, v0 in cases]
+        dgconv.batch_rk_substeps([c[0] for c in cases], [c[1] for c in cases], states, ds, nsteps, scheme, prec)
+        for got, ref in zip(states, singles):
+            assert np.array_equal(host(got), ref)
+    for m, _, _ in cases:
+        m.check()
+
+
 def test_batch_instances_match_oracle():
     insts = []
     for k, n, seed in [(2, 6, 11), (4, 5, 12)]:
