@@ -379,7 +379,6 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
     tc::fence_after_sync();
     const bool run = *abort_flag == 0;
     if (t == issuer_t && run) {
-      if (next < ntiles) load_wind(tile_src(next));   // the staging buffer is free again
       // ---- GEMM A ------------------------------------------------------------------
       // products of pieces (A piece, B piece), smallest first: the tensor-core FP32
       // accumulation rounds partly toward zero, so the small correction products
@@ -411,18 +410,6 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
       }
       tc::mma_commit(bar_A);
     }
-    // ---- own and neighbour facet traces from the trace buffer (while GEMM A runs) ---
-    float to[NF][NFM], tn[NF][NFM];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const int code = (producer && valid) ? checked_code(nbr[(size_t)e * NF + f], 2, E, status) : -1;
-      const int ne = code >> 2, fn = code & 3;
-#pragma unroll
-      for (int m = 0; m < NFM; ++m) {
-        to[f][m] = (producer && valid) ? tr_t[tr_index(e, c, f, m, NFM)] : 0.f;
-        tn[f][m] = code >= 0 ? tr_t[tr_index(ne, c, fn, m, NFM)] : 0.f;
-      }
-    }
     if (producer && run && *abort_flag == 0 && !tc::mbar_wait(bar_A, it & 1, poll)) *abort_flag = 1;
     tc::fence_after_sync();
     __syncthreads();
@@ -448,12 +435,94 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
       }
     }
 
-    // ---- test contractions on CUDA cores (FP32): r_i = facet part + volume part ------
-    // r is held as packed pairs (i = 2j, 2j + 1); the tables' padding rows are zero
+    // ---- test contractions on CUDA cores (FP32): r_i = volume part + facet part ------
+    // r is held as packed pairs (i = 2j, 2j + 1); the tables' padding rows are zero.
+    // Volume part, split by output halves: thread (r, c) accumulates the outputs i of
+    // half c (i in [c NH, c NH + NH)) of BOTH components, so each value of G it loads
+    // serves two products; the other component's half goes to thread (r, 1 - c) through
+    // the wind staging buffer (free from the wind operand until the next tile's wind is
+    // loaded after the epilogue wait).
     constexpr int NP2 = NP4 / 2;
-    unsigned long long r2[NP2];
+    constexpr int NH = NP4 / 2, NH2 = NH / 2;    // outputs per half, as packed pairs
+    static_assert(NH * 256 <= L::WSTAGE, "the exchange fits the wind staging buffer");
+    unsigned long long va[NH2], vb[NH2];         // half c of component c (va) and 1 - c (vb)
 #pragma unroll
-    for (int j = 0; j < NP2; ++j) r2[j] = 0ull;
+    for (int j = 0; j < NH2; ++j) va[j] = vb[j] = 0ull;
+    if (run2 && producer) {
+      // volume: r_i -= sum_q sum_d (Uw[q][d] w_c(xi_q)) G[q][d][i], 4 points per TMEM load
+      // (the state columns are padded to a multiple of 16, so a group never runs past them)
+#pragma unroll 1
+      for (int q0 = 0; q0 < QV; q0 += 4) {
+        float wa[4], wb[4], uq0[4], uq1[4];
+        tc::tmem_ld4(lane_base + L::cS + c * L::NAS + q0, wa);
+        tc::tmem_ld4(lane_base + L::cS + (1 - c) * L::NAS + q0, wb);
+        tc::tmem_ld4(lane_base + L::cW + q0, uq0);
+        tc::tmem_ld4(lane_base + L::cW + L::NAW + q0, uq1);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int ql = 0; ql < 4; ++ql) {
+          if (q0 + ql >= QV) break;
+          const float a0 = valid ? -uq0[ql] * wa[ql] : 0.f, a1 = valid ? -uq1[ql] * wa[ql] : 0.f;
+          const float b0 = valid ? -uq0[ql] * wb[ql] : 0.f, b1 = valid ? -uq1[ql] * wb[ql] : 0.f;
+          const unsigned long long pa0 = tc::f2_pack(a0, a0), pa1 = tc::f2_pack(a1, a1);
+          const unsigned long long pb0 = tc::f2_pack(b0, b0), pb1 = tc::f2_pack(b1, b1);
+          const float* Gq = G + (q0 + ql) * 2 * NP4 + c * NH;   // G[q][0][half c], then G[q][1][half c]
+          if constexpr (NH % 4 == 0) {
+            const ulonglong2* g0p = reinterpret_cast<const ulonglong2*>(Gq);
+            const ulonglong2* g1p = reinterpret_cast<const ulonglong2*>(Gq + NP4);
+#pragma unroll
+            for (int j4 = 0; j4 < NH / 4; ++j4) {
+              const ulonglong2 g0 = g0p[j4], g1 = g1p[j4];
+              va[2 * j4] = tc::f2_fma(pa1, g1.x, tc::f2_fma(pa0, g0.x, va[2 * j4]));
+              va[2 * j4 + 1] = tc::f2_fma(pa1, g1.y, tc::f2_fma(pa0, g0.y, va[2 * j4 + 1]));
+              vb[2 * j4] = tc::f2_fma(pb1, g1.x, tc::f2_fma(pb0, g0.x, vb[2 * j4]));
+              vb[2 * j4 + 1] = tc::f2_fma(pb1, g1.y, tc::f2_fma(pb0, g0.y, vb[2 * j4 + 1]));
+            }
+          } else {
+            const unsigned long long* g0p = reinterpret_cast<const unsigned long long*>(Gq);
+            const unsigned long long* g1p = reinterpret_cast<const unsigned long long*>(Gq + NP4);
+#pragma unroll
+            for (int j = 0; j < NH2; ++j) {
+              const unsigned long long g0 = g0p[j], g1 = g1p[j];
+              va[j] = tc::f2_fma(pa1, g1, tc::f2_fma(pa0, g0, va[j]));
+              vb[j] = tc::f2_fma(pb1, g1, tc::f2_fma(pb0, g0, vb[j]));
+            }
+          }
+        }
+      }
+      // component 1 - c of half c to thread (r, 1 - c): [i within the half][thread]
+#pragma unroll
+      for (int j = 0; j < NH2; ++j) {
+        float lo, hi;
+        tc::f2_unpack(vb[j], lo, hi);
+        wst[(2 * j) * 256 + t] = lo;
+        wst[(2 * j + 1) * 256 + t] = hi;
+      }
+    }
+    __syncthreads();
+    unsigned long long r2[NP2];   // component c, every output
+#pragma unroll
+    for (int j = 0; j < NH2; ++j) {
+      // half 1 - c of component c, from thread (r, 1 - c)
+      const unsigned long long o = (run2 && producer)
+                                       ? tc::f2_pack(wst[(2 * j) * 256 + (t ^ 128)], wst[(2 * j + 1) * 256 + (t ^ 128)])
+                                       : 0ull;
+      r2[j] = c == 0 ? va[j] : o;
+      r2[NH2 + j] = c == 0 ? o : va[j];
+    }
+    // ---- own and neighbour facet traces from the trace buffer (L2: the tile's block is
+    //      prefetched with its state) ---
+    float to[NF][NFM], tn[NF][NFM];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int code = (producer && valid) ? checked_code(nbr[(size_t)e * NF + f], 2, E, status) : -1;
+      const int ne = code >> 2, fn = code & 3;
+#pragma unroll
+      for (int m = 0; m < NFM; ++m) {
+        to[f][m] = (producer && valid) ? tr_t[tr_index(e, c, f, m, NFM)] : 0.f;
+        tn[f][m] = code >= 0 ? tr_t[tr_index(ne, c, fn, m, NFM)] : 0.f;
+      }
+    }
     if (run2 && producer) {
       // facets: upwind flux at the facet points, projected onto the facet basis, then
       // r_i += sum_{f,m} Ef[f][m][i] phi[f][m]
@@ -512,30 +581,6 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
           }
         }
       }
-
-      // volume: r_i -= sum_q sum_d (Uw[q][d] w_c(xi_q)) G[q][d][i], 8 points per TMEM load
-#pragma unroll 1
-      for (int q0 = 0; q0 < QV; q0 += 8) {
-        float wq[8], uq0[8], uq1[8];
-        tcimpl::tmem_load<8>(lane_base + L::cS + c * L::NAS + q0, wq);
-        tcimpl::tmem_load<8>(lane_base + L::cW + q0, uq0);
-        tcimpl::tmem_load<8>(lane_base + L::cW + L::NAW + q0, uq1);
-#pragma unroll
-        for (int ql = 0; ql < 8; ++ql) {
-          if (q0 + ql >= QV) break;
-          const float p0 = valid ? -uq0[ql] * wq[ql] : 0.f;
-          const float p1 = valid ? -uq1[ql] * wq[ql] : 0.f;
-          const unsigned long long pp0 = tc::f2_pack(p0, p0), pp1 = tc::f2_pack(p1, p1);
-          const ulonglong2* Gq = reinterpret_cast<const ulonglong2*>(G + (q0 + ql) * 2 * NP4);
-#pragma unroll
-          for (int j4 = 0; j4 < NP4 / 4; ++j4) {
-            const ulonglong2 g0 = Gq[j4];
-            const ulonglong2 g1 = Gq[NP4 / 4 + j4];
-            r2[2 * j4] = tc::f2_fma(pp1, g1.x, tc::f2_fma(pp0, g0.x, r2[2 * j4]));
-            r2[2 * j4 + 1] = tc::f2_fma(pp1, g1.y, tc::f2_fma(pp0, g0.y, r2[2 * j4 + 1]));
-          }
-        }
-      }
     }
 
     float rr[NP4];
@@ -552,6 +597,10 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
     __syncthreads();
     tc::fence_after_sync();
     const bool fin = run2 && *abort_flag == 0;   // uniform after the barrier
+    if (fin && t == issuer_t && next < ntiles) {
+      tc::fence_proxy_async_smem();   // the exchange's reads of the staging buffer come first
+      load_wind(tile_src(next));
+    }
     if (!fin) {
       // a bounded wait gave up: this CTA stops (in a batched launch its later tiles may
       // belong to any of the meshes: each is told)
