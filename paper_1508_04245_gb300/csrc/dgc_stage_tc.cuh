@@ -208,7 +208,7 @@ __device__ __forceinline__ void facet_traces(const float* Ef, const float* x, fl
 // RICH: the variant for mode 3 (pseudo-time iteration); modes 0-2 compile without it
 // resident CTAs per SM: two for k <= 4, one for k = 5, 6 (their shared memory and
 // TMEM exceed half of the SM's); the register budget follows
-constexpr int tc_ctas_per_sm(int K) { return K <= 4 ? 2 : 1; }
+__host__ __device__ constexpr int tc_ctas_per_sm(int K) { return K <= 4 ? 2 : 1; }
 
 // BATCH: the tiles of the meshes in a.list (a batched launch); per tile, the mesh's own
 // buffers, size, neighbours, status word and stage coefficients
@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
   using L = TcLayout2D<K, P>;
   constexpr int N = L::N, QV = L::QV, QF = L::QF, NFM = L::NFM, NF = L::NF, NK = L::NK;
   constexpr int NP4 = L::NP4, NFM4 = L::NFM4;
+  constexpr bool EARLY_TRACES = tc_ctas_per_sm(K) == 1;
   extern __shared__ __align__(1024) float sm[];
   float* blob = sm;
   float* wst = sm + L::oWst;
@@ -410,6 +411,23 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
       }
       tc::mma_commit(bar_A);
     }
+    // ---- own and neighbour facet traces from the trace buffer: with one CTA per SM
+    //      (k = 5, 6; registers to spare) loaded while GEMM A runs, with two (k <= 4) after
+    //      the volume part, from L2 (the tile's block is prefetched with its state) ----
+    float to[NF][NFM], tn[NF][NFM];
+    auto load_traces = [&]() {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const int code = (producer && valid) ? checked_code(nbr[(size_t)e * NF + f], 2, E, status) : -1;
+        const int ne = code >> 2, fn = code & 3;
+#pragma unroll
+        for (int m = 0; m < NFM; ++m) {
+          to[f][m] = (producer && valid) ? tr_t[tr_index(e, c, f, m, NFM)] : 0.f;
+          tn[f][m] = code >= 0 ? tr_t[tr_index(ne, c, fn, m, NFM)] : 0.f;
+        }
+      }
+    };
+    if constexpr (EARLY_TRACES) load_traces();
     if (producer && run && *abort_flag == 0 && !tc::mbar_wait(bar_A, it & 1, poll)) *abort_flag = 1;
     tc::fence_after_sync();
     __syncthreads();
@@ -472,7 +490,14 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
             const ulonglong2* g1p = reinterpret_cast<const ulonglong2*>(Gq + NP4);
 #pragma unroll
             for (int j4 = 0; j4 < NH / 4; ++j4) {
-              const ulonglong2 g0 = g0p[j4], g1 = g1p[j4];
+              ulonglong2 g0, g1;
+              if constexpr (L::G_GLOBAL) {
+                g0 = tc::ld_keep_u64x2(g0p + j4);
+                g1 = tc::ld_keep_u64x2(g1p + j4);
+              } else {
+                g0 = g0p[j4];
+                g1 = g1p[j4];
+              }
               va[2 * j4] = tc::f2_fma(pa1, g1.x, tc::f2_fma(pa0, g0.x, va[2 * j4]));
               va[2 * j4 + 1] = tc::f2_fma(pa1, g1.y, tc::f2_fma(pa0, g0.y, va[2 * j4 + 1]));
               vb[2 * j4] = tc::f2_fma(pb1, g1.x, tc::f2_fma(pb0, g0.x, vb[2 * j4]));
@@ -483,7 +508,8 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
             const unsigned long long* g1p = reinterpret_cast<const unsigned long long*>(Gq + NP4);
 #pragma unroll
             for (int j = 0; j < NH2; ++j) {
-              const unsigned long long g0 = g0p[j], g1 = g1p[j];
+              const unsigned long long g0 = L::G_GLOBAL ? tc::ld_keep_u64(g0p + j) : g0p[j];
+              const unsigned long long g1 = L::G_GLOBAL ? tc::ld_keep_u64(g1p + j) : g1p[j];
               va[j] = tc::f2_fma(pa1, g1, tc::f2_fma(pa0, g0, va[j]));
               vb[j] = tc::f2_fma(pb1, g1, tc::f2_fma(pb0, g0, vb[j]));
             }
@@ -510,19 +536,7 @@ __global__ void __launch_bounds__(288, tc_ctas_per_sm(K)) stage_tc_kernel(StageT
       r2[j] = c == 0 ? va[j] : o;
       r2[NH2 + j] = c == 0 ? o : va[j];
     }
-    // ---- own and neighbour facet traces from the trace buffer (L2: the tile's block is
-    //      prefetched with its state) ---
-    float to[NF][NFM], tn[NF][NFM];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const int code = (producer && valid) ? checked_code(nbr[(size_t)e * NF + f], 2, E, status) : -1;
-      const int ne = code >> 2, fn = code & 3;
-#pragma unroll
-      for (int m = 0; m < NFM; ++m) {
-        to[f][m] = (producer && valid) ? tr_t[tr_index(e, c, f, m, NFM)] : 0.f;
-        tn[f][m] = code >= 0 ? tr_t[tr_index(ne, c, fn, m, NFM)] : 0.f;
-      }
-    }
+    if constexpr (!EARLY_TRACES) load_traces();
     if (run2 && producer) {
       // facets: upwind flux at the facet points, projected onto the facet basis, then
       // r_i += sum_{f,m} Ef[f][m][i] phi[f][m]

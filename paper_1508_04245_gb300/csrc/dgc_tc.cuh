@@ -111,6 +111,19 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
                : "memory");
 }
 
+// read-only global loads that the L1 keeps ahead of other lines (a table that every
+// thread of the SM reads again for each tile while gathers stream past it)
+__device__ __forceinline__ unsigned long long ld_keep_u64(const void* p) {
+  unsigned long long v;
+  asm("ld.global.nc.L1::evict_last.u64 %0, [%1];" : "=l"(v) : "l"(__cvta_generic_to_global(p)));
+  return v;
+}
+__device__ __forceinline__ ulonglong2 ld_keep_u64x2(const void* p) {
+  ulonglong2 v;
+  asm("ld.global.nc.L1::evict_last.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(__cvta_generic_to_global(p)));
+  return v;
+}
+
 // 32 lanes x 32 bits, 4 / 8 / 16 consecutive columns per thread
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
   uint32_t r[4];
